@@ -1,0 +1,234 @@
+"""FP64 CPU reference of SRM -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, single-threaded reference of the Swelling and Random Migration
+method (Section 2, Algorithms 1-6), written in C (``srm_oracle.c``) and driven
+from here through ctypes.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the product library
+never does, and the two share no code.  See the header of ``srm_oracle.c``
+for the readings of the paper it fixes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "srm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libsrm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.POINTER
+_d, _i64, _u64, _int = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+
+
+def build(force: bool = False) -> str:
+    """Compile the reference with plain gcc, no FMA contraction, no fast-math."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            sig = {
+                "orc_philox4x64_10": ([P(_u64), P(_u64), P(_u64)], None),
+                "orc_unit_dir": ([_u64, _u64, _u64, _u64, _int, P(_d)], _int),
+                "orc_wrap": ([_d, _d], _d),
+                "orc_grid": ([_int, P(_d), _d, _d, _d, P(_i64), P(_d)], None),
+                "orc_create": ([_int, P(_d), _i64, P(_d), P(_d), _d, _d, _d, _d, _int, _int, _int,
+                                _u64, _u64, _int], ctypes.c_void_p),
+                "orc_destroy": ([ctypes.c_void_p], None),
+                "orc_get_x": ([ctypes.c_void_p, P(_d)], None),
+                "orc_set_x": ([ctypes.c_void_p, P(_d)], None),
+                "orc_get_lambda": ([ctypes.c_void_p], _d),
+                "orc_set_lambda": ([ctypes.c_void_p, _d], None),
+                "orc_get_sweep": ([ctypes.c_void_p], _u64),
+                "orc_set_margin": ([ctypes.c_void_p, P(_d)], None),
+                "orc_get_counters": ([ctypes.c_void_p, P(_i64)], None),
+                "orc_phi": ([ctypes.c_void_p, _d], _d),
+                "orc_lambda_for_phi": ([ctypes.c_void_p, _d], _d),
+                "orc_sweep": ([ctypes.c_void_p], _i64),
+                "orc_check": ([ctypes.c_void_p, P(ctypes.c_uint8)], _i64),
+                "orc_pairs": ([ctypes.c_void_p, P(_i64), _i64], _i64),
+                "orc_iterate": ([ctypes.c_void_p, P(_i64)], _int),
+                "orc_run": ([ctypes.c_void_p, _i64], _i64),
+                "orc_pairs_brute": ([_int, P(_d), _i64, P(_d), P(_d), P(_i64), _i64, P(_d)], _i64),
+                "orc_certify": ([_int, P(_d), _i64, P(_d), P(_d), P(_d)], _i64),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(P(_d))
+
+
+def _box3(box, dim):
+    L = np.ones(3)
+    L[:dim] = np.asarray(box, dtype=np.float64)[:dim]
+    return L
+
+
+def philox4x64_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    _load().orc_philox4x64_10(c.ctypes.data_as(P(_u64)), k.ctypes.data_as(P(_u64)),
+                              out.ctypes.data_as(P(_u64)))
+    return out
+
+
+def unit_dir(seed: int, sweep: int, pid: int, l: int, dim: int):
+    u = np.zeros(3)
+    m = _load().orc_unit_dir(seed, sweep, pid, l, dim, _dp(u))
+    return u[:dim], m
+
+
+def wrap(x: float, L: float) -> float:
+    return _load().orc_wrap(x, L)
+
+
+def grid(dim, box, lam, rmax, c_m):
+    n = np.zeros(3, dtype=np.int64)
+    w = np.zeros(3)
+    _load().orc_grid(dim, _dp(_box3(box, dim)), lam, rmax, c_m, n.ctypes.data_as(P(_i64)), _dp(w))
+    return n[:dim], w[:dim]
+
+
+def pairs_brute(dim, box, X, R, cap: int = 1 << 20):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    ij = np.zeros((cap, 2), dtype=np.int64)
+    mg = np.zeros(1)
+    cnt = _load().orc_pairs_brute(dim, _dp(_box3(box, dim)), R.size, _dp(X), _dp(R),
+                                  ij.ctypes.data_as(P(_i64)), cap, _dp(mg))
+    return ij[:min(cnt, cap)].copy(), int(cnt), float(mg[0])
+
+
+def certify(dim, box, X, R):
+    """(colliding pair count, minimum gap S - (R_i + R_j)) by a cell list."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    mg = np.zeros(1)
+    cnt = _load().orc_certify(dim, _dp(_box3(box, dim)), R.size, _dp(X), _dp(R), _dp(mg))
+    return int(cnt), float(mg[0])
+
+
+class System:
+    """One RVE in the reference: P (positions in id order), base radii r,
+    scale lambda (R_i = lambda r_i), target scale, and the SRM parameters."""
+
+    def __init__(self, dim, box, x, r, lam=1.0, lam_t=None, target_phi=None, c_w=0.01,
+                 c_m=0.01, N_k=10, N_l=10, N_shake=10, seed=1, sweep=0, literal=False):
+        lib = _load()
+        self.dim = int(dim)
+        self.box = _box3(box, dim)
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        self.r = np.ascontiguousarray(r, dtype=np.float64)
+        self.n = int(self.r.size)
+        self._h = lib.orc_create(self.dim, _dp(self.box), self.n, _dp(x), _dp(self.r), lam,
+                                 lam if lam_t is None else lam_t, c_w, c_m, N_k, N_l, N_shake,
+                                 seed, sweep, 1 if literal else 0)
+        if lam_t is None and target_phi is not None:
+            lt = lib.orc_lambda_for_phi(self._h, target_phi)
+            lib.orc_destroy(self._h)
+            self._h = lib.orc_create(self.dim, _dp(self.box), self.n, _dp(x), _dp(self.r), lam,
+                                     lt, c_w, c_m, N_k, N_l, N_shake, seed, sweep,
+                                     1 if literal else 0)
+        self._margin = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_destroy(h)
+            self._h = None
+
+    @property
+    def x(self) -> np.ndarray:
+        out = np.zeros(self.n * self.dim)
+        _lib.orc_get_x(self._h, _dp(out))
+        return out.reshape(self.n, self.dim)
+
+    @x.setter
+    def x(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        _lib.orc_set_x(self._h, _dp(v))
+
+    @property
+    def lam(self) -> float:
+        return _lib.orc_get_lambda(self._h)
+
+    @lam.setter
+    def lam(self, v: float):
+        _lib.orc_set_lambda(self._h, v)
+
+    @property
+    def sweep_counter(self) -> int:
+        return int(_lib.orc_get_sweep(self._h))
+
+    def radii(self) -> np.ndarray:
+        return self.lam * self.r
+
+    def phi(self, lam=None) -> float:
+        return _lib.orc_phi(self._h, self.lam if lam is None else lam)
+
+    def lambda_for_phi(self, phi: float) -> float:
+        return _lib.orc_lambda_for_phi(self._h, phi)
+
+    def track_margins(self, on: bool = True):
+        self._margin = np.full(self.n, np.inf) if on else None
+        _lib.orc_set_margin(self._h, _dp(self._margin) if on else None)
+
+    @property
+    def margins(self):
+        return None if self._margin is None else self._margin.copy()
+
+    def counters(self) -> dict:
+        c = np.zeros(5, dtype=np.int64)
+        _lib.orc_get_counters(self._h, c.ctypes.data_as(P(_i64)))
+        return dict(iters=int(c[0]), accepted=int(c[1]), shaken=int(c[2]),
+                    moves_accepted=int(c[3]), sweeps=int(c[4]))
+
+    def sweep(self) -> int:
+        return int(_lib.orc_sweep(self._h))
+
+    def check(self):
+        flags = np.zeros(self.n, dtype=np.uint8)
+        cnt = _lib.orc_check(self._h, flags.ctypes.data_as(P(ctypes.c_uint8)))
+        return int(cnt), flags
+
+    def pairs(self, cap: int = 1 << 20) -> np.ndarray:
+        ij = np.zeros((cap, 2), dtype=np.int64)
+        cnt = _lib.orc_pairs(self._h, ij.ctypes.data_as(P(_i64)), cap)
+        if cnt > cap:
+            return self.pairs(int(cnt))
+        return ij[:cnt].copy()
+
+    def iterate(self):
+        info = np.zeros(3, dtype=np.int64)
+        acc = _lib.orc_iterate(self._h, info.ctypes.data_as(P(_i64)))
+        return int(acc), dict(k_sweeps=int(info[0]), overlapping=int(info[1]),
+                              shake_sweeps=int(info[2]))
+
+    def run(self, max_iters: int = 1 << 40) -> int:
+        return int(_lib.orc_run(self._h, max_iters))
+
+    def certify(self):
+        return certify(self.dim, self.box[:self.dim], self.x, self.radii())
