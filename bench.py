@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the SRM hot path on GB300 (one JSON line on stdout).
+
+A step is one complete generation: Algorithm 1 iterated from the RSA start
+to the target volume fraction, followed by the binary64 certification of the
+final state (time-to-target).  The workload is the 1e6-sphere polydisperse
+clustered RVE (log-normal radii, 200 Gaussian clusters, RSA at 0.1, target
+0.40) in the FP32 cell-relative form with FP64 certification.
+
+value    particle-updates/s = N x sweeps / device time of the K timed steps
+         (inputs resident on the device, CUDA events on the handle's stream),
+         summed over ranks (each rank runs its own RVE: weak scaling).
+e2e      the same metric through the public API from host buffers: srm_init
+         from host arrays (host-to-device copies), the run, the certification
+         and srm_positions (device-to-host copy of the result) all inside the
+         timed region.
+roofline the dominant kernel, from CUDA events recorded between the launches
+         of each super-step in a separate timing pass over the first sweeps.
+
+--impl reference times the FP64 CPU reference on the host cores, each step a
+bounded sample (one sweep of Algorithm 3 over all particles).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s & time-to-target phi, 1e6 3D spheres; FP32 vs FP64; % HBM peak"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def workload_desc(w, precision):
+    return {
+        "workload": (f"{w.name}: {w.dim}D, N={w.n}, box {w.box[0]:.4g}^{w.dim}, target phi "
+                     f"{w.target_phi}, RSA start at f0=0.1"
+                     + (", log-normal radii (mean 1, sd 0.2, truncated [0.5, 2]), 200 Gaussian "
+                        "clusters (sigma = 5 mean radii)" if w.name == "poly_1m" else ", monodisperse")),
+        "n": w.n, "dim": w.dim, "target_phi": w.target_phi,
+        "c_w": w.c_w, "c_m": round(w.c_m, 8), "N_k": w.N_k, "N_l": w.N_l, "N_shake": w.N_shake,
+        "precision": ("fp32 cell-relative offsets, fp64 scale/phi bookkeeping and certification"
+                      if precision == 32 else "fp64 absolute positions (bit-exact with the reference)"),
+        "l2": "256 MiB buffer written between timed steps (L2 flushed)",
+    }
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.dev), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = ["paper_2605_18254_gb300/csrc/k_sweep.cu", "paper_2605_18254_gb300/csrc/k_check.cu",
+                  "paper_2605_18254_gb300/csrc/srm_dev.cuh", "paper_2605_18254_gb300/csrc/srm_stencil.cuh"]
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_sha") != source_sha(KERNEL_SOURCES):
+        return None
+    return e.get("dram_bytes_per_launch_full")
+
+
+def cpu_sample(w, sweeps=1):
+    """The FP64 reference on the host: sweeps of Algorithm 3 over all particles
+    at the first swollen scale.  Returns (particle-updates/s, seconds)."""
+    import oracle
+    s = oracle.System(w.dim, w.box, w.x, w.radii, lam=1.0, target_phi=w.target_phi, c_w=w.c_w,
+                      c_m=w.c_m, N_k=w.N_k, N_l=w.N_l, N_shake=w.N_shake, seed=w.seed)
+    s.lam = 1.0 * (1.0 + w.c_w)
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        s.sweep()
+    dt = time.perf_counter() - t0
+    return w.n * sweeps / dt, dt
+
+
+def make_workload(name):
+    import srm_inputs
+    return srm_inputs.RECIPES[name]()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.time()
+    w = make_workload(args.workload)
+    for _ in range(args.warmup):
+        cpu_sample(w, 1)
+    tot, dt_all = 0.0, []
+    for _ in range(args.steps):
+        ups, dt = cpu_sample(w, 1)
+        dt_all.append(dt)
+    value = w.n * args.steps / sum(dt_all)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particle-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(dt_all) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(w, 64),
+        "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: 1 sweep of Algorithm 3 over all {w.n} particles at the "
+                                   "first swollen scale, single-threaded FP64 reference"},
+        "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": time.time() - t0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_2605_18254_gb300 as srm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    w = make_workload(args.workload)
+    if rank:
+        # every rank generates its own RVE (weak scaling, no data exchange)
+        import srm_inputs
+        w = srm_inputs.RECIPES[args.workload](seed=w.seed + 1000 * rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    x_host = torch.from_numpy(np.ascontiguousarray(w.x)).pin_memory()
+    r_host = torch.from_numpy(np.ascontiguousarray(w.radii)).pin_memory()
+    kw = dict(c_m=w.c_m, c_w=w.c_w, N_k=w.N_k, N_l=w.N_l, N_shake=w.N_shake,
+              precision=args.precision, init="explicit", stream=stream.cuda_stream)
+
+    def new_rve():
+        return srm.Rve(w.dim, w.box, r_host.numpy(), w.target_phi, w.seed, positions=x_host.numpy(), **kw)
+
+    def one_step(timed):
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        ev[0].record(stream)
+        g = new_rve()                       # host -> device copies of the inputs
+        ev[1].record(stream)
+        info = g.run_to_target(args.max_iters)
+        pairs, gap, phi = g.certify()
+        ev[2].record(stream)
+        xo, ro = g.positions()               # device -> host copy of the result
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        st = g.state()
+        g.close()
+        return dict(info=info, pairs=pairs, gap=gap, phi=phi, launches=st["kernel_launches"],
+                    dev_s=ev[1].elapsed_time(ev[2]) / 1e3, e2e_s=ev[0].elapsed_time(ev[3]) / 1e3,
+                    wall_s=wall, sweeps=info["sweeps"])
+
+    for _ in range(args.warmup):
+        one_step(False)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    res = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            res.append(one_step(True))
+    torch.cuda.synchronize()
+    dev_s = sum(r["dev_s"] for r in res)
+    e2e_s = sum(r["e2e_s"] for r in res)
+    sweeps = sum(r["sweeps"] for r in res)
+    updates = float(w.n) * sweeps
+    if dist:
+        t = torch.tensor([dev_s, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([updates], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dev_max, e2e_max, updates_all = float(t[0]), float(t[1]), float(u[0])
+    else:
+        dev_max, e2e_max, updates_all = dev_s, e2e_s, updates
+    if rank != 0:
+        return
+    ok = all(r["pairs"] == 0 and r["info"]["converged"] and abs(r["phi"] - w.target_phi) < 1e-9
+             for r in res)
+
+    # ---- roofline of the dominant kernel: timing pass over the first sweeps
+    g = new_rve()
+    g.set_timing(True)
+    st0 = g.state()
+    info = g.run_to_target(args.timing_iters)
+    tm = g.timings()
+    st1 = g.state()
+    g.close()
+    per_launch = {
+        "sweep": tm["ms_sweep"] / max(1, tm["sweep_launches"]),
+        "check": tm["ms_check"] / max(1, tm["check_launches"]),
+        "bin": tm["ms_bin"] / max(1, tm["supersteps"]),
+    }
+    totals = {"sweep": tm["ms_sweep"], "check": tm["ms_check"], "bin": tm["ms_bin"], "control": tm["ms_control"]}
+    dom = max(("sweep", "check", "bin"), key=lambda k: totals[k])
+    pk, pk_kind = peaks()
+    flops_per_pair = 11.0 if w.dim == 3 else 8.0
+    if dom in ("sweep", "check"):
+        pairs = (st1["pairs_sweep"] - st0["pairs_sweep"]) if dom == "sweep" else (st1["pairs_check"] - st0["pairs_check"])
+        launches = tm["sweep_launches"] if dom == "sweep" else tm["check_launches"]
+        flops = flops_per_pair * pairs / max(1, launches)
+        achieved = flops / (per_launch[dom] * 1e-3) / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e12
+        if args.precision == 64:
+            peak = peak / 64.0
+        roof = {"kernel": f"k_{dom}{args.precision}<{w.dim}>", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": committed_traffic(f"k_{dom}{args.precision}"),
+                "per_launch_ms": per_launch[dom],
+                "work": f"{flops_per_pair:.0f} flops per candidate pair tested x {pairs / max(1, launches):.4g} "
+                        f"pairs per launch (counted by the kernel)",
+                "peak_basis": (f"FP32 lanes: {N_SM} SMs x {FP32_LANES_PER_SM} x 2 flops x "
+                               f"{pk.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz" + (" / 64 (FP64 rate)" if args.precision == 64 else "")),
+                "stage_ms_total": totals, "supersteps": tm["supersteps"]}
+    else:
+        bytes_per = w.n * (64 if args.precision == 32 else 96)
+        achieved = bytes_per / (per_launch["bin"] * 1e-3) / 1e9
+        roof = {"kernel": "binning", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "stage_ms_total": totals}
+    roof["peak_source"] = f"{pk_kind}" + (" (HBM from MEASURED_PEAKS.json)" if pk_kind == "measured" else "")
+
+    # ---- FP64 form on the same sample (first sweeps), for the precision comparison
+    cmp = {}
+    if args.compare_fp64 and args.precision == 32:
+        for prec in (32, 64):
+            kw2 = dict(kw)
+            kw2["precision"] = prec
+            g = srm.Rve(w.dim, w.box, r_host.numpy(), w.target_phi, w.seed, positions=x_host.numpy(), **kw2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            inf = g.run_to_target(args.timing_iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cmp[f"fp{prec}"] = {"particle_updates_per_s": w.n * inf["sweeps"] / (e0.elapsed_time(e1) / 1e3),
+                                "sweeps": inf["sweeps"], "iterations": inf["iterations"]}
+            g.close()
+        cmp["sample"] = f"first {args.timing_iters} iterations of Algorithm 1 from the RSA start"
+        cmp["fp32_over_fp64"] = cmp["fp32"]["particle_updates_per_s"] / cmp["fp64"]["particle_updates_per_s"]
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ups, dt = cpu_sample(w, 1)
+        cpu = {"value": ups, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"1 sweep of Algorithm 3 over all {w.n} particles at the first swollen scale "
+                         f"({dt:.1f} s, single-threaded FP64 reference)"}
+
+    h2d = int(x_host.numel() * 8 + r_host.numel() * 8)
+    d2h = int(w.n * w.dim * 8 + w.n * 8)
+    line = {
+        "metric": METRIC, "value": updates_all / dev_max, "unit": "particle-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dev_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+        "config": workload_desc(w, args.precision) | {"parallelism": f"replicas x{world}"},
+        "time_to_target_s": dev_max / args.steps,
+        "sweeps_per_step": sweeps / args.steps,
+        "certified": ok,
+        "e2e": {"value": updates_all / e2e_max, "unit": "particle-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "time_to_target_s": e2e_max / args.steps},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "precision_compare": cmp or None,
+        "gpu_launches": int(sum(r["launches"] for r in res)),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="poly_1m")
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--max-iters", type=int, default=1 << 40)
+    ap.add_argument("--timing-iters", type=int, default=30)
+    ap.add_argument("--compare-fp64", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

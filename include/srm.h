@@ -1,0 +1,218 @@
+/*
+ * srm.h -- C interface of the GB300 implementation of Swelling and Random
+ * Migration (SRM): generation of periodic representative volume elements
+ * (RVEs) of non-overlapping disks (2D) or spheres (3D) at a target volume
+ * fraction (Tarasovs, "Efficient generation of large-scale non-equilibrium
+ * distributions of particles", Section 2, Algorithms 1-6).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an srm_status; no C++ exception crosses this
+ *     interface.  On failure srm_last_error() returns a message for the
+ *     calling thread.
+ *   - Host pointers are caller-owned; the library copies what it needs and
+ *     never keeps them.  Device memory of a handle is owned by the handle and
+ *     released by srm_destroy (through the allocator given to srm_init, if
+ *     any).
+ *   - All device work of a handle is ordered on the CUDA stream given at
+ *     creation.  Functions that return host results synchronise that stream.
+ *   - A handle must not be used by two threads at once.
+ *   - Positions are in [0, L) per axis, particle-id order, dim values per
+ *     particle (x, y[, z]), double precision.
+ *   - Radii: each particle has a base radius r_i; its radius is R_i =
+ *     lambda * r_i with one scale factor lambda per RVE (the swelling of
+ *     Algorithm 1 line 8, read as a multiplicative factor (1 + c_w) per
+ *     iteration).
+ */
+#ifndef SRM_H
+#define SRM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum srm_status {
+    SRM_OK = 0,
+    SRM_E_ARG = 1,            /* invalid argument (message says which)          */
+    SRM_E_NOMEM = 2,          /* device or host allocation failed                */
+    SRM_E_CUDA = 3,           /* a CUDA call failed (message has the CUDA error) */
+    SRM_E_NOT_CONVERGED = 4,  /* iteration cap reached before the target        */
+    SRM_E_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up              */
+    SRM_E_CERTIFY_FAILED = 6, /* FP64 certification found overlapping pairs     */
+    SRM_E_STATE = 7,          /* call not valid in the handle's current state   */
+    SRM_E_INIT = 8            /* random sequential addition could not place all */
+} srm_status;
+
+/* Base radii.  SRM_RADII_EXPLICIT: r[0..n) given.  SRM_RADII_MONO: every
+ * r_i = mean.  SRM_RADII_LOGNORMAL: log-normal with the given mean and
+ * standard deviation of the radius itself, truncated to [lo, hi] by redrawing
+ * (drawn from the handle's seed). */
+typedef enum { SRM_RADII_EXPLICIT = 0, SRM_RADII_MONO = 1, SRM_RADII_LOGNORMAL = 2 } srm_radii_kind;
+
+typedef struct srm_radii {
+    int32_t kind;
+    int64_t n;
+    const double *r;
+    double mean, sd, lo, hi;
+} srm_radii;
+
+/* Starting configuration (Algorithm 1 line 2).  RSA: random sequential
+ * addition at volume fraction f0, proposals uniform in the box or Gaussian
+ * around n_clusters uniform centres (standard deviation cluster_sigma).
+ * EXPLICIT: init_pos holds non-overlapping positions at scale lambda0. */
+typedef enum { SRM_INIT_RSA_UNIFORM = 0, SRM_INIT_RSA_CLUSTERED = 1, SRM_INIT_EXPLICIT = 2 } srm_init_kind;
+
+/* Arithmetic of the path: SRM_PREC_F64 keeps absolute positions in binary64
+ * and reproduces the FP64 reference bit for bit; SRM_PREC_F32 keeps binary32
+ * offsets relative to the particle's cell and decides collisions with a
+ * conservative guard band, with the scale, phi and the final certification in
+ * binary64. */
+typedef enum { SRM_PREC_F64 = 64, SRM_PREC_F32 = 32 } srm_precision;
+
+typedef struct srm_params {
+    double c_w;              /* swelling rate: lambda <- lambda (1 + c_w)        */
+    double c_m;              /* migration step length (absolute)                 */
+    int32_t N_k;             /* sweeps tried per iteration before the shake      */
+    int32_t N_l;             /* trial moves per particle and sweep               */
+    int32_t N_shake;         /* sweeps of the shake step                          */
+    int32_t precision;       /* srm_precision                                    */
+    int32_t init;            /* srm_init_kind                                    */
+    int32_t n_clusters;      /* SRM_INIT_RSA_CLUSTERED                           */
+    double cluster_sigma;    /* SRM_INIT_RSA_CLUSTERED                           */
+    double f0;               /* RSA: starting volume fraction                    */
+    const double *init_pos;  /* SRM_INIT_EXPLICIT: host, n*dim                   */
+    double lambda0;          /* > 0: starting scale (EXPLICIT); else 1            */
+    double lambda_t;         /* > 0: target scale instead of the one of phi      */
+    double guard;            /* SRM_PREC_F32: relative guard on squared distance */
+    uint64_t sweep0;         /* first value of the sweep counter (resume)        */
+} srm_params;
+
+/* Fills p with the defaults: c_w = 0.01, c_m = 0 (must be set), N_k = N_l =
+ * N_shake = 10, FP64, RSA uniform, f0 = 0.1, guard = 4e-6. */
+void srm_params_default(srm_params *p);
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns a device pointer of at least bytes, usable on stream, or NULL.
+ * NULL allocator: the library uses cudaMallocAsync/cudaFreeAsync on the
+ * handle's stream. */
+typedef struct srm_allocator {
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, void *stream);
+    void *ctx;
+} srm_allocator;
+
+typedef struct srm_rve srm_rve;
+
+/* Creates an RVE: periodic box L[0..dim), dimension 2 or 3, base radii,
+ * target volume fraction phi_t in (0, 1), seed of the migration draws,
+ * parameters (NULL: defaults, which leaves c_m = 0 and fails), CUDA stream
+ * (NULL: the legacy default stream), allocator (NULL: cudaMallocAsync).
+ * The target scale is lambda_t = (phi_t prod L / S0)^(1/d), S0 = sum of the
+ * base disk areas or sphere volumes (Algorithm 1 line 3).
+ * Rejects (SRM_E_ARG): dim not 2 or 3, n < 1, L <= 0, phi_t outside (0, 1),
+ * c_m <= 0, N_k, N_l < 1, N_shake < 0, and boxes narrower than three cells of
+ * the final cell size 2.5 lambda_t max r + c_m on some axis (the minimum-image
+ * search of Algorithm 5 needs them).  The starting positions are uploaded;
+ * device state is created.  Returns SRM_E_INIT if RSA fails. */
+srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_radii *radii,
+                    double phi_t, uint64_t seed, const srm_params *p, void *cuda_stream,
+                    const srm_allocator *alloc);
+
+typedef struct srm_step_info {
+    int32_t result;        /* 1 swollen state accepted, 0 discarded and shaken, 2 at target */
+    int32_t k_sweeps;      /* sweeps of the N_k loop in this iteration                      */
+    int32_t shake_sweeps;  /* sweeps of the shake step                                       */
+    int64_t overlapping;   /* colliding particles after the last check of the N_k loop       */
+    double phi;            /* volume fraction of P after the iteration (binary64)            */
+    double lambda;         /* scale of P after the iteration                                 */
+    uint64_t sweep;        /* sweep counter after the iteration                              */
+} srm_step_info;
+
+/* One iteration of Algorithm 1 (lines 4-23): swell the copy Q, up to N_k
+ * rounds of (bin, sweep of Algorithm 3, check of Algorithm 6); accept Q if it
+ * is collision-free, else discard it and shake P with N_shake sweeps. */
+srm_status srm_step(srm_rve *h, srm_step_info *out);
+
+typedef struct srm_run_info {
+    int64_t iterations, accepted, shaken, sweeps;
+    double phi, lambda;
+    uint64_t sweep;
+} srm_run_info;
+
+/* Iterates Algorithm 1 until P reaches the target scale (volume fraction
+ * phi_t, Section 2 step e) or max_iters iterations were run
+ * (SRM_E_NOT_CONVERGED).  Runs on the device without a host round trip per
+ * iteration; the host polls a completion word every few dozen sweeps. */
+srm_status srm_run_to_target(srm_rve *h, int64_t max_iters, srm_run_info *out);
+
+/* FP64 certification of P (termination, Section 2 step e): number of pairs
+ * i < j with sqrt(|x_i - x_j|^2) <= R_i + R_j under the minimum image,
+ * smallest gap S - (R_i + R_j) over pairs of neighbouring cells, and phi.
+ * Any pointer may be NULL.  Returns SRM_E_CERTIFY_FAILED if pairs > 0. */
+srm_status srm_certify(srm_rve *h, int64_t *overlap_pairs, double *min_gap, double *phi);
+
+/* Copies P to the host in particle-id order: xyz[n*dim], radii[n] (R_i =
+ * lambda r_i; may be NULL).  Synchronises the stream. */
+srm_status srm_positions(srm_rve *h, double *xyz, double *radii);
+
+/* Colliding pairs of P at its current scale (Algorithm 6 over all pairs),
+ * i < j by particle id, lexicographic order, as int64 pairs ij[2k], ij[2k+1];
+ * writes min(cap, *n) pairs and sets *n to the total. */
+srm_status srm_overlap_pairs(srm_rve *h, int64_t *ij, int64_t cap, int64_t *n);
+
+/* Runs count sweeps of Algorithm 3 on P at its current scale (each preceded
+ * by a fresh binning, grid of the current scale): the relaxation move with
+ * no swelling (Section 3.3, zero swelling rate).  Advances the sweep counter.
+ * *moved (may be NULL) receives the number of accepted moves of the last
+ * sweep. */
+srm_status srm_sweep(srm_rve *h, int32_t count, int64_t *moved);
+
+/* Sets the scale of P (no moves; may create overlaps). */
+srm_status srm_set_scale(srm_rve *h, double lambda);
+
+typedef struct srm_state_info {
+    int32_t dim, precision;
+    int64_t n;
+    double lambda, lambda_t, phi, phi_t;
+    uint64_t sweep;
+    int64_t iterations, accepted, shaken, sweeps;
+    int32_t done;
+    int32_t grid[3];            /* cells per axis of the current iteration           */
+    int64_t kernel_launches;    /* kernels this handle has launched since creation   */
+    uint64_t pairs_sweep;       /* candidate pairs tested by the sweeps (Alg 3/5)    */
+    uint64_t pairs_check;       /* candidate pairs tested by the checks (Alg 6)      */
+} srm_state_info;
+
+srm_status srm_get_state(srm_rve *h, srm_state_info *out);
+
+/* Per-stage device time of the super-steps run while timing is on, from CUDA
+ * events recorded between the launches of each super-step (one host
+ * synchronisation per super-step while on, so use it for measurement only).
+ * Stages: begin + binning (Algorithm 2), each colour launch of the sweep
+ * (Algorithm 3), the check (Algorithm 6), the control step. */
+typedef struct srm_timings {
+    double ms_bin, ms_sweep, ms_check, ms_control;
+    int64_t supersteps;       /* super-steps that did work while timing was on */
+    int64_t sweep_launches;   /* colour launches of the sweep kernel            */
+    int64_t check_launches;   /* launches of the check kernel that did work     */
+} srm_timings;
+
+/* on != 0: later srm_step / srm_run_to_target / srm_sweep calls record
+ * per-stage times (and the accumulated times are reset); on == 0: back to
+ * plain graph replay. */
+srm_status srm_set_timing(srm_rve *h, int32_t on);
+srm_status srm_get_timings(srm_rve *h, srm_timings *out);
+
+/* Releases the handle and its device memory (stream-ordered). */
+void srm_destroy(srm_rve *h);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *srm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRM_H */

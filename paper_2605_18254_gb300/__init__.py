@@ -1,0 +1,354 @@
+"""Python binding of the SRM CUDA library (include/srm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of ``libsrm.so``.  Functions carry the names of the C interface
+(``srm_init``, ``srm_step``, ``srm_run_to_target``, ``srm_certify``,
+``srm_positions``, ...); the ``Rve`` class wraps one handle.  PyTorch supplies
+the CUDA stream and, by default, device memory through its caching allocator.
+
+The library is built in the package tree (``build.py``); loading fails with
+an exception if it cannot be built or loaded -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_double, c_int32, c_int64,
+                    c_size_t, c_uint64, c_void_p)
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["SrmError", "Rve", "load", "srm_init", "srm_step", "srm_run_to_target", "srm_certify",
+           "srm_positions", "srm_overlap_pairs", "srm_sweep", "srm_set_scale", "srm_get_state",
+           "srm_destroy", "srm_last_error", "srm_set_timing", "srm_get_timings", "PREC_F64",
+           "PREC_F32"]
+
+PREC_F64, PREC_F32 = 64, 32
+RADII_EXPLICIT, RADII_MONO, RADII_LOGNORMAL = 0, 1, 2
+INIT_RSA_UNIFORM, INIT_RSA_CLUSTERED, INIT_EXPLICIT = 0, 1, 2
+
+STATUS = {0: "SRM_OK", 1: "SRM_E_ARG", 2: "SRM_E_NOMEM", 3: "SRM_E_CUDA",
+          4: "SRM_E_NOT_CONVERGED", 5: "SRM_E_DEVICE_TIMEOUT", 6: "SRM_E_CERTIFY_FAILED",
+          7: "SRM_E_STATE", 8: "SRM_E_INIT"}
+
+
+class SrmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class srm_radii(Structure):
+    _fields_ = [("kind", c_int32), ("n", c_int64), ("r", c_void_p), ("mean", c_double),
+                ("sd", c_double), ("lo", c_double), ("hi", c_double)]
+
+
+class srm_params(Structure):
+    _fields_ = [("c_w", c_double), ("c_m", c_double), ("N_k", c_int32), ("N_l", c_int32),
+                ("N_shake", c_int32), ("precision", c_int32), ("init", c_int32),
+                ("n_clusters", c_int32), ("cluster_sigma", c_double), ("f0", c_double),
+                ("init_pos", c_void_p), ("lambda0", c_double), ("lambda_t", c_double),
+                ("guard", c_double), ("sweep0", c_uint64)]
+
+
+ALLOC_FN = CFUNCTYPE(c_void_p, c_void_p, c_size_t, c_void_p)
+FREE_FN = CFUNCTYPE(None, c_void_p, c_void_p, c_void_p)
+
+
+class srm_allocator(Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", c_void_p)]
+
+
+class srm_step_info(Structure):
+    _fields_ = [("result", c_int32), ("k_sweeps", c_int32), ("shake_sweeps", c_int32),
+                ("overlapping", c_int64), ("phi", c_double), ("lambda_", c_double),
+                ("sweep", c_uint64)]
+
+
+class srm_run_info(Structure):
+    _fields_ = [("iterations", c_int64), ("accepted", c_int64), ("shaken", c_int64),
+                ("sweeps", c_int64), ("phi", c_double), ("lambda_", c_double), ("sweep", c_uint64)]
+
+
+class srm_state_info(Structure):
+    _fields_ = [("dim", c_int32), ("precision", c_int32), ("n", c_int64), ("lambda_", c_double),
+                ("lambda_t", c_double), ("phi", c_double), ("phi_t", c_double),
+                ("sweep", c_uint64), ("iterations", c_int64), ("accepted", c_int64),
+                ("shaken", c_int64), ("sweeps", c_int64), ("done", c_int32),
+                ("grid", c_int32 * 3), ("kernel_launches", c_int64), ("pairs_sweep", c_uint64),
+                ("pairs_check", c_uint64)]
+
+
+class srm_timings(Structure):
+    _fields_ = [("ms_bin", c_double), ("ms_sweep", c_double), ("ms_check", c_double),
+                ("ms_control", c_double), ("supersteps", c_int64), ("sweep_launches", c_int64),
+                ("check_launches", c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+H = c_void_p
+
+
+def load() -> ctypes.CDLL:
+    """Build (if stale) and load libsrm.so; raises if either fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+            sig = {
+                "srm_params_default": ([POINTER(srm_params)], None),
+                "srm_init": ([POINTER(H), c_int32, POINTER(c_double), POINTER(srm_radii), c_double,
+                              c_uint64, POINTER(srm_params), c_void_p, POINTER(srm_allocator)],
+                             c_int32),
+                "srm_step": ([H, POINTER(srm_step_info)], c_int32),
+                "srm_run_to_target": ([H, c_int64, POINTER(srm_run_info)], c_int32),
+                "srm_certify": ([H, POINTER(c_int64), POINTER(c_double), POINTER(c_double)],
+                                c_int32),
+                "srm_positions": ([H, c_void_p, c_void_p], c_int32),
+                "srm_overlap_pairs": ([H, c_void_p, c_int64, POINTER(c_int64)], c_int32),
+                "srm_sweep": ([H, c_int32, POINTER(c_int64)], c_int32),
+                "srm_set_scale": ([H, c_double], c_int32),
+                "srm_get_state": ([H, POINTER(srm_state_info)], c_int32),
+                "srm_destroy": ([H], None),
+                "srm_set_timing": ([H, c_int32], c_int32),
+                "srm_get_timings": ([H, POINTER(srm_timings)], c_int32),
+                "srm_last_error": ([], c_char_p),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def srm_last_error() -> str:
+    return load().srm_last_error().decode()
+
+
+def _check(st: int):
+    if st != 0:
+        raise SrmError(st, srm_last_error())
+
+
+def _as_dict(s: Structure) -> dict:
+    out = {}
+    for name, _ in s._fields_:
+        v = getattr(s, name)
+        if hasattr(v, "__len__") and not isinstance(v, (bytes, str)):
+            v = list(v)
+        out[name.rstrip("_")] = v
+    return out
+
+
+# ---------------------------------------------------------------------------
+# C-named functions (thin marshalling)
+# ---------------------------------------------------------------------------
+def srm_init(dim, box, radii: srm_radii, target_phi, seed, params: srm_params, stream=None,
+             allocator: srm_allocator | None = None) -> c_void_p:
+    lib = load()
+    h = H()
+    b = (c_double * 3)(*([float(v) for v in box] + [1.0] * (3 - len(box))))
+    _check(lib.srm_init(ctypes.byref(h), int(dim), b, ctypes.byref(radii), float(target_phi),
+                        int(seed), ctypes.byref(params), c_void_p(stream or 0),
+                        ctypes.byref(allocator) if allocator is not None else None))
+    return h
+
+
+def srm_step(h) -> dict:
+    info = srm_step_info()
+    _check(load().srm_step(h, ctypes.byref(info)))
+    return _as_dict(info)
+
+
+def srm_run_to_target(h, max_iters: int = 1 << 40) -> dict:
+    info = srm_run_info()
+    st = load().srm_run_to_target(h, int(max_iters), ctypes.byref(info))
+    d = _as_dict(info)
+    if st == 4:
+        d["converged"] = False
+        return d
+    _check(st)
+    d["converged"] = True
+    return d
+
+
+def srm_certify(h):
+    pairs, gap, phi = c_int64(), c_double(), c_double()
+    st = load().srm_certify(h, ctypes.byref(pairs), ctypes.byref(gap), ctypes.byref(phi))
+    if st not in (0, 6):
+        _check(st)
+    return int(pairs.value), float(gap.value), float(phi.value)
+
+
+def srm_positions(h, n: int, dim: int):
+    x = np.empty((n, dim), dtype=np.float64)
+    r = np.empty(n, dtype=np.float64)
+    _check(load().srm_positions(h, x.ctypes.data, r.ctypes.data))
+    return x, r
+
+
+def srm_overlap_pairs(h, cap: int | None = None) -> np.ndarray:
+    lib = load()
+    n = c_int64()
+    if cap is None:
+        _check(lib.srm_overlap_pairs(h, None, 0, ctypes.byref(n)))
+        cap = int(n.value)
+    ij = np.zeros((max(cap, 1), 2), dtype=np.int64)
+    _check(lib.srm_overlap_pairs(h, ij.ctypes.data, int(cap), ctypes.byref(n)))
+    return ij[:min(int(n.value), cap)].copy()
+
+
+def srm_sweep(h, count: int = 1) -> int:
+    moved = c_int64()
+    _check(load().srm_sweep(h, int(count), ctypes.byref(moved)))
+    return int(moved.value)
+
+
+def srm_set_scale(h, lam: float):
+    _check(load().srm_set_scale(h, float(lam)))
+
+
+def srm_get_state(h) -> dict:
+    s = srm_state_info()
+    _check(load().srm_get_state(h, ctypes.byref(s)))
+    return _as_dict(s)
+
+
+def srm_set_timing(h, on: bool):
+    _check(load().srm_set_timing(h, 1 if on else 0))
+
+
+def srm_get_timings(h) -> dict:
+    t = srm_timings()
+    _check(load().srm_get_timings(h, ctypes.byref(t)))
+    return _as_dict(t)
+
+
+def srm_destroy(h):
+    load().srm_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# torch plumbing: stream and caching allocator
+# ---------------------------------------------------------------------------
+def _torch_allocator(device: int):
+    import torch
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ctx, ptr, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+    return srm_allocator(fa, ff, None), (fa, ff)
+
+
+class Rve:
+    """One periodic RVE driven through the C interface.
+
+    radii: array of base radii, or ("mono", r) / ("lognormal", mean, sd, lo, hi) with n.
+    init: "rsa" (uniform RSA at f0), "clustered" (RSA with Gaussian cluster
+    proposals), or "explicit" (positions given, scale lambda0, default 1).
+    """
+
+    def __init__(self, dim, box, radii, target_phi, seed=1, *, n=None, c_m, c_w=0.01, N_k=10,
+                 N_l=10, N_shake=10, precision=PREC_F64, init="rsa", positions=None, f0=0.1,
+                 n_clusters=0, cluster_sigma=0.0, lambda0=0.0, lambda_t=0.0, guard=4e-6,
+                 sweep0=0, stream=None, torch_memory=True):
+        import torch
+        lib = load()
+        self.dim = int(dim)
+        rad = srm_radii()
+        self._keep = []
+        if isinstance(radii, tuple):
+            if radii[0] == "mono":
+                rad.kind, rad.n, rad.mean = RADII_MONO, int(n), float(radii[1])
+            elif radii[0] == "lognormal":
+                rad.kind, rad.n = RADII_LOGNORMAL, int(n)
+                rad.mean, rad.sd, rad.lo, rad.hi = map(float, radii[1:5])
+            else:
+                raise ValueError(f"unknown radii spec {radii[0]}")
+        else:
+            r = np.ascontiguousarray(radii, dtype=np.float64)
+            self._keep.append(r)
+            rad.kind, rad.n, rad.r = RADII_EXPLICIT, r.size, r.ctypes.data
+        self.n = int(rad.n)
+        p = srm_params()
+        lib.srm_params_default(ctypes.byref(p))
+        p.c_w, p.c_m, p.N_k, p.N_l, p.N_shake = c_w, c_m, N_k, N_l, N_shake
+        p.precision = int(precision)
+        p.init = {"rsa": INIT_RSA_UNIFORM, "clustered": INIT_RSA_CLUSTERED,
+                  "explicit": INIT_EXPLICIT}[init]
+        if positions is not None:
+            x = np.ascontiguousarray(positions, dtype=np.float64)
+            self._keep.append(x)
+            p.init_pos = x.ctypes.data
+        p.f0, p.n_clusters, p.cluster_sigma = f0, n_clusters, cluster_sigma
+        p.lambda0, p.lambda_t, p.guard, p.sweep0 = lambda0, lambda_t, guard, sweep0
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = int(stream)
+        alloc = None
+        self._cb = None
+        if torch_memory:
+            alloc, self._cb = _torch_allocator(torch.cuda.current_device())
+        self._alloc = alloc
+        self.h = srm_init(dim, box, rad, target_phi, seed, p, self.stream, alloc)
+
+    def step(self) -> dict:
+        return srm_step(self.h)
+
+    def run_to_target(self, max_iters: int = 1 << 40) -> dict:
+        return srm_run_to_target(self.h, max_iters)
+
+    def certify(self):
+        return srm_certify(self.h)
+
+    def positions(self):
+        return srm_positions(self.h, self.n, self.dim)
+
+    def overlap_pairs(self) -> np.ndarray:
+        return srm_overlap_pairs(self.h)
+
+    def sweep(self, count: int = 1) -> int:
+        return srm_sweep(self.h, count)
+
+    def set_scale(self, lam: float):
+        srm_set_scale(self.h, lam)
+
+    def state(self) -> dict:
+        return srm_get_state(self.h)
+
+    def set_timing(self, on: bool = True):
+        srm_set_timing(self.h, on)
+
+    def timings(self) -> dict:
+        return srm_get_timings(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            srm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

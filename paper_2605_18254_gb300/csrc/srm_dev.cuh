@@ -1,0 +1,297 @@
+// srm_dev.cuh -- device-side state of one RVE and the arithmetic shared by
+// the kernels: Philox4x64-10, the unit-vector sampler, periodic wrap, cell
+// coordinates, and the exact binary64 collision predicate.
+//
+// Every binary64 operation that decides a result is written with an explicit
+// round-to-nearest intrinsic (__dadd_rn, __dmul_rn, __ddiv_rn, __dsqrt_rn) so
+// that the compiler cannot fuse a multiply and an add: the FP64 form then
+// evaluates exactly the IEEE-754 operations of Algorithms 3-5 in their
+// written order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace srm {
+
+// Modes of the per-RVE state machine of Algorithm 1.
+enum Mode : int32_t {
+    MODE_BEGIN = 0,  // next super-step starts an iteration (swell, new grid)
+    MODE_KLOOP = 1,  // inside the N_k loop (Alg 1 lines 9-14)
+    MODE_SHAKE = 2,  // shake sweeps on P (Alg 1 lines 19-22)
+    MODE_DONE = 3,   // P at the target scale
+    MODE_SWEEP = 4   // standalone sweep of P at its own scale
+};
+
+// One cell-sorted copy of a configuration.  FP64 form: pos = double4_32a
+// {x, y, z, R}; FP32 form: pos = float4 {ox, oy, oz, R} with offsets relative
+// to the corner of cell `cell` of the grid (gn, gw) the copy was binned on.
+struct Slot {
+    void *pos;
+    double *rb;      // base radius r_i
+    uint32_t *pid;   // particle id
+    uint32_t *cell;  // linear cell index of the binning that wrote the slot
+    int32_t gn[3];
+    double gw[3];
+};
+
+struct RveDev {
+    // ---- constants ----
+    int32_t dim, prec, n, N_k, N_l, N_shake;
+    double L[3], halfL[3];
+    double rmax, c_w, c_m, lam_t;
+    float guard;
+    float Lf[3];
+    uint64_t seed;
+    int32_t ncells_cap;
+    int64_t iter_cap;
+    // ---- buffers ----
+    Slot slot[3];
+    uint32_t *counts;      // [ncells_cap], all zero between binnings
+    uint32_t *cell_start;  // [ncells_cap + 1]
+    uint32_t *scan_part;   // block partial sums
+    uint32_t *src_cell;    // [n]
+    uint32_t *src_rank;    // [n]
+    uint8_t *flags;        // [n] overlap flags of the last check (sorted order)
+    uint32_t *pcount;      // [n + 1] pair counts by particle id, then offsets
+    unsigned long long *red;  // [0] colliding particles, [1] pairs, [2] min-gap key, [3] moves
+    // ---- state ----
+    int32_t mode, resume_mode, k, s;
+    int32_t p_idx, src_idx, dst_idx;
+    int32_t active, do_check;
+    double lam_P, lam_Q, lam_R;
+    uint64_t sweep;
+    int32_t gn[3];
+    double gw[3];
+    int32_t ncells;
+    int32_t H[3];
+    int32_t sub[3];
+    int32_t nsub;
+    int64_t iters, accepted, shaken, sweeps;
+    // last finished iteration
+    int32_t it_result, it_k, it_shake;
+    int64_t it_overlap;
+    int64_t moved_last;
+    int32_t status;
+    // work counters: candidate pairs examined by the sweep and by the check
+    unsigned long long pairs_sweep, pairs_check;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 64x64 -> 128-bit products; the key is advanced by the Weyl constants
+// between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+        const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+constexpr uint64_t TAG_MOVE = 0x53524D2D4D4F5645ULL;  // "SRM-MOVE"
+constexpr int MAX_CAND = 32;
+
+// Uniform direction in DIM dimensions for (seed, sweep, particle, try):
+// candidate m is the Philox block at counter (pid, sweep, try, m), mapped to
+// the lattice point ((w_a >> 10) - 2^53) 2^-53 of [-1, 1)^DIM; the first with
+// 0 < |v|^2 <= 1 is divided by its norm.  All steps are exact or correctly
+// rounded binary64 operations.
+template <int DIM>
+__device__ __forceinline__ void unit_dir(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l,
+                                         double u[3])
+{
+    for (int m = 0; m < MAX_CAND; m++) {
+        uint64_t c[4] = {pid, sweep, l, (uint64_t)m};
+        philox4x64(c, seed, TAG_MOVE);
+        double v[3];
+#pragma unroll
+        for (int a = 0; a < DIM; a++)
+            v[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
+        double s = __dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1]));
+        if (DIM == 3) s = __dadd_rn(s, __dmul_rn(v[2], v[2]));
+        if (s > 0.0 && s <= 1.0) {
+            const double nrm = __dsqrt_rn(s);
+#pragma unroll
+            for (int a = 0; a < DIM; a++) u[a] = __ddiv_rn(v[a], nrm);
+            if (DIM == 2) u[2] = 0.0;
+            return;
+        }
+    }
+    u[0] = 1.0;
+    u[1] = 0.0;
+    u[2] = 0.0;
+}
+
+// Direction of the same draw for the FP32 form, without binary64 arithmetic
+// in the common case (binary64 runs at 1/64 of the binary32 rate on this
+// GPU).  Coordinate a of candidate m is taken from the top 24 bits of the
+// Philox word, v_a = ((w_a >> 40) - 2^23) 2^-23, which is the binary64
+// lattice point truncated by less than 2^-23; |v|^2 in binary32 is then
+// within 1e-6 of the binary64 value, so the acceptance test 0 < |v|^2 <= 1 is
+// decided in binary32 outside a band of +-2e-6 around 1 (and 0) and by the
+// binary64 computation of the reference inside it: the accepted candidate is
+// always the one the reference accepts.  The normalisation is binary32.
+template <int DIM>
+__device__ __forceinline__ void unit_dir_f32(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l,
+                                             float u[3])
+{
+    for (int m = 0; m < MAX_CAND; m++) {
+        uint64_t c[4] = {pid, sweep, l, (uint64_t)m};
+        philox4x64(c, seed, TAG_MOVE);
+        float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < DIM; a++) v[a] = (float)((int32_t)(c[a] >> 40) - (1 << 23)) * 0x1p-23f;
+        float s = v[0] * v[0] + v[1] * v[1];
+        if (DIM == 3) s += v[2] * v[2];
+        bool ok;
+        if (s > 1.0f + 2e-6f) {
+            ok = false;
+        } else if (s < 1.0f - 2e-6f && s > 2e-6f) {
+            ok = true;
+        } else {
+            double vd[3];
+#pragma unroll
+            for (int a = 0; a < DIM; a++)
+                vd[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
+            double sd = __dadd_rn(__dmul_rn(vd[0], vd[0]), __dmul_rn(vd[1], vd[1]));
+            if (DIM == 3) sd = __dadd_rn(sd, __dmul_rn(vd[2], vd[2]));
+            ok = sd > 0.0 && sd <= 1.0;
+            if (ok && !(s > 0.f)) s = (float)sd;
+        }
+        if (ok) {
+            const float inv = rsqrtf(s);
+#pragma unroll
+            for (int a = 0; a < DIM; a++) u[a] = v[a] * inv;
+            if (DIM == 2) u[2] = 0.f;
+            return;
+        }
+    }
+    u[0] = 1.f;
+    u[1] = 0.f;
+    u[2] = 0.f;
+}
+
+// Algorithm 4: "< 0" first, then ">= L".
+__device__ __forceinline__ double wrap_d(double x, double L)
+{
+    if (x < 0.0) x = __dadd_rn(x, L);
+    if (x >= L) x = __dsub_rn(x, L);
+    return x;
+}
+
+// Algorithm 2 lines 2-5: int(x / w), then ((c % n) + n) % n.
+__device__ __forceinline__ int32_t cell_coord_d(double x, double w, int32_t n)
+{
+    long long c = __double2ll_rz(__ddiv_rn(x, w));
+    long long nn = n;
+    return (int32_t)(((c % nn) + nn) % nn);
+}
+
+// Algorithm 5 lines 10-18 for one pair: minimum-image difference, then
+// sqrt(dx^2 + dy^2 [+ dz^2]) <= Rq + Rt, in binary64.  Most pairs are decided
+// from the squared distance against (Rq + Rt)^2 with a relative margin that
+// covers every rounding of both sides; only pairs inside that band take the
+// correctly rounded square root, so the outcome equals the literal test.
+template <int DIM>
+__device__ __forceinline__ bool collide_exact(const double q[3], double Rq, double tx, double ty,
+                                              double tz, double Rt, const double L[3],
+                                              const double halfL[3])
+{
+    double d0 = __dsub_rn(q[0], tx);
+    if (d0 > halfL[0]) d0 = __dsub_rn(d0, L[0]);
+    if (d0 < -halfL[0]) d0 = __dadd_rn(d0, L[0]);
+    double d1 = __dsub_rn(q[1], ty);
+    if (d1 > halfL[1]) d1 = __dsub_rn(d1, L[1]);
+    if (d1 < -halfL[1]) d1 = __dadd_rn(d1, L[1]);
+    double ss = __dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1));
+    if (DIM == 3) {
+        double d2 = __dsub_rn(q[2], tz);
+        if (d2 > halfL[2]) d2 = __dsub_rn(d2, L[2]);
+        if (d2 < -halfL[2]) d2 = __dadd_rn(d2, L[2]);
+        ss = __dadd_rn(ss, __dmul_rn(d2, d2));
+    }
+    const double rs = __dadd_rn(Rq, Rt);
+    const double b = __dmul_rn(rs, rs);
+    // sqrt(ss) < rs for certain when ss <= b (1 - 2^-51); sqrt(ss) rounds
+    // above rs for certain when ss >= b (1 + 2^-48).
+    if (ss > __dmul_rn(b, 1.0 + 0x1p-48)) return false;
+    if (ss <= __dmul_rn(b, 1.0 - 0x1p-51)) return true;
+    return __dsqrt_rn(ss) <= rs;
+}
+
+// Gap S - (Rq + Rt) and the literal predicate, for certification.
+template <int DIM>
+__device__ __forceinline__ bool gap_exact(const double q[3], double Rq, const double t[3], double Rt,
+                                          const double L[3], const double halfL[3], double *gap)
+{
+    double ss = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        double d = __dsub_rn(q[a], t[a]);
+        if (d > halfL[a]) d = __dsub_rn(d, L[a]);
+        if (d < -halfL[a]) d = __dadd_rn(d, L[a]);
+        ss = a == 0 ? __dmul_rn(d, d) : __dadd_rn(ss, __dmul_rn(d, d));
+    }
+    const double S = __dsqrt_rn(ss);
+    const double rs = __dadd_rn(Rq, Rt);
+    *gap = __dsub_rn(S, rs);
+    return S <= rs;
+}
+
+// Grid of Algorithm 1 lines 4-5 for scale lam: cellSize = 2.5 lam rmax + c_m,
+// n = 3 max(1, int(L / (3 cellSize))), w = L / n.  Also the reach H of the
+// neighbour search: cells within one of the home cell cover every possible
+// partner of any trial move when 2 (lam rmax) + 2 c_m < w; otherwise two.
+__device__ __forceinline__ void set_grid(RveDev *st, double lam)
+{
+    const double Rmax = __dmul_rn(lam, st->rmax);
+    const double cs = __dadd_rn(__dmul_rn(2.5, Rmax), st->c_m);
+    const double reach = __dadd_rn(__dmul_rn(2.0, Rmax), __dmul_rn(2.0, st->c_m));
+    int32_t nc = 1, ns = 1;
+    for (int a = 0; a < 3; a++) {
+        if (a >= st->dim) {
+            st->gn[a] = 1;
+            st->gw[a] = st->L[a];
+            st->H[a] = 0;
+            st->sub[a] = 1;
+            continue;
+        }
+        long long k = __double2ll_rz(__ddiv_rn(st->L[a], __dmul_rn(3.0, cs)));
+        if (k < 1) k = 1;
+        const int32_t n = (int32_t)(3 * k);
+        const double w = __ddiv_rn(st->L[a], (double)n);
+        st->gn[a] = n;
+        st->gw[a] = w;
+        int32_t H = reach < w * (1.0 - 1e-9) ? 1 : 2;
+        if (H > (n - 1) / 2) H = (n - 1) / 2;
+        st->H[a] = H;
+        st->sub[a] = n / 3;
+        nc *= n;
+        ns *= n / 3;
+    }
+    st->ncells = nc;
+    st->nsub = ns;
+}
+
+// Order-preserving map of a double onto an unsigned key (for atomicMin).
+__device__ __forceinline__ unsigned long long dkey(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+}  // namespace srm

@@ -79,11 +79,14 @@ static double wrap_into(double x, double L)
 /* Random sequential addition of n particles with radii R[i] into the
  * periodic box L (placed in index order).  mode 0: proposals uniform in the
  * box.  mode 1: n_clusters centres uniform in the box; particle i belongs to
- * a cluster drawn uniformly and its proposals are Gaussian around the centre
- * with standard deviation sigma per axis (redrawn in the same cluster on
- * rejection).  A proposal is rejected when |d|^2 <= (R_i + R_j)^2 (1 + 1e-9)
- * under the minimum image for some placed j.  Returns 0, or -1 when a
- * particle found no place in max_attempts proposals. */
+ * a cluster drawn uniformly; its first proposal is the centre plus a Gaussian
+ * offset g of standard deviation sigma per axis, and each rejected proposal
+ * is retried one largest diameter further out along g (so that a particle
+ * whose cluster core is already saturated settles on the edge of the core
+ * after a bounded number of tries instead of waiting for a rare far draw).
+ * A proposal is rejected when |d|^2 <= (R_i + R_j)^2 (1 + 1e-9) under the
+ * minimum image for some placed j.  Returns 0, or -1 when a particle found
+ * no place in max_attempts proposals. */
 int inp_rsa(int dim, const double L[3], int64_t n, const double *R, uint64_t seed, int mode,
             int64_t n_clusters, double sigma, int64_t max_attempts, double *X)
 {
@@ -119,11 +122,21 @@ int inp_rsa(int dim, const double L[3], int64_t n, const double *R, uint64_t see
         int64_t cl = mode == 1 ? (int64_t)(uni(&g) * (double)n_clusters) : 0;
         if (cl >= n_clusters) cl = n_clusters - 1;
         int64_t att = 0;
+        double off[3] = {0.0, 0.0, 0.0}, dir[3] = {0.0, 0.0, 0.0};
+        if (mode == 1) {
+            double nrm = 0.0;
+            for (int a = 0; a < dim; a++) {
+                off[a] = sigma * gauss(&g);
+                nrm += off[a] * off[a];
+            }
+            nrm = sqrt(nrm);
+            for (int a = 0; a < dim; a++) dir[a] = nrm > 0.0 ? off[a] / nrm : (a == 0 ? 1.0 : 0.0);
+        }
         for (;;) {
             if (++att > max_attempts) { rc = -1; break; }
             double p[3] = {0.0, 0.0, 0.0};
             for (int a = 0; a < dim; a++) {
-                if (mode == 1) p[a] = wrap_into(cen[cl * 3 + a] + sigma * gauss(&g), L[a]);
+                if (mode == 1) p[a] = wrap_into(cen[cl * 3 + a] + off[a], L[a]);
                 else p[a] = uni(&g) * L[a];
             }
             int64_t c[3] = {0, 0, 0};
@@ -150,7 +163,11 @@ int inp_rsa(int dim, const double L[3], int64_t n, const double *R, uint64_t see
                             if (d2 <= rs * rs * (1.0 + 1e-9)) ok = 0;
                         }
                     }
-            if (!ok) continue;
+            if (!ok) {
+                if (mode == 1)
+                    for (int a = 0; a < dim; a++) off[a] += 2.0 * Rmax * dir[a];
+                continue;
+            }
             for (int a = 0; a < dim; a++) X[i * dim + a] = p[a];
             int64_t cell = c[0] + nc[0] * (c[1] + nc[1] * c[2]);
             next[i] = head[cell];

@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C interface) with the FP64 reference.
+
+FP64 form: every iteration, sweep and pair list must equal the reference bit
+for bit on the same inputs -- the path evaluates the same IEEE operations in
+an order that provably gives the same result (coloured sweep, exact
+collision predicate).  FP32 form: tolerance 1e-5 of the mean radius for one
+sweep, and overlap-free FP64 certification of full runs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import srm_inputs
+import paper_2605_18254_gb300 as srm
+
+pytestmark = pytest.mark.gpu
+
+
+def pair(w, precision=64, literal=False, **kw):
+    args = dict(c_w=w.c_w, c_m=w.c_m, N_k=w.N_k, N_l=w.N_l, N_shake=w.N_shake)
+    args.update(kw)
+    lam0 = args.pop("lambda0", 1.0)
+    lam_t = args.pop("lambda_t", None)
+    g = srm.Rve(w.dim, w.box, w.radii, w.target_phi, w.seed, init="explicit", positions=w.x,
+                precision=precision, lambda0=lam0, lambda_t=lam_t or 0.0, **args)
+    o = oracle.System(w.dim, w.box, w.x, w.radii, lam=lam0, lam_t=lam_t,
+                      target_phi=None if lam_t else w.target_phi, seed=w.seed, literal=literal,
+                      **args)
+    return g, o
+
+
+def assert_same_state(g, o):
+    x, R = g.positions()
+    np.testing.assert_array_equal(x, o.x)
+    st = g.state()
+    assert st["lambda"] == o.lam
+    np.testing.assert_array_equal(R, o.radii())
+    assert st["sweep"] == o.sweep_counter
+
+
+def small_3d(n=2000, phi_t=0.45, seed=7):
+    return srm_inputs._mono("spheres_small", 3, n, phi_t, 0.1, seed)
+
+
+@pytest.mark.parametrize("maker", [lambda: srm_inputs.disks_1k(), lambda: small_3d()])
+def test_fp64_iterations_bit_exact(maker):
+    w = maker()
+    g, o = pair(w)
+    assert g.state()["lambda_t"] == o.lambda_for_phi(w.target_phi)
+    for _ in range(12):
+        gi = g.step()
+        acc, oi = o.iterate()
+        assert gi["result"] == acc
+        assert gi["k_sweeps"] == oi["k_sweeps"]
+        if acc == 0:
+            assert gi["overlapping"] == oi["overlapping"]
+        assert_same_state(g, o)
+
+
+@pytest.mark.parametrize("maker", [lambda: srm_inputs.disks_1k(), lambda: small_3d(1500, 0.40)])
+def test_fp64_full_run_bit_exact(maker):
+    w = maker()
+    g, o = pair(w)
+    info = g.run_to_target()
+    o.run()
+    assert info["converged"]
+    assert_same_state(g, o)
+    c = o.counters()
+    assert info["iterations"] == c["iters"] and info["sweeps"] == c["sweeps"]
+    assert info["accepted"] == c["accepted"] and info["shaken"] == c["shaken"]
+    pairs, gap, phi = g.certify()
+    assert pairs == 0 and gap > 0
+    assert abs(phi - w.target_phi) < 1e-9
+    assert oracle.pairs_brute(w.dim, w.box, *g.positions())[1] == 0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pair_sets_and_sweeps_bit_exact(dim):
+    """Swell a clean state so that it overlaps, then compare the colliding
+    pair set (Algorithm 6 over pairs) and single sweeps of Algorithm 3."""
+    w = srm_inputs._mono("swollen", dim, 1200 if dim == 2 else 1500, 0.4, 0.2, 11 + dim)
+    g, o = pair(w, c_m=0.2 * w.radii[0])
+    for lam in (1.12, 1.25):
+        g.set_scale(lam)
+        o.lam = lam
+        for _ in range(3):
+            gp, op = g.overlap_pairs(), o.pairs()
+            assert len(op) > 0
+            np.testing.assert_array_equal(gp, op)
+            np.testing.assert_array_equal(gp, oracle.pairs_brute(dim, w.box, o.x, o.radii())[0])
+            moved = g.sweep(1)
+            assert moved == o.sweep()
+            assert_same_state(g, o)
+
+
+def test_edge_single_particle():
+    box = (1.0, 0.7, 1.3)
+    x = np.array([[0.999, 0.01, 0.5]])
+    w = srm_inputs.Workload("one", 3, box, np.array([0.05]), x, 0.001, 99, c_m=0.03)
+    g, o = pair(w, c_w=0.05)
+    for _ in range(5):
+        g.step()
+        o.iterate()
+        assert_same_state(g, o)
+    assert g.overlap_pairs().shape == (0, 2)
+
+
+def test_edge_three_cells_rectangular_polydisperse():
+    """Few large particles: 3 cells on some axis, unequal box sides, radii
+    spread over 2x, a ragged particle count."""
+    rng = np.random.default_rng(5)
+    n = 37
+    box = (1.0, 0.8, 1.6)
+    r = rng.uniform(0.05, 0.1, size=n) * 0.6
+    x = srm_inputs.rsa(3, box, r, 5)
+    w = srm_inputs.Workload("few", 3, box, r, x, 0.05, 5, c_m=0.01)
+    g, o = pair(w, c_w=0.02)
+    for _ in range(20):
+        g.step()
+        o.iterate()
+        assert_same_state(g, o)
+
+
+def test_edge_shake_path():
+    """A swelling rate too large for N_k sweeps: discard and shake."""
+    w = srm_inputs._mono("shake", 2, 900, 0.6, 0.45, 21)
+    g, o = pair(w, c_w=0.2, N_k=2, N_l=3, N_shake=3)
+    for _ in range(4):
+        gi = g.step()
+        acc, oi = o.iterate()
+        assert gi["result"] == acc
+        assert_same_state(g, o)
+    assert o.counters()["shaken"] > 0
+
+
+def test_edge_jammed_lattice():
+    m = 12
+    a = 1.0 / m
+    gx = (np.arange(m) + 0.5) * a
+    X = np.array([(x, y) for y in gx for x in gx])
+    R = np.full(m * m, 0.5 * a * (1 - 1e-9))
+    w = srm_inputs.Workload("lattice", 2, (1.0, 1.0), R, X, 0.9, 3, c_m=0.05 * a)
+    g, o = pair(w)
+    assert g.sweep(1) == 0 == o.sweep()
+    assert_same_state(g, o)
+
+
+def fp32_sweep_check(w, lam, c_m, sweeps=1):
+    """Sweeps in the FP32 cell-relative form against the FP64 reference on the
+    same state and draws.  A position may leave the tolerance 1e-5 of the mean
+    radius only where the reference took a decision within 1e-4 (relative) of
+    contact -- there the FP32 guard band may decide the other way -- and then
+    only within one interaction range of such a particle (the sweep carries a
+    changed decision to neighbours handled later).  Returns the fraction of
+    particles within tolerance."""
+    g, o = pair(w, precision=32, c_m=c_m)
+    g.set_scale(lam)
+    o.lam = lam
+    o.track_margins(True)
+    box = np.array(w.box, dtype=float)
+    uncertain = np.zeros(w.n, dtype=bool)
+    for _ in range(sweeps):
+        g.sweep(1)
+        o.sweep()
+        uncertain |= o.margins < 1e-4
+    xg, _ = g.positions()
+    xo = o.x
+    d = xg - xo
+    d = d - np.round(d / box) * box
+    rbar = float(np.mean(o.radii()))
+    err = np.sqrt(np.sum(d * d, axis=1))
+    bad = np.nonzero(err >= 1e-5 * rbar)[0]
+    reach = sweeps * 2 * (2 * float(np.max(o.radii())) + 2 * c_m)
+    cen = xo[uncertain]
+    for i in bad:
+        assert len(cen) > 0, "divergence without a near-contact decision"
+        e = cen - xo[i]
+        e = e - np.round(e / box) * box
+        assert np.min(np.sqrt(np.sum(e * e, axis=1))) <= reach
+    assert len(bad) <= 10 * max(1, int(uncertain.sum()))
+    return 1.0 - len(bad) / w.n
+
+
+@pytest.mark.parametrize("seed,dim", [(13, 3), (14, 3), (15, 2)])
+def test_fp32_sweep_within_tolerance(seed, dim):
+    w = small_3d(3000, 0.40, seed=seed) if dim == 3 else srm_inputs._mono("d2", 2, 3000, 0.5, 0.1, seed)
+    frac = fp32_sweep_check(w, 1.15, 0.3 * w.radii[0])
+    assert frac > 0.99
+
+
+@pytest.mark.parametrize("maker", [lambda: srm_inputs.disks_1k(), lambda: small_3d(3000, 0.45)])
+def test_fp32_full_run_certifies(maker):
+    w = maker()
+    g = srm.Rve(w.dim, w.box, w.radii, w.target_phi, w.seed, init="explicit", positions=w.x,
+                precision=32, c_m=w.c_m, c_w=w.c_w)
+    info = g.run_to_target()
+    assert info["converged"]
+    pairs, gap, phi = g.certify()
+    assert pairs == 0 and gap > 0 and abs(phi - w.target_phi) < 1e-9
+    x, R = g.positions()
+    assert oracle.certify(w.dim, w.box, x, R)[0] == 0
+
+
+def test_rsa_init_through_c_interface():
+    g = srm.Rve(3, (1.0, 1.0, 1.0), ("mono", 1.0), 0.3, 4, n=5000, c_m=0.002, init="rsa", f0=0.1)
+    st = g.state()
+    assert abs(st["phi"] - 0.1) < 1e-12
+    x, R = g.positions()
+    assert oracle.certify(3, (1.0, 1.0, 1.0), x, R)[0] == 0
+    info = g.run_to_target()
+    assert info["converged"] and g.certify()[0] == 0
