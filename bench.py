@@ -356,13 +356,13 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poly_1m")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--max-iters", type=int, default=1 << 40)
-    ap.add_argument("--timing-iters", type=int, default=30)
+    ap.add_argument("--timing-iters", type=int, default=20)
     ap.add_argument("--compare-fp64", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -183,6 +183,8 @@ typedef struct srm_state_info {
     int64_t kernel_launches;    /* kernels this handle has launched since creation   */
     uint64_t pairs_sweep;       /* candidate pairs tested by the sweeps (Alg 3/5)    */
     uint64_t pairs_check;       /* candidate pairs tested by the checks (Alg 6)      */
+    uint64_t stage_overflow;    /* sweep cells whose candidates exceeded the staging */
+    int32_t stage_capacity;     /* candidates a sweep warp stages in shared memory   */
 } srm_state_info;
 
 srm_status srm_get_state(srm_rve *h, srm_state_info *out);

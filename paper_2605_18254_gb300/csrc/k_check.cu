@@ -24,96 +24,73 @@ __device__ __forceinline__ void decode_cell(uint32_t c, const int32_t gn[3], int
 __device__ __forceinline__ int wrapi(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
 // ---------------------------------------------------------------------------
-// Algorithm 6 with a full count: one warp per cell stages the stencil's
-// particles in shared memory, then for each particle of the cell the lanes
-// test interleaved slices of the candidates and vote; the flag of every
-// particle (sorted order) and the number of colliding particles result.
+// Algorithm 6 with a full count, after a sweep (one thread per particle,
+// walking the cells within H of its home cell).  Every particle moves at most
+// once per sweep and a move is accepted only if the new position collides
+// with no particle at that moment; every other particle is then either at
+// its final position already or will itself move only to a position that
+// collides with nothing.  Hence a pair in which at least one particle moved
+// cannot collide at the end of the sweep, and the colliding particles of
+// Algorithm 6 are exactly the non-moved particles that collide with another
+// non-moved particle (the same predicate is evaluated on the same values, so
+// the count equals the full check's).  Moved particles return at once, and
+// the others test non-moved candidates only.
 // ---------------------------------------------------------------------------
 template <int DIM, bool F32>
-__global__ void __launch_bounds__(SW_WARPS * 32) k_check(RveDev *st, int cap)
+__global__ void __launch_bounds__(256) k_check(RveDev *st)
 {
-    extern __shared__ __align__(32) unsigned char smem[];
+    using PT = typename std::conditional<F32, float4, double4_32a>::type;
     if (!st->active || !st->do_check) return;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int cell = blockIdx.x * SW_WARPS + wib;
-    int count = 0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int hit = 0;
     unsigned examined = 0;
-    if (cell < st->ncells) {
+    if (i < st->n && !st->flags[i]) {
+        const Slot d = st->slot[st->dst_idx];
+        const PT *pos = reinterpret_cast<const PT *>(d.pos);
         const uint32_t *cs = st->cell_start;
-        const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
-        if (nh > 0) {
-            using PT = typename std::conditional<F32, float4, double4_32a>::type;
-            unsigned char *base = smem + (size_t)wib * warp_smem_bytes<PT>(cap);
-            StencilSmem &S = *reinterpret_cast<StencilSmem *>(base);
-            PT *cpos = reinterpret_cast<PT *>(base + ST_HDR);
-            uint32_t *cidx = reinterpret_cast<uint32_t *>(cpos + cap);
-            const Slot d = st->slot[st->dst_idx];
-            const PT *pos = reinterpret_cast<const PT *>(d.pos);
-            int hx, hy, hz;
-            decode_cell((uint32_t)cell, st->gn, hx, hy, hz);
-            int nst, center;
-            const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
-            const float w0 = (float)st->gw[0], w1 = (float)st->gw[1], w2 = (float)st->gw[2];
-            const bool staged = T <= (uint32_t)cap;
-            auto fetch = [&](uint32_t k, uint32_t &g) -> PT {
-                const int j = find_cell(S, nst, k);
-                g = S.b[j] + (k - S.o[j]);
-                PT c = pos[g];
-                if (F32) {
-                    c.x += (float)S.sh[j][0] * w0;
-                    c.y += (float)S.sh[j][1] * w1;
-                    c.z += (float)S.sh[j][2] * w2;
-                }
-                return c;
-            };
-            if (staged) {
-                for (uint32_t k = lane; k < T; k += 32) {
-                    uint32_t g;
-                    cpos[k] = fetch(k, g);
-                    cidx[k] = g;
-                }
-                __syncwarp();
-            }
-            const float g1 = 1.0f + st->guard;
-            for (uint32_t m = 0; m < nh; m++) {
-                const uint32_t gi = hb + m;
-                const PT p = pos[gi];
-                bool hit = false;
-                for (uint32_t k = lane; k < T && !hit; k += 32) {
-                    uint32_t g;
-                    PT c;
-                    if (staged) {
-                        c = cpos[k];
-                        g = cidx[k];
-                    } else {
-                        c = fetch(k, g);
-                    }
-                    if (g == gi) continue;
-                    examined++;
-                    if (F32) {
-                        const float ex = (float)p.x - (float)c.x, ey = (float)p.y - (float)c.y;
-                        float d2 = ex * ex + ey * ey;
-                        if (DIM == 3) {
-                            const float ez = (float)p.z - (float)c.z;
-                            d2 += ez * ez;
+        int hx, hy, hz;
+        decode_cell(d.cell[i], st->gn, hx, hy, hz);
+        const int n0 = st->gn[0], n1 = st->gn[1], n2 = st->gn[2];
+        const int H0 = st->H[0], H1 = st->H[1], H2 = st->H[2];
+        const float w0 = (float)st->gw[0], w1 = (float)st->gw[1], w2 = (float)st->gw[2];
+        const float g1 = 1.0f + st->guard;
+        const PT p = pos[i];
+        for (int dz = -H2; dz <= H2 && !hit; dz++)
+            for (int dy = -H1; dy <= H1 && !hit; dy++) {
+                const int row = n0 * (wrapi(hy + dy, n1) + n1 * wrapi(hz + dz, n2));
+                for (int dx = -H0; dx <= H0 && !hit; dx++) {
+                    const int c = row + wrapi(hx + dx, n0);
+                    for (uint32_t j = cs[c]; j < cs[c + 1]; j++) {
+                        if ((int)j == i || st->flags[j]) continue;
+                        examined++;
+                        const PT t = pos[j];
+                        bool h;
+                        if constexpr (F32) {
+                            const float ex = p.x - (t.x + (float)dx * w0);
+                            const float ey = p.y - (t.y + (float)dy * w1);
+                            float d2 = ex * ex + ey * ey;
+                            if (DIM == 3) {
+                                const float ez = p.z - (t.z + (float)dz * w2);
+                                d2 += ez * ez;
+                            }
+                            const float rs = p.w + t.w;
+                            h = d2 <= rs * rs * g1;
+                        } else {
+                            const double q[3] = {p.x, p.y, p.z};
+                            h = collide_exact<DIM>(q, p.w, t.x, t.y, t.z, t.w, st->L, st->halfL);
                         }
-                        const float rs = (float)p.w + (float)c.w;
-                        hit = d2 <= rs * rs * g1;
-                    } else {
-                        const double q[3] = {(double)p.x, (double)p.y, (double)p.z};
-                        hit = collide_exact<DIM>(q, (double)p.w, (double)c.x, (double)c.y, (double)c.z,
-                                                 (double)c.w, st->L, st->halfL);
+                        if (h) {
+                            hit = 1;
+                            break;
+                        }
                     }
                 }
-                const bool any = __any_sync(0xffffffffu, hit);
-                if (lane == 0) st->flags[gi] = (uint8_t)any;
-                count += any;
             }
-        }
     }
-    if (lane == 0 && count) atomicAdd(&st->red[0], (unsigned long long)count);
+    const int tot = __reduce_add_sync(0xffffffffu, hit);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&st->red[0], (unsigned long long)tot);
     examined = __reduce_add_sync(0xffffffffu, examined);
-    if (lane == 0 && examined) atomicAdd(&st->pairs_check, (unsigned long long)examined);
+    if ((threadIdx.x & 31) == 0 && examined) atomicAdd(&st->pairs_check, (unsigned long long)examined);
 }
 
 // ---------------------------------------------------------------------------
@@ -269,36 +246,21 @@ __global__ void __launch_bounds__(256) k_gather(RveDev *st, double *xyz, double 
 // ---------------------------------------------------------------------------
 static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-int check_cap_max(bool f32) { return f32 ? 1024 : 512; }
-
-static size_t check_smem(bool f32, int cap)
-{
-    return SW_WARPS * (f32 ? warp_smem_bytes<float4>(cap) : warp_smem_bytes<double4_32a>(cap));
-}
+int check_cap_max(bool f32) { return f32 ? 512 : 256; }
 
 void launch_check(RveDev *d_st, const HostShape &sh, cudaStream_t s)
 {
-    const int nb = blocks_for(sh.ncells_cap, SW_WARPS);
-    const int cap = sh.cap_check;
-    const size_t smem = check_smem(sh.f32, cap);
+    const int nb = blocks_for(sh.n, 256);
     if (sh.dim == 2) {
-        if (sh.f32) k_check<2, true><<<nb, SW_WARPS * 32, smem, s>>>(d_st, cap);
-        else k_check<2, false><<<nb, SW_WARPS * 32, smem, s>>>(d_st, cap);
+        if (sh.f32) k_check<2, true><<<nb, 256, 0, s>>>(d_st);
+        else k_check<2, false><<<nb, 256, 0, s>>>(d_st);
     } else {
-        if (sh.f32) k_check<3, true><<<nb, SW_WARPS * 32, smem, s>>>(d_st, cap);
-        else k_check<3, false><<<nb, SW_WARPS * 32, smem, s>>>(d_st, cap);
+        if (sh.f32) k_check<3, true><<<nb, 256, 0, s>>>(d_st);
+        else k_check<3, false><<<nb, 256, 0, s>>>(d_st);
     }
 }
 
-void check_configure()
-{
-    const int s32 = (int)check_smem(true, check_cap_max(true));
-    const int s64 = (int)check_smem(false, check_cap_max(false));
-    cudaFuncSetAttribute(k_check<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-    cudaFuncSetAttribute(k_check<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-    cudaFuncSetAttribute(k_check<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-    cudaFuncSetAttribute(k_check<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-}
+void check_configure() {}
 
 void launch_inspect_bin(RveDev *d_st, const HostShape &sh, cudaStream_t s)
 {

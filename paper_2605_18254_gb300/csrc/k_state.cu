@@ -45,6 +45,7 @@ __global__ void k_begin(RveDev *st)
     st->active = 1;
     st->red[0] = 0;
     st->red[3] = 0;
+    for (int c = 0; c < 27; c++) st->wq[c] = 0;
 }
 
 __global__ void k_control(RveDev *st)

@@ -3,18 +3,34 @@
 //
 // Cells are coloured by (c_x mod 3, c_y mod 3[, c_z mod 3]); the sweep runs
 // the 3^d colours in ascending order, one launch per colour.  Within a
-// colour every cell is handled by one thread, which moves the particles of
-// its cell one after the other in ascending id.  Two cells of one colour are
-// at least three cells apart along some axis, while a particle reads only
-// cells within H <= 2 of its home cell, so the cells of one colour never read
-// each other's particles: the parallel sweep equals the serial sweep in
-// colour -> cell -> id order, for any scheduling of the threads.
+// colour every cell is handled by one warp, which moves the particles of its
+// cell one after the other in ascending id.  Two cells of one colour are at
+// least three cells apart along some axis, while a particle reads only cells
+// within H <= 2 of its home cell, so the cells of one colour never read each
+// other's particles: the parallel sweep equals the serial sweep in
+// colour -> cell -> id order, whatever the scheduling.
 //
-// A trial move (Algorithm 3 lines 4-10) is q = wrap(q_old + c_m u) with u
-// the Philox-drawn direction; the collision test (Algorithm 5) scans the
-// cells within H of the home cell, which contain every particle that can
-// touch any trial position (cells are at least 2.5 R_max + c_m wide and the
-// lists are at most one move stale).
+// A trial move (Algorithm 3 lines 4-10) is q = wrap(q_old + c_m u) with u the
+// Philox-drawn direction; the collision test (Algorithm 5) covers the cells
+// within H of the home cell, which contain every particle that can touch any
+// trial position (cells are at least 2.5 R_max + c_m wide and the lists are
+// at most one move stale).
+//
+// Per cell, one warp:
+//  1. lists the stencil cells (home cell first) and stages in shared memory
+//     the candidates that can reach the home cell: distance to the home
+//     cell box <= R_home,max + R_t + 2 c_m (a conservative bound: trials stay
+//     within c_m of positions that stay within c_m of the box).  FP32 form:
+//     positions relative to the home cell corner; FP64 form: absolute
+//     binary64 positions plus binary32 copies relative to the corner;
+//  2. for each particle of the cell, in ascending id: builds its near list,
+//     the candidates within R_i + R_t + c_m of it (superset of everything a
+//     trial can touch), as copies in shared memory; lane l draws trial l of a
+//     batch; for each trial the lanes test the near list and vote;
+//  3. an accepted move updates the staged copy (later particles of the cell
+//     see it) and the slot in global memory, and marks the particle moved.
+// If the culled candidates exceed the staging capacity, the near lists are
+// built straight from global memory (same arithmetic, slower).
 #include "srm_dev.cuh"
 #include "srm_launch.h"
 #include "srm_stencil.cuh"
@@ -23,95 +39,99 @@
 
 namespace srm {
 
-// ---------------------------------------------------------------------------
-// Warp-per-cell sweep.  One warp owns one cell of the current colour:
-//  1. the (2H+1)^d stencil cells around the home cell are listed (begin,
-//     count, offset) and their particles staged in shared memory -- for the
-//     FP32 form as positions relative to the home cell corner (the stencil
-//     shift s*w is added once here), for the FP64 form as absolute binary64
-//     positions;
-//  2. the particles of the home cell are moved one after the other in
-//     ascending id (Algorithm 3); lane l draws the direction of trial l in
-//     parallel, and for each trial the 32 lanes test interleaved slices of
-//     the staged candidates and vote with __any_sync (Algorithm 5);
-//  3. an accepted move updates the staged copy (later particles of the cell
-//     see it) and the slot in global memory.
-// Candidate lists longer than the staging capacity are read from global
-// memory instead (same arithmetic).
-// ---------------------------------------------------------------------------
-// ---- one kernel for both forms -----------------------------------------------
-// Per-warp shared memory: stencil list | staged positions | (FP64 form: FP32
-// copies relative to the home corner, for culling) | staged indices | near list.
-constexpr int NEAR_CAP = 192;
+constexpr int NEAR_CAP = 128;
+constexpr int PRE_NH = 64;    // home particles whose first trials are drawn up front
+constexpr int PRE_TRIALS = 2; // trials drawn up front per particle
 
 template <bool F32>
 struct SweepSmem {
     using PT = typename std::conditional<F32, float4, double4_32a>::type;
+    using DT = typename std::conditional<F32, float, double>::type;
     static __host__ __device__ constexpr size_t bytes(int cap)
     {
         return (ST_HDR + (size_t)cap * sizeof(PT) + (F32 ? 0 : (size_t)cap * sizeof(float4)) +
-                (size_t)cap * 4 + (size_t)NEAR_CAP * 2 + 31) / 32 * 32;
+                (size_t)NEAR_CAP * sizeof(PT) + (size_t)PRE_NH * PRE_TRIALS * 3 * sizeof(DT) + 31) /
+               32 * 32;
     }
 };
 
-// Cull test on FP32 positions relative to the home corner: t can touch a
-// trial position of p (within c_m of p) only if |p - t| <= R_p + R_t + c_m;
-// the relative slack 1e-4 covers the FP32 rounding of both positions, so the
-// near list is a superset of every partner the exact test can find.
-__device__ __forceinline__ bool near_f32(const float4 &p, const float4 &t, float cm, int dim)
+// |p - t|^2 against r^2 with relative slack 4e-4 (covers the binary32
+// rounding of relative positions of magnitude up to a few cells).
+__device__ __forceinline__ bool within_f32(const float4 &p, const float4 &t, float r, int dim)
 {
     const float ex = p.x - t.x, ey = p.y - t.y, ez = dim == 3 ? p.z - t.z : 0.f;
-    const float d2 = ex * ex + ey * ey + ez * ez;
-    const float r = p.w + t.w + cm;
-    return d2 <= r * r * 1.0002f;
+    return ex * ex + ey * ey + ez * ez <= r * r * 1.0004f;
+}
+
+// Squared distance from a point (relative to the home corner) to the home box.
+__device__ __forceinline__ float box_dist2(const float4 &t, const float w[3], int dim)
+{
+    const float ex = fmaxf(fmaxf(-t.x, t.x - w[0]), 0.f);
+    const float ey = fmaxf(fmaxf(-t.y, t.y - w[1]), 0.f);
+    const float ez = dim == 3 ? fmaxf(fmaxf(-t.z, t.z - w[2]), 0.f) : 0.f;
+    return ex * ex + ey * ey + ez * ez;
 }
 
 template <int DIM, bool F32>
 __global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(RveDev *st, int chi, int cap)
 {
     using PT = typename SweepSmem<F32>::PT;
+    using DT = typename SweepSmem<F32>::DT;
     extern __shared__ __align__(32) unsigned char smem[];
     if (!st->active) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int t = blockIdx.x * SW_WARPS + wib;  // cell of this colour
+    unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
+    StencilSmem &S = *reinterpret_cast<StencilSmem *>(base);
+    PT *cpos = reinterpret_cast<PT *>(base + ST_HDR);
+    float4 *capx = reinterpret_cast<float4 *>(cpos + cap);  // FP64 form only
+    PT *nbuf = reinterpret_cast<PT *>(F32 ? (void *)(cpos + cap) : (void *)(capx + cap));
+    DT *pre = reinterpret_cast<DT *>(nbuf + NEAR_CAP);      // [PRE_NH][PRE_TRIALS][3]
+
+    const Slot d = st->slot[st->dst_idx];
+    PT *pos = reinterpret_cast<PT *>(d.pos);
+    const uint32_t *cs = st->cell_start;
+    const int s0 = st->sub[0], s1 = st->sub[1], nsub = st->nsub;
+    const float w[3] = {(float)st->gw[0], (float)st->gw[1], (float)st->gw[2]};
+    const uint64_t seed = st->seed, sweep = st->sweep;
+    const double c_m = st->c_m;
+    const float cmf = (float)c_m;
+    const float g1 = 1.0f + st->guard;
+    const int N_l = st->N_l;
     int moved = 0;
-    unsigned long long examined = 0;
-    if (t < st->nsub) {
-        unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
-        StencilSmem &S = *reinterpret_cast<StencilSmem *>(base);
-        PT *cpos = reinterpret_cast<PT *>(base + ST_HDR);
-        float4 *capx = reinterpret_cast<float4 *>(cpos + cap);  // FP64 form only
-        uint32_t *cidx = reinterpret_cast<uint32_t *>(F32 ? (void *)(cpos + cap) : (void *)(capx + cap));
-        uint16_t *near = reinterpret_cast<uint16_t *>(cidx + cap);
-        const int s0 = st->sub[0], s1 = st->sub[1];
+    unsigned examined = 0;
+
+    // cells of this colour are handed out one at a time to whichever warp
+    // is free (dense cells take far longer than sparse ones)
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&st->wq[chi], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nsub) break;
         const int hx = 3 * (t % s0) + chi % 3;
         const int hy = 3 * ((t / s0) % s1) + (chi / 3) % 3;
         const int hz = DIM == 3 ? 3 * (t / (s0 * s1)) + chi / 9 : 0;
-        const uint32_t *cs = st->cell_start;
         const int cell = hx + st->gn[0] * (hy + st->gn[1] * hz);
         const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
-        if (nh > 0) {
-            const Slot d = st->slot[st->dst_idx];
-            PT *pos = reinterpret_cast<PT *>(d.pos);
-            int nst, center;
-            const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
-            const float w0 = (float)st->gw[0], w1 = (float)st->gw[1], w2 = (float)st->gw[2];
-            // home corner (FP64 form: absolute; used for the FP32 culling copies)
-            const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
-            const bool staged = T <= (uint32_t)cap;
-            auto fetch = [&](uint32_t k, uint32_t &g) -> PT {
-                const int j = find_cell(S, nst, k);
-                g = S.b[j] + (k - S.o[j]);
-                PT c = pos[g];
-                if (F32) {
-                    c.x += (float)S.sh[j][0] * w0;
-                    c.y += (float)S.sh[j][1] * w1;
-                    c.z += (float)S.sh[j][2] * w2;
-                }
+        if (nh == 0) continue;
+        int nst, center;
+        const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
+        // home corner (FP64 form: the binary32 copies are relative to it)
+        const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
+        auto fetch = [&](uint32_t k, uint32_t &g) -> PT {
+            const int j = find_cell(S, nst, k);
+            g = S.b[j] + (k - S.o[j]);
+            PT c = pos[g];
+            if constexpr (F32) {
+                c.x += (float)S.sh[j][0] * w[0];
+                c.y += (float)S.sh[j][1] * w[1];
+                c.z += (float)S.sh[j][2] * w[2];
+            }
+            return c;
+        };
+        auto approx = [&](const PT &c) -> float4 {
+            if constexpr (F32) {
                 return c;
-            };
-            // FP32 copy relative to the home corner (FP64 form), via the minimum image
-            auto approx = [&](const double4_32a &c) -> float4 {
+            } else {
                 double ex = c.x - ox, ey = c.y - oy, ez = DIM == 3 ? c.z - oz : 0.0;
                 if (ex > st->halfL[0]) ex -= st->L[0];
                 if (ex < -st->halfL[0]) ex += st->L[0];
@@ -122,174 +142,244 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(RveDev *st, int chi, in
                     if (ez < -st->halfL[2]) ez += st->L[2];
                 }
                 return make_float4((float)ex, (float)ey, (float)ez, (float)c.w);
-            };
-            if (staged) {
-                for (uint32_t k = lane; k < T; k += 32) {
-                    uint32_t g;
-                    const PT c = fetch(k, g);
-                    cpos[k] = c;
-                    if constexpr (!F32) capx[k] = approx(c);
-                    cidx[k] = g;
-                }
-                __syncwarp();
             }
-            const uint64_t seed = st->seed, sweep = st->sweep;
-            const double c_m = st->c_m;
-            const float cmf = (float)c_m;
-            const float g1 = 1.0f + st->guard;
-            const int N_l = st->N_l;
-            const uint32_t ko = S.o[center];
-            for (uint32_t m = 0; m < nh; m++) {
-                const uint32_t gi = hb + m;
-                const uint32_t kself = ko + m;
-                const PT p = staged ? cpos[kself] : pos[gi];
-                const uint64_t pid = d.pid[gi];
-                // ---- near list of this particle (staged case)
-                uint32_t nn = 0;
-                bool use_near = false;
-                if (staged) {
-                    float4 pa;
-                    if constexpr (F32) pa = p;
-                    else pa = capx[kself];
-                    for (uint32_t k0 = 0; k0 < T; k0 += 32) {
-                        const uint32_t k = k0 + lane;
-                        bool nb = false;
-                        if (k < T && k != kself) {
-                            float4 ca;
-                            if constexpr (F32) ca = cpos[k];
-                            else ca = capx[k];
-                            nb = near_f32(pa, ca, cmf, DIM);
-                        }
-                        const unsigned bal = __ballot_sync(0xffffffffu, nb);
-                        const uint32_t at = nn + __popc(bal & ((1u << lane) - 1u));
-                        if (nb && at < NEAR_CAP) near[at] = (uint16_t)k;
-                        nn += __popc(bal);
-                    }
-                    use_near = nn <= NEAR_CAP;
-                    __syncwarp();
-                }
-                const uint32_t L = use_near ? nn : T;
-                bool done = false;
-                // trials are drawn in batches, one per lane: 2 first (most
-                // particles take the first trial), then 8 at a time
-                for (int l0 = 0; l0 < N_l && !done;) {
-                    const int bsz = l0 == 0 ? 2 : 8;
-                    const int lmax = N_l - l0 < bsz ? N_l - l0 : bsz;
-                    double qt[3] = {0.0, 0.0, 0.0};
-                    float qs[3] = {0.f, 0.f, 0.f};
-                    if constexpr (F32) {
-                        qs[0] = p.x;
-                        qs[1] = p.y;
-                        qs[2] = p.z;
+        };
+        // largest radius among the particles of the home cell
+        float rh = 0.f;
+        for (uint32_t m = lane; m < nh; m += 32) rh = fmaxf(rh, (float)pos[hb + m].w);
+        for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
+        // 1. stage the candidates that can reach the home cell (home first)
+        // Staging stops at the first 32-candidate chunk that would overflow
+        // the capacity; candidates from kstop on are read from global memory
+        // (culled the same way) when the near lists are built.
+        uint32_t Tk = 0, kstop = T;
+        for (uint32_t k0 = 0; k0 < T; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            bool keep = false;
+            PT c;
+            float4 ca;
+            if (k < T) {
+                uint32_t g;
+                c = fetch(k, g);
+                ca = approx(c);
+                const float r = rh + ca.w + 2.f * cmf;
+                keep = k < nh || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (Tk + __popc(bal) > (uint32_t)cap) {
+                kstop = k0;
+                break;
+            }
+            const uint32_t at = Tk + __popc(bal & ((1u << lane) - 1u));
+            if (keep) {
+                cpos[at] = c;
+                if constexpr (!F32) capx[at] = ca;
+            }
+            Tk += __popc(bal);
+        }
+        const bool staged = kstop == T;
+        if (!staged && lane == 0) atomicAdd(&st->stage_overflow, 1ull);
+        // the first trial directions of every home particle, drawn in
+        // parallel (they depend on the particle id and the counters only)
+        const uint32_t npre = nh < (uint32_t)PRE_NH ? nh : (uint32_t)PRE_NH;
+        for (uint32_t e = lane; e < npre * PRE_TRIALS; e += 32) {
+            const uint32_t m = e / PRE_TRIALS, l = e % PRE_TRIALS;
+            const uint64_t pid = d.pid[hb + m];
+            DT *u = pre + 3 * e;
+            if constexpr (F32) {
+                float v[3];
+                unit_dir_f32<DIM>(seed, sweep, pid, l, v);
+                u[0] = v[0];
+                u[1] = v[1];
+                u[2] = v[2];
+            } else {
+                double v[3];
+                unit_dir<DIM>(seed, sweep, pid, l, v);
+                u[0] = v[0];
+                u[1] = v[1];
+                u[2] = v[2];
+            }
+        }
+        __syncwarp();
+
+        // 2. the particles of the home cell, ascending id
+        for (uint32_t m = 0; m < nh; m++) {
+            const uint32_t gi = hb + m;
+            // home particles lead the candidate list and are always kept, so
+            // the first ones are staged at their own index
+            const PT p = m < Tk ? cpos[m] : pos[gi];
+            const float4 pa = approx(p);
+            const uint64_t pid = d.pid[gi];
+            // near list: copies of every candidate within R_i + R_t + c_m
+            // (staged candidates, then the unstaged remainder from global)
+            uint32_t nn = 0;
+            const uint32_t scan = Tk + (T - kstop);
+            for (uint32_t k0 = 0; k0 < scan; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                bool nb = false;
+                PT c;
+                if (k < scan) {
+                    float4 ca;
+                    bool self;
+                    if (k < Tk) {
+                        self = k == m;
+                        c = cpos[k];
+                        if constexpr (F32) ca = c;
+                        else ca = capx[k];
                     } else {
-                        qt[0] = p.x;
-                        qt[1] = p.y;
-                        qt[2] = p.z;
+                        uint32_t g;
+                        c = fetch(kstop + (k - Tk), g);
+                        self = g == gi;
+                        ca = approx(c);
                     }
-                    if (lane < lmax) {
-                        if constexpr (F32) {
-                            float u[3];
+                    nb = !self && within_f32(pa, ca, pa.w + ca.w + cmf, DIM);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, nb);
+                const uint32_t at = nn + __popc(bal & ((1u << lane) - 1u));
+                if (nb && at < NEAR_CAP) nbuf[at] = c;
+                nn += __popc(bal);
+            }
+            __syncwarp();
+            const bool use_near = nn <= NEAR_CAP;
+            bool done = false;
+            // trials in batches, one per lane: 2 first (most particles take
+            // the first trial), then 8 at a time
+            for (int l0 = 0; l0 < N_l && !done;) {
+                const int bsz = l0 == 0 ? PRE_TRIALS : 8;
+                const int lmax = N_l - l0 < bsz ? N_l - l0 : bsz;
+                double qt[3] = {0.0, 0.0, 0.0};
+                float qs[3] = {0.f, 0.f, 0.f};
+                if (lane < lmax) {
+                    const bool have = l0 == 0 && m < (uint32_t)PRE_NH;
+                    const DT *up = pre + 3 * (m * PRE_TRIALS + lane);
+                    if constexpr (F32) {
+                        float u[3];
+                        if (have) {
+                            u[0] = up[0];
+                            u[1] = up[1];
+                            u[2] = up[2];
+                        } else {
                             unit_dir_f32<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), u);
-                            qs[0] = p.x + cmf * u[0];
-                            qs[1] = p.y + cmf * u[1];
-                            if (DIM == 3) qs[2] = p.z + cmf * u[2];
+                        }
+                        qs[0] = p.x + cmf * u[0];
+                        qs[1] = p.y + cmf * u[1];
+                        qs[2] = DIM == 3 ? p.z + cmf * u[2] : p.z;
+                    } else {
+                        double u[3];
+                        if (have) {
+                            u[0] = up[0];
+                            u[1] = up[1];
+                            u[2] = up[2];
                         } else {
-                            double u[3];
                             unit_dir<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), u);
-                            qt[0] = wrap_d(__dadd_rn((double)p.x, __dmul_rn(c_m, u[0])), st->L[0]);
-                            qt[1] = wrap_d(__dadd_rn((double)p.y, __dmul_rn(c_m, u[1])), st->L[1]);
-                            if (DIM == 3) qt[2] = wrap_d(__dadd_rn((double)p.z, __dmul_rn(c_m, u[2])), st->L[2]);
+                        }
+                        qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, u[0])), st->L[0]);
+                        qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, u[1])), st->L[1]);
+                        qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, u[2])), st->L[2]) : p.z;
+                    }
+                }
+                l0 += lmax;
+                for (int l = 0; l < lmax; l++) {
+                    double q[3] = {0.0, 0.0, 0.0};
+                    float qf[3] = {0.f, 0.f, 0.f};
+                    if constexpr (F32) {
+                        qf[0] = __shfl_sync(0xffffffffu, qs[0], l);
+                        qf[1] = __shfl_sync(0xffffffffu, qs[1], l);
+                        qf[2] = __shfl_sync(0xffffffffu, qs[2], l);
+                    } else {
+                        q[0] = __shfl_sync(0xffffffffu, qt[0], l);
+                        q[1] = __shfl_sync(0xffffffffu, qt[1], l);
+                        q[2] = __shfl_sync(0xffffffffu, qt[2], l);
+                    }
+                    bool hit = false;
+                    const uint32_t L = use_near ? nn : scan;
+                    for (uint32_t kk = lane; kk < L && !hit; kk += 32) {
+                        PT c;
+                        if (use_near) {
+                            c = nbuf[kk];
+                        } else if (kk < Tk) {
+                            if (kk == m) continue;
+                            c = cpos[kk];
+                        } else {
+                            uint32_t g;
+                            c = fetch(kstop + (kk - Tk), g);
+                            if (g == gi) continue;
+                        }
+                        examined++;
+                        if constexpr (F32) {
+                            const float ex = qf[0] - c.x, ey = qf[1] - c.y;
+                            float d2 = ex * ex + ey * ey;
+                            if (DIM == 3) {
+                                const float ez = qf[2] - c.z;
+                                d2 += ez * ez;
+                            }
+                            const float rs = p.w + c.w;
+                            hit = d2 <= rs * rs * g1;
+                        } else {
+                            hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
                         }
                     }
-                    l0 += lmax;
-                    for (int l = 0; l < lmax; l++) {
-                        double q[3] = {0.0, 0.0, 0.0};
-                        float qf[3] = {0.f, 0.f, 0.f};
-                        if constexpr (F32) {
-                            qf[0] = __shfl_sync(0xffffffffu, qs[0], l);
-                            qf[1] = __shfl_sync(0xffffffffu, qs[1], l);
-                            qf[2] = __shfl_sync(0xffffffffu, qs[2], l);
-                        } else {
-                            q[0] = __shfl_sync(0xffffffffu, qt[0], l);
-                            q[1] = __shfl_sync(0xffffffffu, qt[1], l);
-                            q[2] = __shfl_sync(0xffffffffu, qt[2], l);
-                        }
-                        bool hit = false;
-                        for (uint32_t kk = lane; kk < L && !hit; kk += 32) {
-                            PT c;
-                            uint32_t g;
-                            if (use_near) {
-                                const uint32_t k = near[kk];
-                                c = cpos[k];
-                                g = gi + 1;  // never self: the near list excludes it
-                            } else if (staged) {
-                                c = cpos[kk];
-                                g = cidx[kk];
-                            } else {
-                                c = fetch(kk, g);
+                    if (!__any_sync(0xffffffffu, hit)) {
+                        if (lane == 0) {
+                            PT np;
+                            if constexpr (F32) np = make_float4(qf[0], qf[1], qf[2], p.w);
+                            else np = make_double4_32a(q[0], q[1], q[2], p.w);
+                            if (m < Tk) {
+                                cpos[m] = np;
+                                if constexpr (!F32) capx[m] = approx(np);
                             }
-                            if (g == gi) continue;
-                            examined++;
-                            if constexpr (F32) {
-                                const float ex = qf[0] - c.x, ey = qf[1] - c.y;
-                                float d2 = ex * ex + ey * ey;
-                                if (DIM == 3) {
-                                    const float ez = qf[2] - c.z;
-                                    d2 += ez * ez;
-                                }
-                                const float rs = p.w + c.w;
-                                hit = d2 <= rs * rs * g1;
-                            } else {
-                                hit = collide_exact<DIM>(q, (double)p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
-                            }
+                            pos[gi] = np;
                         }
-                        if (!__any_sync(0xffffffffu, hit)) {
-                            if (lane == 0) {
-                                PT np;
-                                if constexpr (F32) {
-                                    np = make_float4(qf[0], qf[1], DIM == 3 ? qf[2] : p.z, p.w);
-                                } else {
-                                    np = make_double4_32a(q[0], q[1], DIM == 3 ? q[2] : p.z, p.w);
-                                }
-                                if (staged) {
-                                    cpos[kself] = np;
-                                    if constexpr (!F32) capx[kself] = approx(np);
-                                }
-                                pos[gi] = np;
-                            }
-                            moved++;
-                            done = true;
-                            __syncwarp();
-                            break;
-                        }
+                        moved++;
+                        done = true;
+                        __syncwarp();
+                        break;
                     }
                 }
             }
+            if (lane == 0) st->flags[gi] = done ? 1 : 0;
+            __syncwarp();
         }
     }
     if (lane == 0 && moved) atomicAdd(&st->red[3], (unsigned long long)moved);
-    examined = __reduce_add_sync(0xffffffffu, (unsigned)examined);
-    if (lane == 0 && examined) atomicAdd(&st->pairs_sweep, examined);
+    examined = __reduce_add_sync(0xffffffffu, examined);
+    if (lane == 0 && examined) atomicAdd(&st->pairs_sweep, (unsigned long long)examined);
 }
 
-int sweep_cap_max(bool f32) { return f32 ? 1024 : 512; }
+int sweep_cap_max(bool f32) { return f32 ? 512 : 256; }
 
 static size_t sweep_smem(bool f32, int cap)
 {
     return SW_WARPS * (f32 ? SweepSmem<true>::bytes(cap) : SweepSmem<false>::bytes(cap));
 }
 
+static int g_sms = 0;
+
+// Blocks that stay resident on one SM at this shared memory size; a launch
+// uses at most that many per SM and the warps loop over the cells.
+template <typename K>
+static int resident_blocks(K kern, size_t smem)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SW_WARPS * 32, smem);
+    return nb > 0 ? nb : 1;
+}
+
 void launch_sweep_colour(RveDev *d_st, const HostShape &sh, int chi, cudaStream_t s)
 {
-    const int nb = (int)((sh.nsub_cap + SW_WARPS - 1) / SW_WARPS);
     const int cap = sh.cap_sweep;
     const size_t smem = sweep_smem(sh.f32, cap);
+    const int want = (int)((sh.nsub_cap + SW_WARPS - 1) / SW_WARPS);
+    auto shape = [&](auto kern) {
+        const int res = resident_blocks(kern, smem) * (g_sms > 0 ? g_sms : 1);
+        return want < res ? want : res;
+    };
     if (sh.f32) {
-        if (sh.dim == 2) k_sweep<2, true><<<nb, SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
-        else k_sweep<3, true><<<nb, SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
+        if (sh.dim == 2) k_sweep<2, true><<<shape(k_sweep<2, true>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
+        else k_sweep<3, true><<<shape(k_sweep<3, true>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
     } else {
-        if (sh.dim == 2) k_sweep<2, false><<<nb, SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
-        else k_sweep<3, false><<<nb, SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
+        if (sh.dim == 2) k_sweep<2, false><<<shape(k_sweep<2, false>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
+        else k_sweep<3, false><<<shape(k_sweep<3, false>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
     }
 }
 
@@ -302,6 +392,11 @@ void launch_sweep(RveDev *d_st, const HostShape &sh, cudaStream_t s)
 // Dynamic shared memory above 48 KB needs an opt-in per kernel.
 void sweep_configure()
 {
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     const int s32 = (int)sweep_smem(true, sweep_cap_max(true));
     const int s64 = (int)sweep_smem(false, sweep_cap_max(false));
     cudaFuncSetAttribute(k_sweep<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);

@@ -10,6 +10,7 @@
 // Every launch reads what changes from the device state, so one captured
 // CUDA graph of a few super-steps is replayed for the whole run and the host
 // only polls the state word every few dozen sweeps.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -432,10 +433,11 @@ srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_r
     h->sh.out_f32 = h->sh.f32;
     h->launches_per_step = kernels_per_superstep(dim);
 
-    // staging capacity of the warp-per-cell kernels: the largest stencil
-    // population of the starting positions on the grid of the target scale
-    // (the coarsest grid of the run), with a quarter of slack; rarer larger
-    // stencils take the unstaged path of the same kernels
+    // Staging capacity of the warp-per-cell sweep: the 95th percentile of
+    // the stencil population of the starting positions on the grid of the
+    // target scale (the coarsest grid of the run), times the part of the
+    // stencil volume within reach of the home cell, with slack.  Denser
+    // cells stage what fits and read the rest from global memory.
     {
         int64_t pa[3];
         const int64_t nc = cells_for(h, s.lam_t, pa);
@@ -451,12 +453,13 @@ srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_r
             }
             occ[(size_t)lin]++;
         }
-        int64_t tmax = 0;
+        std::vector<uint32_t> tpop;
+        tpop.reserve((size_t)n);
         const int zr = dim == 3 ? 1 : 0;
         for (int64_t c = 0; c < nc; c++) {
             if (!occ[(size_t)c]) continue;
             const int64_t cx = c % pa[0], cy = (c / pa[0]) % pa[1], cz = c / (pa[0] * pa[1]);
-            int64_t t = 0;
+            uint32_t t = 0;
             for (int dz = -zr; dz <= zr; dz++)
                 for (int dy = -1; dy <= 1; dy++)
                     for (int dx = -1; dx <= 1; dx++) {
@@ -464,13 +467,25 @@ srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_r
                                       ez = (cz + dz + pa[2]) % pa[2];
                         t += occ[(size_t)(ex + pa[0] * (ey + pa[1] * ez))];
                     }
-            tmax = t > tmax ? t : tmax;
+            for (uint32_t k = 0; k < occ[(size_t)c]; k++) tpop.push_back(t);  // per particle
         }
+        uint32_t t95 = 0;
+        if (!tpop.empty()) {
+            const size_t q = tpop.size() * 95 / 100;
+            std::nth_element(tpop.begin(), tpop.begin() + (ptrdiff_t)q, tpop.end());
+            t95 = tpop[q];
+        }
+        const double wt = s.L[0] / (double)pa[0];
+        const double reach = 2.0 * (2.0 * s.lam_t * rmax + 2.0 * p.c_m);
+        double frac = (wt + reach) / (3.0 * wt);
+        frac = frac > 1.0 ? 1.0 : frac;
+        frac = dim == 3 ? frac * frac * frac : frac * frac;
         const bool f32 = p.precision == SRM_PREC_F32;
-        int64_t cap = (tmax + tmax / 4 + 31) / 32 * 32;
+        int64_t cap = (int64_t)(1.25 * frac * (double)t95) + 16;
+        cap = (cap + 31) / 32 * 32;
         if (cap < 64) cap = 64;
         h->sh.cap_sweep = (int)(cap < srm::sweep_cap_max(f32) ? cap : srm::sweep_cap_max(f32));
-        h->sh.cap_check = (int)(cap < srm::check_cap_max(f32) ? cap : srm::check_cap_max(f32));
+        h->sh.cap_check = h->sh.cap_sweep;
     }
 
     // device buffers
@@ -775,6 +790,8 @@ srm_status srm_get_state(srm_rve *h, srm_state_info *o)
     o->kernel_launches = h->launches;
     o->pairs_sweep = s.pairs_sweep;
     o->pairs_check = s.pairs_check;
+    o->stage_overflow = s.stage_overflow;
+    o->stage_capacity = h->sh.cap_sweep;
     return SRM_OK;
 }
 

@@ -52,7 +52,7 @@ struct RveDev {
     uint32_t *scan_part;   // block partial sums
     uint32_t *src_cell;    // [n]
     uint32_t *src_rank;    // [n]
-    uint8_t *flags;        // [n] overlap flags of the last check (sorted order)
+    uint8_t *flags;        // [n] 1 if the particle moved in the last sweep (sorted order)
     uint32_t *pcount;      // [n + 1] pair counts by particle id, then offsets
     unsigned long long *red;  // [0] colliding particles, [1] pairs, [2] min-gap key, [3] moves
     // ---- state ----
@@ -75,6 +75,8 @@ struct RveDev {
     int32_t status;
     // work counters: candidate pairs examined by the sweep and by the check
     unsigned long long pairs_sweep, pairs_check;
+    unsigned long long stage_overflow;  // cells whose culled stencil exceeded the staging capacity
+    uint32_t wq[27];                    // per-colour work counters of the current sweep
 };
 
 // ---------------------------------------------------------------------------

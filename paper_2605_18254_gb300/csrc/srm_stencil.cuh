@@ -25,7 +25,9 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int cap)
     return (ST_HDR + (size_t)cap * sizeof(PT) + (size_t)cap * 4 + 31) / 32 * 32;
 }
 
-// Lists the stencil cells of home (hx, hy, hz) and returns the candidate count.
+// Lists the stencil cells of home (hx, hy, hz) and returns the candidate
+// count; the home cell is stencil cell 0, so its particles are candidates
+// 0 .. n_home-1.
 __device__ __forceinline__ uint32_t list_stencil(const RveDev *st, const uint32_t *cs, int hx, int hy,
                                                  int hz, StencilSmem &S, int &nst, int &center)
 {
@@ -40,7 +42,10 @@ __device__ __forceinline__ uint32_t list_stencil(const RveDev *st, const uint32_
         const int j = base + lane;
         uint32_t cnt = 0;
         if (j < nst) {
-            const int dx = j % w0 - H0, dy = (j / w0) % w1 - H1, dz = j / (w0 * w1) - H2;
+            // the home cell is listed first: stencil position 0 <-> offset
+            // index `center`, so the home particles lead the candidate list
+            const int jj = j == 0 ? center : (j == center ? 0 : j);
+            const int dx = jj % w0 - H0, dy = (jj / w0) % w1 - H1, dz = jj / (w0 * w1) - H2;
             int cx = hx + dx, cy = hy + dy, cz = hz + dz;
             cx = cx < 0 ? cx + n0 : (cx >= n0 ? cx - n0 : cx);
             cy = cy < 0 ? cy + n1 : (cy >= n1 ? cy - n1 : cy);

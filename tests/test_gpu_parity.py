@@ -131,6 +131,8 @@ def test_edge_shake_path():
         gi = g.step()
         acc, oi = o.iterate()
         assert gi["result"] == acc
+        assert gi["k_sweeps"] == oi["k_sweeps"]
+        assert gi["overlapping"] == oi["overlapping"]
         assert_same_state(g, o)
     assert o.counters()["shaken"] > 0
 
