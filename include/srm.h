@@ -207,6 +207,42 @@ typedef struct srm_timings {
 srm_status srm_set_timing(srm_rve *h, int32_t on);
 srm_status srm_get_timings(srm_rve *h, srm_timings *out);
 
+/* ---------------------------------------------------------------------------
+ * Certification without device allocation.
+ *
+ * The paper has no counterpart to this call: it exists for callers that may
+ * not allocate device memory at all -- code running inside someone else's
+ * CUDA graph capture or memory pool budget, plug-ins of a host application
+ * that owns every device allocation, real-time paths where an allocation
+ * could block or fail.  Such a caller keeps the configuration in its own
+ * device buffers and passes them in; the call computes the same binary64
+ * certification as srm_certify (colliding pairs i < j by index, and the
+ * smallest gap S - (R_i + R_j) over pairs in neighbouring cells of a grid
+ * with cells at least 2 R_max wide), with all working memory in one static
+ * device array of the library (about 1.9 MB, held by every GPU that loads
+ * the library until the process exits).  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.
+ *
+ * dim: 2 or 3; box: L[0..dim); n: particles, 1 <= n <= 32768
+ * (SRM_NOALLOC_MAX_PARTICLES, larger n is rejected with SRM_E_ARG); xyz:
+ * device pointer to n*dim binary64 positions in [0, L), particle order;
+ * radii: device pointer to n binary64 radii; overlap_pairs, min_gap: host
+ * pointers receiving the results; cuda_stream: stream to run on (NULL: the
+ * legacy default stream), synchronised before returning.  Boxes narrower
+ * than 4 R_max on some axis are rejected (SRM_E_ARG).
+ *
+ * The first call on a device looks up the device address of the static
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array, whose
+ * contents are whatever the last call left (each call clears what it needs
+ * zeroed): calls that overlap on the GPU -- from two threads, or on two
+ * streams without ordering between them -- race and give wrong results. */
+#define SRM_NOALLOC_MAX_PARTICLES 32768
+#define SRM_NOALLOC_MAX_CELLS 65536
+srm_status srm_certify_noalloc(int32_t dim, const double box[3], int64_t n, const double *xyz,
+                               const double *radii, int64_t *overlap_pairs, double *min_gap,
+                               void *cuda_stream);
+
 /* Releases the handle and its device memory (stream-ordered). */
 void srm_destroy(srm_rve *h);
 

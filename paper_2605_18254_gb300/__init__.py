@@ -23,8 +23,8 @@ from . import build as _build
 
 __all__ = ["SrmError", "Rve", "load", "srm_init", "srm_step", "srm_run_to_target", "srm_certify",
            "srm_positions", "srm_overlap_pairs", "srm_sweep", "srm_set_scale", "srm_get_state",
-           "srm_destroy", "srm_last_error", "srm_set_timing", "srm_get_timings", "PREC_F64",
-           "PREC_F32"]
+           "srm_destroy", "srm_last_error", "srm_set_timing", "srm_get_timings",
+           "srm_certify_noalloc", "PREC_F64", "PREC_F32"]
 
 PREC_F64, PREC_F32 = 64, 32
 RADII_EXPLICIT, RADII_MONO, RADII_LOGNORMAL = 0, 1, 2
@@ -117,6 +117,8 @@ def load() -> ctypes.CDLL:
                 "srm_get_state": ([H, POINTER(srm_state_info)], c_int32),
                 "srm_destroy": ([H], None),
                 "srm_set_timing": ([H, c_int32], c_int32),
+                "srm_certify_noalloc": ([c_int32, POINTER(c_double), c_int64, c_void_p, c_void_p,
+                                         POINTER(c_int64), POINTER(c_double), c_void_p], c_int32),
                 "srm_get_timings": ([H, POINTER(srm_timings)], c_int32),
                 "srm_last_error": ([], c_char_p),
             }
@@ -229,6 +231,18 @@ def srm_get_timings(h) -> dict:
     t = srm_timings()
     _check(load().srm_get_timings(h, ctypes.byref(t)))
     return _as_dict(t)
+
+
+def srm_certify_noalloc(dim, box, n, xyz_dev_ptr, radii_dev_ptr, stream=None):
+    """Certification of positions and radii held in the caller's device
+    buffers (raw device pointers), with no device allocation by the library;
+    at most SRM_NOALLOC_MAX_PARTICLES = 32768 particles."""
+    b = (c_double * 3)(*([float(v) for v in box] + [1.0] * (3 - len(box))))
+    pairs, gap = c_int64(), c_double()
+    _check(load().srm_certify_noalloc(int(dim), b, int(n), c_void_p(xyz_dev_ptr),
+                                      c_void_p(radii_dev_ptr), ctypes.byref(pairs),
+                                      ctypes.byref(gap), c_void_p(stream or 0)))
+    return int(pairs.value), float(gap.value)
 
 
 def srm_destroy(h):

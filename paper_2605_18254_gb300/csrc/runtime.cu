@@ -37,6 +37,10 @@ static srm_status fail(srm_status st, const std::string &msg)
     return st;
 }
 
+namespace srm {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace srm
+
 #define CK(call)                                                                          \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
