@@ -208,6 +208,77 @@ srm_status srm_set_timing(srm_rve *h, int32_t on);
 srm_status srm_get_timings(srm_rve *h, srm_timings *out);
 
 /* ---------------------------------------------------------------------------
+ * Checkpoints.  The state of an RVE between iterations (accepted positions
+ * exactly as stored, radii, scale, sweep counter, counters, parameters) is
+ * serialised into a caller buffer; a handle loaded from it continues bit for
+ * bit as the saved one would have (the migration draws are counter-based).
+ * srm_save: buf == NULL sets *len to the size needed; otherwise *len is the
+ * buffer size (SRM_E_ARG if too small) and receives the bytes written.
+ * --------------------------------------------------------------------------- */
+srm_status srm_save(srm_rve *h, void *buf, size_t *len);
+srm_status srm_load(srm_rve **out, const void *buf, size_t len, void *cuda_stream,
+                    const srm_allocator *alloc);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent RVEs advanced by the same kernel launches (sizes,
+ * dimensions and targets may differ; one precision per batch).  Each RVE
+ * keeps its own state, grid, buffers and Philox counters, so its result does
+ * not depend on which other RVEs share the batch.
+ * --------------------------------------------------------------------------- */
+typedef struct srm_job {
+    int32_t dim;
+    double box[3];
+    srm_radii radii;
+    double phi_t;
+    uint64_t seed;
+    srm_params params;
+} srm_job;
+
+typedef struct srm_batch srm_batch;
+
+/* A batch holding the given jobs, each loaded into a slot sized for it. */
+srm_status srm_batch_create(srm_batch **out, const srm_job *jobs, int32_t n_jobs, void *cuda_stream,
+                            const srm_allocator *alloc);
+
+/* A batch of n_slots empty slots for continuous serving: each slot takes a
+ * job of at most max_particles particles and max_cells cells on the finest
+ * grid of its run (srm_job_footprint), 2D or 3D.  stage_capacity: candidates
+ * a sweep warp stages in shared memory (0: 256). */
+srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_particles,
+                                  int64_t max_cells, int32_t precision, int32_t stage_capacity,
+                                  void *cuda_stream, const srm_allocator *alloc);
+
+/* Particles and finest-grid cells a job needs (for admission decisions). */
+srm_status srm_job_footprint(const srm_job *job, int64_t *particles, int64_t *cells);
+
+/* Loads a job into a slot that is empty or finished and polled (SRM_E_STATE
+ * if the slot is busy, SRM_E_ARG if the job does not fit). */
+srm_status srm_batch_admit(srm_batch *b, int32_t slot, const srm_job *job);
+
+/* Enqueues `supersteps` super-steps (one sweep each, with binning, check and
+ * control) for every running slot; returns without waiting. */
+srm_status srm_batch_advance(srm_batch *b, int32_t supersteps);
+
+/* Runs every RVE of the batch to its target (at most max_iters iterations
+ * each; SRM_E_NOT_CONVERGED otherwise). */
+srm_status srm_batch_run(srm_batch *b, int64_t max_iters);
+
+/* Slots that reached their target since the last poll, each reported once. */
+srm_status srm_batch_poll(srm_batch *b, int32_t *done_slots, int32_t cap, int32_t *n_done);
+
+/* Marks a finished slot free for the next admission. */
+srm_status srm_batch_release(srm_batch *b, int32_t slot);
+
+int32_t srm_batch_size(const srm_batch *b);
+srm_status srm_batch_state(srm_batch *b, int32_t slot, srm_state_info *out);
+srm_status srm_batch_positions(srm_batch *b, int32_t slot, double *xyz, double *radii);
+srm_status srm_batch_certify(srm_batch *b, int32_t slot, int64_t *overlap_pairs, double *min_gap,
+                             double *phi);
+srm_status srm_batch_set_timing(srm_batch *b, int32_t on);
+srm_status srm_batch_get_timings(srm_batch *b, srm_timings *out);
+void srm_batch_destroy(srm_batch *b);
+
+/* ---------------------------------------------------------------------------
  * Certification without device allocation.
  *
  * The paper has no counterpart to this call: it exists for callers that may

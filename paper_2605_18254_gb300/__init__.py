@@ -24,7 +24,8 @@ from . import build as _build
 __all__ = ["SrmError", "Rve", "load", "srm_init", "srm_step", "srm_run_to_target", "srm_certify",
            "srm_positions", "srm_overlap_pairs", "srm_sweep", "srm_set_scale", "srm_get_state",
            "srm_destroy", "srm_last_error", "srm_set_timing", "srm_get_timings",
-           "srm_certify_noalloc", "PREC_F64", "PREC_F32"]
+           "srm_certify_noalloc", "srm_save", "srm_load", "srm_job_footprint", "make_job", "Batch",
+           "PREC_F64", "PREC_F32"]
 
 PREC_F64, PREC_F32 = 64, 32
 RADII_EXPLICIT, RADII_MONO, RADII_LOGNORMAL = 0, 1, 2
@@ -83,6 +84,11 @@ class srm_state_info(Structure):
                 ("pairs_check", c_uint64), ("stage_overflow", c_uint64), ("stage_capacity", c_int32)]
 
 
+class srm_job(Structure):
+    _fields_ = [("dim", c_int32), ("box", c_double * 3), ("radii", srm_radii), ("phi_t", c_double),
+                ("seed", c_uint64), ("params", srm_params)]
+
+
 class srm_timings(Structure):
     _fields_ = [("ms_bin", c_double), ("ms_sweep", c_double), ("ms_check", c_double),
                 ("ms_control", c_double), ("supersteps", c_int64), ("sweep_launches", c_int64),
@@ -117,6 +123,26 @@ def load() -> ctypes.CDLL:
                 "srm_get_state": ([H, POINTER(srm_state_info)], c_int32),
                 "srm_destroy": ([H], None),
                 "srm_set_timing": ([H, c_int32], c_int32),
+                "srm_save": ([H, c_void_p, POINTER(c_size_t)], c_int32),
+                "srm_load": ([POINTER(H), c_void_p, c_size_t, c_void_p, POINTER(srm_allocator)], c_int32),
+                "srm_batch_create": ([POINTER(H), POINTER(srm_job), c_int32, c_void_p,
+                                      POINTER(srm_allocator)], c_int32),
+                "srm_batch_create_slots": ([POINTER(H), c_int32, c_int64, c_int64, c_int32, c_int32,
+                                            c_void_p, POINTER(srm_allocator)], c_int32),
+                "srm_job_footprint": ([POINTER(srm_job), POINTER(c_int64), POINTER(c_int64)], c_int32),
+                "srm_batch_admit": ([H, c_int32, POINTER(srm_job)], c_int32),
+                "srm_batch_advance": ([H, c_int32], c_int32),
+                "srm_batch_run": ([H, c_int64], c_int32),
+                "srm_batch_poll": ([H, POINTER(c_int32), c_int32, POINTER(c_int32)], c_int32),
+                "srm_batch_release": ([H, c_int32], c_int32),
+                "srm_batch_size": ([H], c_int32),
+                "srm_batch_state": ([H, c_int32, POINTER(srm_state_info)], c_int32),
+                "srm_batch_positions": ([H, c_int32, c_void_p, c_void_p], c_int32),
+                "srm_batch_certify": ([H, c_int32, POINTER(c_int64), POINTER(c_double),
+                                       POINTER(c_double)], c_int32),
+                "srm_batch_set_timing": ([H, c_int32], c_int32),
+                "srm_batch_get_timings": ([H, POINTER(srm_timings)], c_int32),
+                "srm_batch_destroy": ([H], None),
                 "srm_certify_noalloc": ([c_int32, POINTER(c_double), c_int64, c_void_p, c_void_p,
                                          POINTER(c_int64), POINTER(c_double), c_void_p], c_int32),
                 "srm_get_timings": ([H, POINTER(srm_timings)], c_int32),
@@ -350,6 +376,9 @@ class Rve:
     def timings(self) -> dict:
         return srm_get_timings(self.h)
 
+    def save(self) -> bytes:
+        return srm_save(self.h)
+
     def close(self):
         if getattr(self, "h", None):
             srm_destroy(self.h)
@@ -366,3 +395,181 @@ class Rve:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# jobs, batches, serving slots, checkpoints
+# ---------------------------------------------------------------------------
+def make_job(dim, box, radii, target_phi, seed=1, *, n=None, c_m, c_w=0.01, N_k=10, N_l=10,
+             N_shake=10, precision=PREC_F32, init="rsa", positions=None, f0=0.1, n_clusters=0,
+             cluster_sigma=0.0, lambda0=0.0, lambda_t=0.0, guard=4e-6, sweep0=0):
+    """An srm_job; returns (job, keep) where keep holds the arrays it points to."""
+    lib = load()
+    job = srm_job()
+    keep = []
+    job.dim = int(dim)
+    for a in range(3):
+        job.box[a] = float(box[a]) if a < len(box) else 1.0
+    if isinstance(radii, tuple):
+        if radii[0] == "mono":
+            job.radii.kind, job.radii.n, job.radii.mean = RADII_MONO, int(n), float(radii[1])
+        else:
+            job.radii.kind, job.radii.n = RADII_LOGNORMAL, int(n)
+            job.radii.mean, job.radii.sd, job.radii.lo, job.radii.hi = map(float, radii[1:5])
+    else:
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        keep.append(r)
+        job.radii.kind, job.radii.n, job.radii.r = RADII_EXPLICIT, r.size, r.ctypes.data
+    job.phi_t = float(target_phi)
+    job.seed = int(seed)
+    p = job.params
+    lib.srm_params_default(ctypes.byref(p))
+    p.c_w, p.c_m, p.N_k, p.N_l, p.N_shake = c_w, c_m, N_k, N_l, N_shake
+    p.precision = int(precision)
+    p.init = {"rsa": INIT_RSA_UNIFORM, "clustered": INIT_RSA_CLUSTERED, "explicit": INIT_EXPLICIT}[init]
+    if positions is not None:
+        x = np.ascontiguousarray(positions, dtype=np.float64)
+        keep.append(x)
+        p.init_pos = x.ctypes.data
+    p.f0, p.n_clusters, p.cluster_sigma = f0, n_clusters, cluster_sigma
+    p.lambda0, p.lambda_t, p.guard, p.sweep0 = lambda0, lambda_t, guard, sweep0
+    return job, keep
+
+
+def srm_job_footprint(job: srm_job):
+    n, c = c_int64(), c_int64()
+    _check(load().srm_job_footprint(ctypes.byref(job), ctypes.byref(n), ctypes.byref(c)))
+    return int(n.value), int(c.value)
+
+
+class Batch:
+    """Many RVEs advanced by the same launches (srm_batch_*).
+
+    Batch(jobs=[...]) loads the jobs; Batch(slots=k, max_particles=, max_cells=)
+    creates empty slots for continuous serving (admit / advance / poll / release).
+    """
+
+    def __init__(self, jobs=None, *, slots=0, max_particles=0, max_cells=0, precision=PREC_F32,
+                 stage_capacity=0, stream=None, torch_memory=True):
+        import torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = int(stream)
+        alloc, self._cb = (None, None)
+        if torch_memory:
+            alloc, self._cb = _torch_allocator(torch.cuda.current_device())
+        self._alloc = alloc
+        self.h = H()
+        self._meta = {}
+        if jobs is not None:
+            arr = (srm_job * len(jobs))(*[j for j, _ in jobs])
+            self._keep = [k for _, k in jobs]
+            _check(lib.srm_batch_create(ctypes.byref(self.h), arr, len(jobs), c_void_p(self.stream),
+                                        ctypes.byref(alloc) if alloc is not None else None))
+            for i, (j, _) in enumerate(jobs):
+                self._meta[i] = (int(j.dim), int(j.radii.n))
+        else:
+            _check(lib.srm_batch_create_slots(ctypes.byref(self.h), int(slots), int(max_particles),
+                                              int(max_cells), int(precision), int(stage_capacity),
+                                              c_void_p(self.stream),
+                                              ctypes.byref(alloc) if alloc is not None else None))
+
+    def __len__(self):
+        return int(load().srm_batch_size(self.h))
+
+    def admit(self, slot: int, job_keep):
+        job, keep = job_keep
+        _check(load().srm_batch_admit(self.h, int(slot), ctypes.byref(job)))
+        self._meta[int(slot)] = (int(job.dim), int(job.radii.n))
+
+    def advance(self, supersteps: int):
+        _check(load().srm_batch_advance(self.h, int(supersteps)))
+
+    def run(self, max_iters: int = 1 << 40) -> bool:
+        st = load().srm_batch_run(self.h, int(max_iters))
+        if st == 4:
+            return False
+        _check(st)
+        return True
+
+    def poll(self) -> list:
+        cap = max(1, len(self))
+        out = (c_int32 * cap)()
+        n = c_int32()
+        _check(load().srm_batch_poll(self.h, out, cap, ctypes.byref(n)))
+        return [int(out[i]) for i in range(n.value)]
+
+    def release(self, slot: int):
+        _check(load().srm_batch_release(self.h, int(slot)))
+
+    def state(self, slot: int) -> dict:
+        s = srm_state_info()
+        _check(load().srm_batch_state(self.h, int(slot), ctypes.byref(s)))
+        return _as_dict(s)
+
+    def positions(self, slot: int):
+        dim, n = self._meta[int(slot)]
+        x = np.empty((n, dim), dtype=np.float64)
+        r = np.empty(n, dtype=np.float64)
+        _check(load().srm_batch_positions(self.h, int(slot), x.ctypes.data, r.ctypes.data))
+        return x, r
+
+    def certify(self, slot: int):
+        pairs, gap, phi = c_int64(), c_double(), c_double()
+        st = load().srm_batch_certify(self.h, int(slot), ctypes.byref(pairs), ctypes.byref(gap),
+                                      ctypes.byref(phi))
+        if st not in (0, 6):
+            _check(st)
+        return int(pairs.value), float(gap.value), float(phi.value)
+
+    def set_timing(self, on: bool = True):
+        _check(load().srm_batch_set_timing(self.h, 1 if on else 0))
+
+    def timings(self) -> dict:
+        t = srm_timings()
+        _check(load().srm_batch_get_timings(self.h, ctypes.byref(t)))
+        return _as_dict(t)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().srm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def srm_save(h) -> bytes:
+    lib = load()
+    n = c_size_t()
+    _check(lib.srm_save(h, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.srm_save(h, buf, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def srm_load(data: bytes, stream=None, torch_memory=True) -> "Rve":
+    """A new Rve handle continuing from a checkpoint."""
+    import torch
+    lib = load()
+    r = Rve.__new__(Rve)
+    r._keep = []
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    r.stream = int(stream)
+    alloc, r._cb = (None, None)
+    if torch_memory:
+        alloc, r._cb = _torch_allocator(torch.cuda.current_device())
+    r._alloc = alloc
+    buf = ctypes.create_string_buffer(data, len(data))
+    h = H()
+    _check(lib.srm_load(ctypes.byref(h), buf, len(data), c_void_p(r.stream),
+                        ctypes.byref(alloc) if alloc is not None else None))
+    r.h = h
+    st = srm_get_state(h)
+    r.dim, r.n = int(st["dim"]), int(st["n"])
+    return r

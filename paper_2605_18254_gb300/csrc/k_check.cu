@@ -37,14 +37,10 @@ __device__ __forceinline__ int wrapi(int c, int n) { return c < 0 ? c + n : (c >
 // the others test non-moved candidates only.
 // ---------------------------------------------------------------------------
 template <int DIM, bool F32>
-__global__ void __launch_bounds__(256) k_check(RveDev *st)
+__device__ __forceinline__ void check_one(RveDev *st, int i, int &hit, unsigned &examined)
 {
     using PT = typename std::conditional<F32, float4, double4_32a>::type;
-    if (!st->active || !st->do_check) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int hit = 0;
-    unsigned examined = 0;
-    if (i < st->n && !st->flags[i]) {
+    {
         const Slot d = st->slot[st->dst_idx];
         const PT *pos = reinterpret_cast<const PT *>(d.pos);
         const uint32_t *cs = st->cell_start;
@@ -86,6 +82,21 @@ __global__ void __launch_bounds__(256) k_check(RveDev *st)
                     }
                 }
             }
+    }
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_check(BatchDev *bd)
+{
+    const int r = block_rve(bd->blk_p, bd->B);
+    RveDev *st = bd->rv[r];
+    if (!st->active || !st->do_check) return;
+    const int i = (blockIdx.x - bd->blk_p[r]) * blockDim.x + threadIdx.x;
+    int hit = 0;
+    unsigned examined = 0;
+    if (i < st->n && !st->flags[i]) {
+        if (st->dim == 3) check_one<3, F32>(st, i, hit, examined);
+        else check_one<2, F32>(st, i, hit, examined);
     }
     const int tot = __reduce_add_sync(0xffffffffu, hit);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&st->red[0], (unsigned long long)tot);
@@ -248,52 +259,46 @@ static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); 
 
 int check_cap_max(bool f32) { return f32 ? 512 : 256; }
 
-void launch_check(RveDev *d_st, const HostShape &sh, cudaStream_t s)
+void launch_check(const BatchShape &b, cudaStream_t s)
 {
-    const int nb = blocks_for(sh.n, 256);
-    if (sh.dim == 2) {
-        if (sh.f32) k_check<2, true><<<nb, 256, 0, s>>>(d_st);
-        else k_check<2, false><<<nb, 256, 0, s>>>(d_st);
-    } else {
-        if (sh.f32) k_check<3, true><<<nb, 256, 0, s>>>(d_st);
-        else k_check<3, false><<<nb, 256, 0, s>>>(d_st);
-    }
+    if (b.f32) k_check<true><<<b.blocks_p, 256, 0, s>>>(b.d);
+    else k_check<false><<<b.blocks_p, 256, 0, s>>>(b.d);
 }
 
 void check_configure() {}
 
-void launch_inspect_bin(RveDev *d_st, const HostShape &sh, cudaStream_t s)
+// Binning of P into a scratch slot, in binary64, for the inspection of one
+// RVE (its single-member batch).
+void launch_inspect_bin(RveDev *d_st, const BatchShape &solo, cudaStream_t s)
 {
     k_inspect_begin<<<1, 1, 0, s>>>(d_st);
-    HostShape b = sh;
-    b.out_f32 = false;
-    launch_bin(d_st, b, s);
+    launch_bin(solo, solo.f32, false, s);
 }
 
-void launch_pairs_count(RveDev *d_st, const HostShape &sh, int want_gap, cudaStream_t s)
+void launch_pairs_count(RveDev *d_st, int dim, int64_t n, int want_gap, cudaStream_t s)
 {
-    const int nb = blocks_for(sh.n, 256);
-    if (sh.dim == 2) k_pairs_count<2><<<nb, 256, 0, s>>>(d_st, want_gap);
+    const int nb = blocks_for(n, 256);
+    if (dim == 2) k_pairs_count<2><<<nb, 256, 0, s>>>(d_st, want_gap);
     else k_pairs_count<3><<<nb, 256, 0, s>>>(d_st, want_gap);
 }
 
-void launch_pairs_fill(RveDev *d_st, const HostShape &sh, long long *ij, cudaStream_t s)
+void launch_pairs_fill(RveDev *d_st, int dim, int64_t n, long long *ij, cudaStream_t s)
 {
-    const int nb = blocks_for(sh.n, 256);
-    if (sh.dim == 2) k_pairs_fill<2><<<nb, 256, 0, s>>>(d_st, ij);
+    const int nb = blocks_for(n, 256);
+    if (dim == 2) k_pairs_fill<2><<<nb, 256, 0, s>>>(d_st, ij);
     else k_pairs_fill<3><<<nb, 256, 0, s>>>(d_st, ij);
 }
 
 void launch_inspect_end(RveDev *d_st, cudaStream_t s) { k_inspect_end<<<1, 1, 0, s>>>(d_st); }
 
-void launch_gather(RveDev *d_st, const HostShape &sh, double *xyz, double *rad, cudaStream_t s)
+void launch_gather(RveDev *d_st, int dim, bool f32, int64_t n, double *xyz, double *rad, cudaStream_t s)
 {
-    const int nb = blocks_for(sh.n, 256);
-    if (sh.dim == 2) {
-        if (sh.f32) k_gather<2, true><<<nb, 256, 0, s>>>(d_st, xyz, rad);
+    const int nb = blocks_for(n, 256);
+    if (dim == 2) {
+        if (f32) k_gather<2, true><<<nb, 256, 0, s>>>(d_st, xyz, rad);
         else k_gather<2, false><<<nb, 256, 0, s>>>(d_st, xyz, rad);
     } else {
-        if (sh.f32) k_gather<3, true><<<nb, 256, 0, s>>>(d_st, xyz, rad);
+        if (f32) k_gather<3, true><<<nb, 256, 0, s>>>(d_st, xyz, rad);
         else k_gather<3, false><<<nb, 256, 0, s>>>(d_st, xyz, rad);
     }
 }

@@ -8,9 +8,13 @@
 
 namespace srm {
 
-__global__ void k_begin(RveDev *st)
+__global__ void k_begin(BatchDev *bd)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0)
+        for (int c = 0; c < 27; c++) bd->wq[c] = 0u;
+    if (r >= bd->B) return;
+    RveDev *st = bd->rv[r];
     st->active = 0;
     st->do_check = 0;
     const int32_t mode = st->mode;
@@ -45,12 +49,13 @@ __global__ void k_begin(RveDev *st)
     st->active = 1;
     st->red[0] = 0;
     st->red[3] = 0;
-    for (int c = 0; c < 27; c++) st->wq[c] = 0;
 }
 
-__global__ void k_control(RveDev *st)
+__global__ void k_control(BatchDev *bd)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= bd->B) return;
+    RveDev *st = bd->rv[r];
     if (!st->active) return;
     st->sweep++;
     st->sweeps++;
@@ -167,11 +172,8 @@ __device__ __forceinline__ bool same_grid(const RveDev *st, const Slot &s)
 }
 
 template <int DIM, bool F32, bool FAST>
-__global__ void k_bin_count(RveDev *st)
+__device__ __forceinline__ void bin_count_one(RveDev *st, int i)
 {
-    if (!st->active) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= st->n) return;
     const Slot s = st->slot[st->src_idx];
     uint32_t lin = 0;
     if (FAST && same_grid(st, s)) {
@@ -191,12 +193,21 @@ __global__ void k_bin_count(RveDev *st)
     st->src_rank[i] = atomicAdd(&st->counts[lin], 1u);
 }
 
-template <int DIM, bool IN32, bool OUT32>
-__global__ void k_bin_scatter(RveDev *st)
+template <bool F32, bool FAST>
+__global__ void k_bin_count(BatchDev *bd)
 {
+    const int r = block_rve(bd->blk_p, bd->B);
+    RveDev *st = bd->rv[r];
     if (!st->active) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x - bd->blk_p[r]) * blockDim.x + threadIdx.x;
     if (i >= st->n) return;
+    if (st->dim == 3) bin_count_one<3, F32, FAST>(st, i);
+    else bin_count_one<2, F32, FAST>(st, i);
+}
+
+template <int DIM, bool IN32, bool OUT32>
+__device__ __forceinline__ void bin_scatter_one(RveDev *st, int i)
+{
     const Slot s = st->slot[st->src_idx];
     const Slot d = st->slot[st->dst_idx];
     const uint32_t lin = st->src_cell[i];
@@ -231,10 +242,25 @@ __global__ void k_bin_scatter(RveDev *st)
     d.cell[j] = lin;
 }
 
-// The destination slot records the grid its offsets refer to.
-__global__ void k_bin_stamp(RveDev *st)
+template <bool IN32, bool OUT32>
+__global__ void k_bin_scatter(BatchDev *bd)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0 || !st->active) return;
+    const int r = block_rve(bd->blk_p, bd->B);
+    RveDev *st = bd->rv[r];
+    if (!st->active) return;
+    const int i = (blockIdx.x - bd->blk_p[r]) * blockDim.x + threadIdx.x;
+    if (i >= st->n) return;
+    if (st->dim == 3) bin_scatter_one<3, IN32, OUT32>(st, i);
+    else bin_scatter_one<2, IN32, OUT32>(st, i);
+}
+
+// The destination slot records the grid its offsets refer to.
+__global__ void k_bin_stamp(BatchDev *bd)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= bd->B) return;
+    RveDev *st = bd->rv[r];
+    if (!st->active) return;
     Slot &d = st->slot[st->dst_idx];
     for (int a = 0; a < 3; a++) {
         d.gn[a] = st->gn[a];
@@ -243,10 +269,12 @@ __global__ void k_bin_stamp(RveDev *st)
 }
 
 template <bool F32>
-__global__ void k_cell_sort(RveDev *st)
+__global__ void k_cell_sort(BatchDev *bd)
 {
+    const int r = block_rve(bd->blk_c, bd->B);
+    RveDev *st = bd->rv[r];
     if (!st->active) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (blockIdx.x - bd->blk_c[r]) * blockDim.x + threadIdx.x;
     if (c >= st->ncells) return;
     const uint32_t b = st->cell_start[c], e = st->cell_start[c + 1];
     if (e - b < 2) return;
@@ -327,11 +355,17 @@ __device__ __forceinline__ uint32_t *scan_in(const RveDev *st, int which)
     return which == 0 ? st->counts : st->pcount;
 }
 
-__global__ void __launch_bounds__(SCAN_T) k_scan_part(RveDev *st, int which)
+// which == 0: the cell counts of each RVE (only RVEs at work in this
+// super-step); which == 1: the pair counts by particle of each RVE.
+__global__ void __launch_bounds__(SCAN_T) k_scan_part(BatchDev *bd, int which)
 {
+    const int32_t *tiles = which == 0 ? bd->tile_c : bd->tile_n;
+    const int r = block_rve(tiles, bd->B);
+    RveDev *st = bd->rv[r];
     if (which == 0 && !st->active) return;
     const int m = scan_len(st, which);
-    const int base = blockIdx.x * SCAN_TILE;
+    const int tile = blockIdx.x - tiles[r];
+    const int base = tile * SCAN_TILE;
     if (base >= m) return;
     const uint32_t *in = scan_in(st, which);
     uint32_t s = 0;
@@ -343,11 +377,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_part(RveDev *st, int which)
     __shared__ uint32_t tot;
     block_excl_scan(s, &tot);
     __syncthreads();
-    if (threadIdx.x == 0) st->scan_part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) st->scan_part[tile] = tot;
 }
 
-__global__ void __launch_bounds__(SCAN_T) k_scan_top(RveDev *st, int which)
+// one block per RVE
+__global__ void __launch_bounds__(SCAN_T) k_scan_top(BatchDev *bd, int which)
 {
+    RveDev *st = bd->rv[blockIdx.x];
     if (which == 0 && !st->active) return;
     const int m = scan_len(st, which);
     const int nb = (m + SCAN_TILE - 1) / SCAN_TILE;
@@ -376,11 +412,15 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_top(RveDev *st, int which)
 
 // which == 0: counts -> cell_start, counts cleared.  which == 1: pcount in
 // place (pcount has n + 1 entries).
-__global__ void __launch_bounds__(SCAN_T) k_scan_down(RveDev *st, int which)
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(BatchDev *bd, int which)
 {
+    const int32_t *tiles = which == 0 ? bd->tile_c : bd->tile_n;
+    const int r = block_rve(tiles, bd->B);
+    RveDev *st = bd->rv[r];
     if (which == 0 && !st->active) return;
     const int m = scan_len(st, which);
-    const int base = blockIdx.x * SCAN_TILE;
+    const int tile = blockIdx.x - tiles[r];
+    const int base = tile * SCAN_TILE;
     if (base >= m) return;
     uint32_t *in = scan_in(st, which);
     uint32_t *out = which == 0 ? st->cell_start : st->pcount;
@@ -392,7 +432,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(RveDev *st, int which)
         v[k] = i < m ? in[i] : 0u;
         s += v[k];
     }
-    uint32_t off = block_excl_scan(s, nullptr) + st->scan_part[blockIdx.x];
+    uint32_t off = block_excl_scan(s, nullptr) + st->scan_part[tile];
 #pragma unroll
     for (int k = 0; k < SCAN_V; k++) {
         const int i = base + threadIdx.x * SCAN_V + k;
@@ -409,47 +449,34 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(RveDev *st, int which)
 // ---------------------------------------------------------------------------
 static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-void launch_begin(RveDev *d_st, cudaStream_t s) { k_begin<<<1, 1, 0, s>>>(d_st); }
-void launch_control(RveDev *d_st, cudaStream_t s) { k_control<<<1, 1, 0, s>>>(d_st); }
+void launch_begin(const BatchShape &b, cudaStream_t s) { k_begin<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d); }
+void launch_control(const BatchShape &b, cudaStream_t s) { k_control<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d); }
 
-void launch_scan(RveDev *d_st, int which, int64_t max_len, cudaStream_t s)
+void launch_scan(const BatchShape &b, int which, cudaStream_t s)
 {
-    const int nb = blocks_for(max_len, SCAN_TILE);
-    k_scan_part<<<nb, SCAN_T, 0, s>>>(d_st, which);
-    k_scan_top<<<1, SCAN_T, 0, s>>>(d_st, which);
-    k_scan_down<<<nb, SCAN_T, 0, s>>>(d_st, which);
+    const int nt = which == 0 ? b.tiles_c : b.tiles_n;
+    k_scan_part<<<nt, SCAN_T, 0, s>>>(b.d, which);
+    k_scan_top<<<b.B, SCAN_T, 0, s>>>(b.d, which);
+    k_scan_down<<<nt, SCAN_T, 0, s>>>(b.d, which);
 }
 
 int64_t scan_part_len(int64_t max_len) { return blocks_for(max_len, SCAN_TILE); }
+int scan_tile() { return SCAN_TILE; }
 
-void launch_bin(RveDev *d_st, const HostShape &sh, cudaStream_t s)
+void launch_bin(const BatchShape &b, bool in32, bool out32, cudaStream_t s)
 {
     const int T = 256;
-    const int nbp = blocks_for(sh.n, T);
     // the binary32 shift path only where the scatter also writes binary32
-    if (sh.dim == 2) {
-        if (sh.f32 && sh.out_f32) k_bin_count<2, true, true><<<nbp, T, 0, s>>>(d_st);
-        else if (sh.f32) k_bin_count<2, true, false><<<nbp, T, 0, s>>>(d_st);
-        else k_bin_count<2, false, false><<<nbp, T, 0, s>>>(d_st);
-    } else {
-        if (sh.f32 && sh.out_f32) k_bin_count<3, true, true><<<nbp, T, 0, s>>>(d_st);
-        else if (sh.f32) k_bin_count<3, true, false><<<nbp, T, 0, s>>>(d_st);
-        else k_bin_count<3, false, false><<<nbp, T, 0, s>>>(d_st);
-    }
-    launch_scan(d_st, 0, sh.ncells_cap, s);
-    if (sh.dim == 2) {
-        if (sh.f32 && sh.out_f32) k_bin_scatter<2, true, true><<<nbp, T, 0, s>>>(d_st);
-        else if (sh.f32) k_bin_scatter<2, true, false><<<nbp, T, 0, s>>>(d_st);
-        else k_bin_scatter<2, false, false><<<nbp, T, 0, s>>>(d_st);
-    } else {
-        if (sh.f32 && sh.out_f32) k_bin_scatter<3, true, true><<<nbp, T, 0, s>>>(d_st);
-        else if (sh.f32) k_bin_scatter<3, true, false><<<nbp, T, 0, s>>>(d_st);
-        else k_bin_scatter<3, false, false><<<nbp, T, 0, s>>>(d_st);
-    }
-    k_bin_stamp<<<1, 1, 0, s>>>(d_st);
-    const int nbc = blocks_for(sh.ncells_cap, T);
-    if (sh.out_f32) k_cell_sort<true><<<nbc, T, 0, s>>>(d_st);
-    else k_cell_sort<false><<<nbc, T, 0, s>>>(d_st);
+    if (in32 && out32) k_bin_count<true, true><<<b.blocks_p, T, 0, s>>>(b.d);
+    else if (in32) k_bin_count<true, false><<<b.blocks_p, T, 0, s>>>(b.d);
+    else k_bin_count<false, false><<<b.blocks_p, T, 0, s>>>(b.d);
+    launch_scan(b, 0, s);
+    if (in32 && out32) k_bin_scatter<true, true><<<b.blocks_p, T, 0, s>>>(b.d);
+    else if (in32) k_bin_scatter<true, false><<<b.blocks_p, T, 0, s>>>(b.d);
+    else k_bin_scatter<false, false><<<b.blocks_p, T, 0, s>>>(b.d);
+    k_bin_stamp<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d);
+    if (out32) k_cell_sort<true><<<b.blocks_c, T, 0, s>>>(b.d);
+    else k_cell_sort<false><<<b.blocks_c, T, 0, s>>>(b.d);
 }
 
 // ---------------------------------------------------------------------------
@@ -495,16 +522,16 @@ __global__ void k_import(RveDev *st, const double *xyz, const double *rb)
     p.cell[i] = lin;
 }
 
-void launch_import(RveDev *d_st, const HostShape &sh, const double *xyz, const double *rb,
+void launch_import(RveDev *d_st, int dim, bool f32, int64_t n, const double *xyz, const double *rb,
                    cudaStream_t s)
 {
     k_import_begin<<<1, 1, 0, s>>>(d_st);
-    const int nb = blocks_for(sh.n, 256);
-    if (sh.dim == 2) {
-        if (sh.f32) k_import<2, true><<<nb, 256, 0, s>>>(d_st, xyz, rb);
+    const int nb = blocks_for(n, 256);
+    if (dim == 2) {
+        if (f32) k_import<2, true><<<nb, 256, 0, s>>>(d_st, xyz, rb);
         else k_import<2, false><<<nb, 256, 0, s>>>(d_st, xyz, rb);
     } else {
-        if (sh.f32) k_import<3, true><<<nb, 256, 0, s>>>(d_st, xyz, rb);
+        if (f32) k_import<3, true><<<nb, 256, 0, s>>>(d_st, xyz, rb);
         else k_import<3, false><<<nb, 256, 0, s>>>(d_st, xyz, rb);
     }
 }

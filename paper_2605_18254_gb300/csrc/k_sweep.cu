@@ -72,15 +72,14 @@ __device__ __forceinline__ float box_dist2(const float4 &t, const float w[3], in
     return ex * ex + ey * ey + ez * ez;
 }
 
+// One cell of colour chi (work item t of its RVE), processed by one warp.
 template <int DIM, bool F32>
-__global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(RveDev *st, int chi, int cap)
+__device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned char *base, int cap,
+                                           int &moved, unsigned &examined)
 {
     using PT = typename SweepSmem<F32>::PT;
     using DT = typename SweepSmem<F32>::DT;
-    extern __shared__ __align__(32) unsigned char smem[];
-    if (!st->active) return;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
+    const int lane = threadIdx.x & 31;
     StencilSmem &S = *reinterpret_cast<StencilSmem *>(base);
     PT *cpos = reinterpret_cast<PT *>(base + ST_HDR);
     float4 *capx = reinterpret_cast<float4 *>(cpos + cap);  // FP64 form only
@@ -90,29 +89,20 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(RveDev *st, int chi, in
     const Slot d = st->slot[st->dst_idx];
     PT *pos = reinterpret_cast<PT *>(d.pos);
     const uint32_t *cs = st->cell_start;
-    const int s0 = st->sub[0], s1 = st->sub[1], nsub = st->nsub;
+    const int s0 = st->sub[0], s1 = st->sub[1];
     const float w[3] = {(float)st->gw[0], (float)st->gw[1], (float)st->gw[2]};
     const uint64_t seed = st->seed, sweep = st->sweep;
     const double c_m = st->c_m;
     const float cmf = (float)c_m;
     const float g1 = 1.0f + st->guard;
     const int N_l = st->N_l;
-    int moved = 0;
-    unsigned examined = 0;
-
-    // cells of this colour are handed out one at a time to whichever warp
-    // is free (dense cells take far longer than sparse ones)
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = (int)atomicAdd(&st->wq[chi], 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= nsub) break;
+    {
         const int hx = 3 * (t % s0) + chi % 3;
         const int hy = 3 * ((t / s0) % s1) + (chi / 3) % 3;
         const int hz = DIM == 3 ? 3 * (t / (s0 * s1)) + chi / 9 : 0;
         const int cell = hx + st->gn[0] * (hy + st->gn[1] * hz);
         const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
-        if (nh == 0) continue;
+        if (nh == 0) return;
         int nst, center;
         const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
         // home corner (FP64 form: the binary32 copies are relative to it)
@@ -341,9 +331,44 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(RveDev *st, int chi, in
             __syncwarp();
         }
     }
-    if (lane == 0 && moved) atomicAdd(&st->red[3], (unsigned long long)moved);
-    examined = __reduce_add_sync(0xffffffffu, examined);
-    if (lane == 0 && examined) atomicAdd(&st->pairs_sweep, (unsigned long long)examined);
+}
+
+// One launch per colour over all RVEs of the batch: each warp takes the next
+// (RVE, cell) work item from the colour's counter.  2D RVEs have 9 colours.
+template <bool F32>
+__global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(BatchDev *bd, int chi, int cap)
+{
+    extern __shared__ __align__(32) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
+    const int B = bd->B;
+    const int total = bd->sub[B];
+    for (;;) {
+        int tg = 0, r = 0;
+        if (lane == 0) {
+            tg = (int)atomicAdd(&bd->wq[chi], 1u);
+            if (tg < total) r = find_seg(bd->sub, B, tg);
+        }
+        tg = __shfl_sync(0xffffffffu, tg, 0);
+        if (tg >= total) break;
+        r = __shfl_sync(0xffffffffu, r, 0);
+        RveDev *st = bd->rv[r];
+        const int t = tg - bd->sub[r];
+        if (!st->active || t >= st->nsub) continue;
+        int moved = 0;
+        unsigned examined = 0;
+        if (st->dim == 3) {
+            sweep_cell<3, F32>(st, chi, t, base, cap, moved, examined);
+        } else {
+            if (chi >= 9) continue;
+            sweep_cell<2, F32>(st, chi, t, base, cap, moved, examined);
+        }
+        examined = __reduce_add_sync(0xffffffffu, examined);
+        if (lane == 0) {
+            if (moved) atomicAdd(&st->red[3], (unsigned long long)moved);
+            if (examined) atomicAdd(&st->pairs_sweep, (unsigned long long)examined);
+        }
+    }
 }
 
 int sweep_cap_max(bool f32) { return f32 ? 512 : 256; }
@@ -356,7 +381,7 @@ static size_t sweep_smem(bool f32, int cap)
 static int g_sms = 0;
 
 // Blocks that stay resident on one SM at this shared memory size; a launch
-// uses at most that many per SM and the warps loop over the cells.
+// uses at most that many per SM and the warps pull work items.
 template <typename K>
 static int resident_blocks(K kern, size_t smem)
 {
@@ -365,28 +390,24 @@ static int resident_blocks(K kern, size_t smem)
     return nb > 0 ? nb : 1;
 }
 
-void launch_sweep_colour(RveDev *d_st, const HostShape &sh, int chi, cudaStream_t s)
+void launch_sweep_colour(const BatchShape &b, int chi, cudaStream_t s)
 {
-    const int cap = sh.cap_sweep;
-    const size_t smem = sweep_smem(sh.f32, cap);
-    const int want = (int)((sh.nsub_cap + SW_WARPS - 1) / SW_WARPS);
+    const int cap = b.cap;
+    const size_t smem = sweep_smem(b.f32, cap);
+    const int64_t want64 = (b.sub_total + SW_WARPS - 1) / SW_WARPS;
+    const int want = (int)(want64 > 0x7fffffff ? 0x7fffffff : want64);
     auto shape = [&](auto kern) {
         const int res = resident_blocks(kern, smem) * (g_sms > 0 ? g_sms : 1);
         return want < res ? want : res;
     };
-    if (sh.f32) {
-        if (sh.dim == 2) k_sweep<2, true><<<shape(k_sweep<2, true>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
-        else k_sweep<3, true><<<shape(k_sweep<3, true>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
-    } else {
-        if (sh.dim == 2) k_sweep<2, false><<<shape(k_sweep<2, false>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
-        else k_sweep<3, false><<<shape(k_sweep<3, false>), SW_WARPS * 32, smem, s>>>(d_st, chi, cap);
-    }
+    if (b.f32) k_sweep<true><<<shape(k_sweep<true>), SW_WARPS * 32, smem, s>>>(b.d, chi, cap);
+    else k_sweep<false><<<shape(k_sweep<false>), SW_WARPS * 32, smem, s>>>(b.d, chi, cap);
 }
 
-void launch_sweep(RveDev *d_st, const HostShape &sh, cudaStream_t s)
+void launch_sweep(const BatchShape &b, cudaStream_t s)
 {
-    const int ncol = sh.dim == 3 ? 27 : 9;
-    for (int chi = 0; chi < ncol; chi++) launch_sweep_colour(d_st, sh, chi, s);
+    const int ncol = b.has3d ? 27 : 9;
+    for (int chi = 0; chi < ncol; chi++) launch_sweep_colour(b, chi, s);
 }
 
 // Dynamic shared memory above 48 KB needs an opt-in per kernel.
@@ -397,12 +418,10 @@ void sweep_configure()
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const int s32 = (int)sweep_smem(true, sweep_cap_max(true));
-    const int s64 = (int)sweep_smem(false, sweep_cap_max(false));
-    cudaFuncSetAttribute(k_sweep<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-    cudaFuncSetAttribute(k_sweep<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-    cudaFuncSetAttribute(k_sweep<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-    cudaFuncSetAttribute(k_sweep<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep_smem(true, sweep_cap_max(true)));
+    cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep_smem(false, sweep_cap_max(false)));
 }
 
 }  // namespace srm

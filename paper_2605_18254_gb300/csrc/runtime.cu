@@ -1,37 +1,35 @@
 // runtime.cu -- host side of the C interface declared in include/srm.h:
-// handle creation and device memory, starting configurations, the captured
-// super-step graph and its replay, inspection and read-back.
+// RVE creation and device memory, starting configurations, the captured
+// super-step graphs and their replay, batches of RVEs, inspection and
+// read-back.
 //
-// A "super-step" is one sweep of Algorithm 3 with everything around it:
+// A "super-step" is one sweep of Algorithm 3 with everything around it, for
+// every RVE of a group at once:
 //   k_begin (state machine: swell and new grid at the start of an
 //   iteration, buffer roles) -> binning (Algorithm 2) -> 3^d colour launches
 //   of the sweep -> Algorithm 6 check (N_k loop only) -> k_control
 //   (accept / next round / shake / done).
 // Every launch reads what changes from the device state, so one captured
 // CUDA graph of a few super-steps is replayed for the whole run and the host
-// only polls the state word every few dozen sweeps.
+// only polls the state every few dozen sweeps.  A single handle is a group
+// of one RVE; a batch is a group of many (uneven sizes, 2D and 3D mixed),
+// advanced by the same launches.
+#include "runtime.h"
+
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
-#include <string>
-#include <vector>
-
-#include "srm.h"
-#include "srm_dev.cuh"
-#include "srm_launch.h"
 
 extern "C" int inp_radii_lognormal(int64_t n, double mean, double sd, double lo, double hi,
                                    uint64_t seed, double *out);
 extern "C" int inp_rsa(int dim, const double L[3], int64_t n, const double *R, uint64_t seed,
                        int mode, int64_t n_clusters, double sigma, int64_t max_attempts, double *X);
 
-using srm::RveDev;
-
 static thread_local std::string g_err;
 
-static srm_status fail(srm_status st, const std::string &msg)
+srm_status fail(srm_status st, const std::string &msg)
 {
     g_err = msg;
     return st;
@@ -41,70 +39,14 @@ namespace srm {
 void set_last_error(const std::string &msg) { g_err = msg; }
 }  // namespace srm
 
-#define CK(call)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(SRM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-struct srm_rve {
-    RveDev h{};               // host copy: constants and buffer pointers
-    RveDev *d = nullptr;      // device state
-    RveDev *pin = nullptr;    // pinned host mirror for read-back
-    srm::HostShape sh{};
-    cudaStream_t stream = nullptr;      // the caller's stream: all work runs here
-    cudaStream_t cap_stream = nullptr;  // private stream used only to record graphs
-    unsigned long long *pin_red = nullptr;
-    srm_allocator alloc{};
-    bool has_alloc = false;
-    std::vector<void *> owned;
-    cudaGraphExec_t g1 = nullptr, gN = nullptr;
-    int gN_steps = 8;
-    double S0 = 0.0, V = 0.0, phi_t = 0.0, lam_min = 0.0;
-    double *d_xyz = nullptr, *d_rad = nullptr;
-    long long *d_ij = nullptr;
-    int64_t d_ij_cap = 0;
-    int64_t launches = 0;          // kernels launched (graph nodes counted per replay)
-    int64_t launches_per_step = 0; // kernels in one super-step
-    // timing mode
-    bool timing = false;
-    cudaGraphExec_t gT = nullptr;
-    std::vector<cudaEvent_t> ev;   // events of one timed super-step
-    srm_timings tm{};
-};
-
 // ---------------------------------------------------------------------------
-// memory
+// host-side preparation of one job: radii, starting positions, scales,
+// capacities
 // ---------------------------------------------------------------------------
-static void *dev_alloc(srm_rve *h, size_t bytes)
-{
-    if (bytes == 0) bytes = 16;
-    void *p = nullptr;
-    if (h->has_alloc) {
-        p = h->alloc.alloc(h->alloc.ctx, bytes, (void *)h->stream);
-    } else if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
-        p = nullptr;
-    }
-    if (p) h->owned.push_back(p);
-    return p;
-}
 
-static void dev_free_all(srm_rve *h)
-{
-    for (void *p : h->owned) {
-        if (h->has_alloc) h->alloc.free(h->alloc.ctx, p, (void *)h->stream);
-        else cudaFreeAsync(p, h->stream);
-    }
-    h->owned.clear();
-}
-
-// ---------------------------------------------------------------------------
-// closed forms of the bookkeeping (binary64)
-// ---------------------------------------------------------------------------
+// sum of base disk areas / sphere volumes in id order
 static double base_measure(int dim, const double *r, int64_t n)
 {
-    // sum of base disk areas / sphere volumes in id order
     double s = 0.0;
     for (int64_t i = 0; i < n; i++) {
         const double ri = r[i];
@@ -113,11 +55,11 @@ static double base_measure(int dim, const double *r, int64_t n)
     return s;
 }
 
-static double phi_of(const srm_rve *h, double lam)
+double phi_of(int dim, double S0, double V, double lam)
 {
     double ld = lam * lam;
-    if (h->h.dim == 3) ld = ld * lam;
-    return ld * h->S0 / h->V;
+    if (dim == 3) ld = ld * lam;
+    return ld * S0 / V;
 }
 
 static double lam_of(int dim, double S0, double V, double phi)
@@ -126,15 +68,15 @@ static double lam_of(int dim, double S0, double V, double phi)
     return dim == 2 ? std::sqrt(q) : std::cbrt(q);
 }
 
-// cells per axis of the grid for scale lam (same rule as the device)
-static int64_t cells_for(const srm_rve *h, double lam, int64_t per_axis[3])
+// cells per axis of the grid for scale lam (the device rule of set_grid)
+int64_t cells_for(int dim, const double L[3], double rmax, double c_m, double lam, int64_t per_axis[3])
 {
-    const double cs = 2.5 * (lam * h->h.rmax) + h->h.c_m;
+    const double cs = 2.5 * (lam * rmax) + c_m;
     int64_t tot = 1;
     for (int a = 0; a < 3; a++) {
         per_axis[a] = 1;
-        if (a >= h->h.dim) continue;
-        int64_t k = (int64_t)(h->h.L[a] / (3.0 * cs));
+        if (a >= dim) continue;
+        int64_t k = (int64_t)(L[a] / (3.0 * cs));
         if (k < 1) k = 1;
         per_axis[a] = 3 * k;
         tot *= per_axis[a];
@@ -142,14 +84,490 @@ static int64_t cells_for(const srm_rve *h, double lam, int64_t per_axis[3])
     return tot;
 }
 
-// ---------------------------------------------------------------------------
-// device state read-back and small writes
-// ---------------------------------------------------------------------------
-static srm_status pull_state(srm_rve *h)
+// Staging capacity of the warp-per-cell sweep: the 95th percentile of the
+// stencil population of the starting positions on the grid of the target
+// scale (the coarsest grid of the run), times the part of the stencil volume
+// within reach of the home cell, with slack.  Denser cells stage what fits
+// and read the rest from global memory (same results).
+static int staging_estimate(const Prep &q)
 {
-    CK(cudaMemcpyAsync(h->pin, h->d, sizeof(RveDev), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    if (h->pin->status != 0) return fail(SRM_E_STATE, "device state reports an error");
+    int64_t pa[3];
+    const int64_t nc = cells_for(q.dim, q.L, q.rmax, q.p.c_m, q.lam_t, pa);
+    std::vector<uint32_t> occ((size_t)nc, 0u);
+    for (int64_t i = 0; i < q.n; i++) {
+        int64_t lin = 0, mul = 1;
+        for (int a = 0; a < q.dim; a++) {
+            const double wa = q.L[a] / (double)pa[a];
+            int64_t c = (int64_t)(q.x[(size_t)i * q.dim + a] / wa);
+            c = ((c % pa[a]) + pa[a]) % pa[a];
+            lin += c * mul;
+            mul *= pa[a];
+        }
+        occ[(size_t)lin]++;
+    }
+    std::vector<uint32_t> tpop;
+    tpop.reserve((size_t)q.n);
+    const int zr = q.dim == 3 ? 1 : 0;
+    for (int64_t c = 0; c < nc; c++) {
+        if (!occ[(size_t)c]) continue;
+        const int64_t cx = c % pa[0], cy = (c / pa[0]) % pa[1], cz = c / (pa[0] * pa[1]);
+        uint32_t t = 0;
+        for (int dz = -zr; dz <= zr; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int64_t ex = (cx + dx + pa[0]) % pa[0], ey = (cy + dy + pa[1]) % pa[1],
+                                  ez = (cz + dz + pa[2]) % pa[2];
+                    t += occ[(size_t)(ex + pa[0] * (ey + pa[1] * ez))];
+                }
+        for (uint32_t k = 0; k < occ[(size_t)c]; k++) tpop.push_back(t);  // per particle
+    }
+    uint32_t t95 = 0;
+    if (!tpop.empty()) {
+        const size_t qi = tpop.size() * 95 / 100;
+        std::nth_element(tpop.begin(), tpop.begin() + (ptrdiff_t)qi, tpop.end());
+        t95 = tpop[qi];
+    }
+    const double wt = q.L[0] / (double)pa[0];
+    const double reach = 2.0 * (2.0 * q.lam_t * q.rmax + 2.0 * q.p.c_m);
+    double frac = (wt + reach) / (3.0 * wt);
+    frac = frac > 1.0 ? 1.0 : frac;
+    frac = q.dim == 3 ? frac * frac * frac : frac * frac;
+    int64_t cap = (int64_t)(1.25 * frac * (double)t95) + 16;
+    cap = (cap + 31) / 32 * 32;
+    return (int)(cap < 64 ? 64 : cap);
+}
+
+srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, double phi_t, uint64_t seed,
+                   const srm_params *pin, Prep &q)
+{
+    if (!box || !radii) return fail(SRM_E_ARG, "null argument");
+    if (pin) q.p = *pin;
+    else srm_params_default(&q.p);
+    const srm_params &p = q.p;
+    if (dim != 2 && dim != 3) return fail(SRM_E_ARG, "dim must be 2 or 3");
+    const int64_t n = radii->n;
+    if (n < 1) return fail(SRM_E_ARG, "n must be >= 1");
+    if (n > 0x7fffffffLL) return fail(SRM_E_ARG, "n must be < 2^31");
+    for (int a = 0; a < dim; a++)
+        if (!(box[a] > 0.0)) return fail(SRM_E_ARG, "box lengths must be > 0");
+    if (!(phi_t > 0.0 && phi_t < 1.0)) return fail(SRM_E_ARG, "target phi must be in (0, 1)");
+    if (!(p.c_m > 0.0)) return fail(SRM_E_ARG, "c_m must be > 0");
+    if (!(p.c_w >= 0.0)) return fail(SRM_E_ARG, "c_w must be >= 0");
+    if (p.N_k < 1 || p.N_l < 1 || p.N_shake < 0) return fail(SRM_E_ARG, "N_k, N_l >= 1, N_shake >= 0");
+    if (p.precision != SRM_PREC_F64 && p.precision != SRM_PREC_F32)
+        return fail(SRM_E_ARG, "precision must be 32 or 64");
+    if (p.precision == SRM_PREC_F32 && !(p.guard > 0.0 && p.guard < 1e-2))
+        return fail(SRM_E_ARG, "FP32 guard must be in (0, 1e-2)");
+    q.dim = dim;
+    q.n = n;
+    q.seed = seed;
+    q.phi_t = phi_t;
+    for (int a = 0; a < 3; a++) q.L[a] = a < dim ? box[a] : 1.0;
+
+    // base radii
+    q.r.assign((size_t)n, 0.0);
+    if (radii->kind == SRM_RADII_EXPLICIT) {
+        if (!radii->r) return fail(SRM_E_ARG, "explicit radii need r");
+        std::memcpy(q.r.data(), radii->r, sizeof(double) * (size_t)n);
+    } else if (radii->kind == SRM_RADII_MONO) {
+        for (auto &v : q.r) v = radii->mean;
+    } else if (radii->kind == SRM_RADII_LOGNORMAL) {
+        if (!(radii->mean > 0 && radii->sd >= 0 && radii->lo <= radii->hi))
+            return fail(SRM_E_ARG, "bad log-normal parameters");
+        if (inp_radii_lognormal(n, radii->mean, radii->sd, radii->lo, radii->hi, seed, q.r.data()))
+            return fail(SRM_E_ARG, "log-normal truncation window too narrow");
+    } else {
+        return fail(SRM_E_ARG, "unknown radii kind");
+    }
+    q.rmax = 0.0;
+    for (double v : q.r) {
+        if (!(v > 0.0)) return fail(SRM_E_ARG, "radii must be > 0");
+        q.rmax = v > q.rmax ? v : q.rmax;
+    }
+    q.V = q.L[0] * q.L[1];
+    if (dim == 3) q.V = q.V * q.L[2];
+    q.S0 = base_measure(dim, q.r.data(), n);
+    q.lam_t = p.lambda_t > 0.0 ? p.lambda_t : lam_of(dim, q.S0, q.V, phi_t);
+
+    // starting configuration (Algorithm 1 line 2)
+    q.x.assign((size_t)n * dim, 0.0);
+    if (p.init == SRM_INIT_EXPLICIT) {
+        if (!p.init_pos) return fail(SRM_E_ARG, "explicit start needs init_pos");
+        std::memcpy(q.x.data(), p.init_pos, sizeof(double) * q.x.size());
+        for (size_t i = 0; i < q.x.size(); i++) {
+            const int a = (int)(i % dim);
+            if (!(q.x[i] >= 0.0 && q.x[i] < q.L[a])) return fail(SRM_E_ARG, "start positions must lie in [0, L)");
+        }
+        q.lam0 = p.lambda0 > 0.0 ? p.lambda0 : 1.0;
+    } else if (p.init == SRM_INIT_RSA_UNIFORM || p.init == SRM_INIT_RSA_CLUSTERED) {
+        if (!(p.f0 > 0.0 && p.f0 <= phi_t)) return fail(SRM_E_ARG, "f0 must be in (0, phi_t]");
+        q.lam0 = lam_of(dim, q.S0, q.V, p.f0);
+        std::vector<double> R0((size_t)n);
+        for (int64_t i = 0; i < n; i++) R0[(size_t)i] = q.lam0 * q.r[(size_t)i];
+        const int clustered = p.init == SRM_INIT_RSA_CLUSTERED;
+        if (inp_rsa(dim, q.L, n, R0.data(), seed, clustered, p.n_clusters, p.cluster_sigma, 100000000LL,
+                    q.x.data()))
+            return fail(SRM_E_INIT, "random sequential addition could not place every particle");
+    } else {
+        return fail(SRM_E_ARG, "unknown init kind");
+    }
+
+    // the minimum-image search needs at least three cells of the final size
+    const double cs_t = 2.5 * (q.lam_t * q.rmax) + p.c_m;
+    for (int a = 0; a < dim; a++)
+        if (q.L[a] < 3.0 * cs_t) return fail(SRM_E_ARG, "box narrower than three cells of size 2.5 R_max + c_m");
+
+    // capacities: the grid is finest at the smallest scale
+    q.lam_min = (q.lam0 < q.lam_t ? q.lam0 : q.lam_t) * (1.0 - 1e-9);
+    int64_t per[3];
+    q.ncells_need = cells_for(dim, q.L, q.rmax, p.c_m, q.lam_min, per);
+    if (q.ncells_need > 0x7ffffff0LL) return fail(SRM_E_ARG, "too many cells (radii too small for the box)");
+    q.nsub_need = 1;
+    for (int a = 0; a < dim; a++) q.nsub_need *= per[a] / 3;
+    q.cap_est = staging_estimate(q);
+    return SRM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// members (one RVE each) and groups (RVEs advanced together)
+// ---------------------------------------------------------------------------
+void *dev_alloc(Group &g, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (g.has_alloc) {
+        p = g.alloc.alloc(g.alloc.ctx, bytes, (void *)g.stream);
+    } else if (cudaMallocAsync(&p, bytes, g.stream) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) g.owned.push_back(p);
+    return p;
+}
+
+void group_free(Group &g)
+{
+    cudaStreamSynchronize(g.stream);
+    if (g.g1) cudaGraphExecDestroy(g.g1);
+    if (g.gN) cudaGraphExecDestroy(g.gN);
+    if (g.gT) cudaGraphExecDestroy(g.gT);
+    g.g1 = g.gN = g.gT = nullptr;
+    for (auto e : g.ev) cudaEventDestroy(e);
+    g.ev.clear();
+    for (void *p : g.owned) {
+        if (g.has_alloc) g.alloc.free(g.alloc.ctx, p, (void *)g.stream);
+        else cudaFreeAsync(p, g.stream);
+    }
+    g.owned.clear();
+    cudaStreamSynchronize(g.stream);
+    if (g.cap_stream) cudaStreamDestroy(g.cap_stream);
+    g.cap_stream = nullptr;
+    if (g.pin) cudaFreeHost(g.pin);
+    if (g.pin_red) cudaFreeHost(g.pin_red);
+    g.pin = nullptr;
+    g.pin_red = nullptr;
+    for (Member *mm : g.m) delete mm;
+    g.m.clear();
+}
+
+// Device buffers of a member with room for n_cap particles and ncells_cap
+// cells (any dimension).
+srm_status member_alloc(Group &g, Member &mb, int64_t n_cap, int64_t ncells_cap, int64_t nsub_cap)
+{
+    bool ok = true;
+    auto A = [&](size_t bytes) -> void * {
+        void *q = dev_alloc(g, bytes);
+        if (!q) ok = false;
+        return q;
+    };
+    RveDev &s = mb.h;
+    const size_t n = (size_t)n_cap;
+    for (int k = 0; k < 3; k++) {
+        s.slot[k].pos = A(sizeof(double4_32a) * n);
+        s.slot[k].rb = (double *)A(sizeof(double) * n);
+        s.slot[k].pid = (uint32_t *)A(sizeof(uint32_t) * n);
+        s.slot[k].cell = (uint32_t *)A(sizeof(uint32_t) * n);
+    }
+    s.counts = (uint32_t *)A(sizeof(uint32_t) * (size_t)ncells_cap);
+    s.cell_start = (uint32_t *)A(sizeof(uint32_t) * (size_t)(ncells_cap + 1));
+    const int64_t parts = srm::scan_part_len(ncells_cap > n_cap + 1 ? ncells_cap : n_cap + 1);
+    s.scan_part = (uint32_t *)A(sizeof(uint32_t) * (size_t)(parts + 1));
+    s.src_cell = (uint32_t *)A(sizeof(uint32_t) * n);
+    s.src_rank = (uint32_t *)A(sizeof(uint32_t) * n);
+    s.flags = (uint8_t *)A(n);
+    s.pcount = (uint32_t *)A(sizeof(uint32_t) * (n + 1));
+    s.red = (unsigned long long *)A(sizeof(unsigned long long) * 8);
+    mb.d = (RveDev *)A(sizeof(RveDev));
+    mb.stage_x = (double *)A(sizeof(double) * 3 * n);
+    mb.stage_r = (double *)A(sizeof(double) * n);
+    if (!ok) return fail(SRM_E_NOMEM, "device allocation failed");
+    mb.n_cap = n_cap;
+    mb.ncells_cap = ncells_cap;
+    mb.nsub_cap = nsub_cap;
+    CK(cudaMemsetAsync(s.counts, 0, sizeof(uint32_t) * (size_t)ncells_cap, g.stream));
+    CK(cudaMemsetAsync(s.red, 0, sizeof(unsigned long long) * 8, g.stream));
+    CK(cudaMemsetAsync(s.flags, 0, n, g.stream));
+    // an empty member takes no part in the super-steps
+    s.mode = srm::MODE_DONE;
+    s.n = 0;
+    s.dim = 3;
+    s.ncells_cap = (int32_t)ncells_cap;
+    s.iter_cap = INT64_MAX;
+    CK(cudaMemcpyAsync(mb.d, &s, sizeof(RveDev), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    return SRM_OK;
+}
+
+bool member_fits(const Member &mb, const Prep &q)
+{
+    return q.n <= mb.n_cap && q.ncells_need <= mb.ncells_cap && q.nsub_need <= mb.nsub_cap;
+}
+
+// Loads a prepared job into a member: constants, fresh state, starting
+// positions (uploaded and binned on the grid of the starting scale).
+srm_status member_load(Group &g, Member &mb, const Prep &q)
+{
+    if (!member_fits(mb, q)) return fail(SRM_E_ARG, "job exceeds the capacity of the slot");
+    if ((q.p.precision == SRM_PREC_F32) != g.f32) return fail(SRM_E_ARG, "job precision differs from the batch");
+    RveDev &s = mb.h;
+    s.dim = q.dim;
+    s.prec = q.p.precision;
+    s.n = (int32_t)q.n;
+    s.N_k = q.p.N_k;
+    s.N_l = q.p.N_l;
+    s.N_shake = q.p.N_shake;
+    for (int a = 0; a < 3; a++) {
+        s.L[a] = q.L[a];
+        s.halfL[a] = 0.5 * q.L[a];
+        s.Lf[a] = (float)q.L[a];
+    }
+    s.rmax = q.rmax;
+    s.c_w = q.p.c_w;
+    s.c_m = q.p.c_m;
+    s.guard = (float)q.p.guard;
+    s.seed = q.seed;
+    s.lam_t = q.lam_t;
+    s.ncells_cap = (int32_t)mb.ncells_cap;
+    s.iter_cap = INT64_MAX;
+    s.lam_P = q.lam0;
+    s.lam_Q = q.lam0;
+    s.mode = q.lam0 >= q.lam_t ? srm::MODE_DONE : srm::MODE_BEGIN;
+    s.resume_mode = s.mode;
+    s.k = s.s = 0;
+    s.p_idx = 0;
+    s.src_idx = 0;
+    s.dst_idx = 1;
+    s.active = s.do_check = 0;
+    s.sweep = q.p.sweep0;
+    s.iters = s.accepted = s.shaken = s.sweeps = 0;
+    s.it_result = s.it_k = s.it_shake = 0;
+    s.it_overlap = s.moved_last = 0;
+    s.status = 0;
+    s.pairs_sweep = s.pairs_check = s.stage_overflow = 0;
+    mb.dim = q.dim;
+    mb.n = q.n;
+    mb.S0 = q.S0;
+    mb.V = q.V;
+    mb.phi_t = q.phi_t;
+    mb.lam_min = q.lam_min;
+    CK(cudaMemcpyAsync(mb.d, &s, sizeof(RveDev), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaMemcpyAsync(mb.stage_x, q.x.data(), sizeof(double) * q.x.size(), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaMemcpyAsync(mb.stage_r, q.r.data(), sizeof(double) * (size_t)q.n, cudaMemcpyHostToDevice, g.stream));
+    srm::launch_import(mb.d, q.dim, g.f32, q.n, mb.stage_x, mb.stage_r, g.stream);
+    g.launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(g.stream));
+    mb.loaded = true;
+    mb.harvested = false;
+    return SRM_OK;
+}
+
+static int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+// Device descriptor of a set of members, with the block offsets of each.
+static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, BatchDev **d_out, BatchShape &sh)
+{
+    const int B = (int)ms.size();
+    std::vector<int32_t> off(5 * (size_t)(B + 1), 0);
+    int32_t *bp = off.data(), *bc = bp + B + 1, *tc = bc + B + 1, *tn = tc + B + 1, *sb = tn + B + 1;
+    bool has3d = false;
+    for (int r = 0; r < B; r++) {
+        const Member &mb = *ms[(size_t)r];
+        bp[r + 1] = bp[r] + blocks(mb.n_cap, 256);
+        bc[r + 1] = bc[r] + blocks(mb.ncells_cap, 256);
+        tc[r + 1] = tc[r] + blocks(mb.ncells_cap, srm::scan_tile());
+        tn[r + 1] = tn[r] + blocks(mb.n_cap, srm::scan_tile());
+        sb[r + 1] = sb[r] + (int32_t)mb.nsub_cap;
+        has3d = has3d || mb.dim == 3 || mb.slot3d;
+    }
+    BatchDev *d = (BatchDev *)dev_alloc(g, sizeof(BatchDev));
+    int32_t *d_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * off.size());
+    RveDev **d_rv = (RveDev **)dev_alloc(g, sizeof(RveDev *) * (size_t)B);
+    if (!d || !d_off || !d_rv) return fail(SRM_E_NOMEM, "device allocation failed");
+    std::vector<RveDev *> rv((size_t)B);
+    for (int r = 0; r < B; r++) rv[(size_t)r] = ms[(size_t)r]->d;
+    BatchDev hb{};
+    hb.B = B;
+    hb.rv = d_rv;
+    hb.blk_p = d_off;
+    hb.blk_c = d_off + (B + 1);
+    hb.tile_c = d_off + 2 * (B + 1);
+    hb.tile_n = d_off + 3 * (B + 1);
+    hb.sub = d_off + 4 * (B + 1);
+    CK(cudaMemcpyAsync(d_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaMemcpyAsync(d_rv, rv.data(), sizeof(RveDev *) * (size_t)B, cudaMemcpyHostToDevice, g.stream));
+    CK(cudaMemcpyAsync(d, &hb, sizeof(BatchDev), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    *d_out = d;
+    sh.d = d;
+    sh.B = B;
+    sh.blocks_p = bp[B];
+    sh.blocks_c = bc[B];
+    sh.tiles_c = tc[B];
+    sh.tiles_n = tn[B];
+    sh.sub_total = sb[B];
+    sh.f32 = g.f32;
+    sh.has3d = has3d;
+    sh.cap = g.cap;
+    return SRM_OK;
+}
+
+// kernels of one super-step: begin, binning (count, 3 scan passes, scatter,
+// stamp, in-cell sort), 3^d sweep colours, check, control
+static int64_t kernels_per_superstep(bool has3d) { return 1 + 7 + (has3d ? 27 : 9) + 1 + 1; }
+
+static void enqueue_superstep(Group &g, cudaStream_t s, const std::vector<cudaEvent_t> *ev = nullptr)
+{
+    const BatchShape &sh = g.sh;
+    if (ev) cudaEventRecordWithFlags((*ev)[0], s, cudaEventRecordExternal);
+    srm::launch_begin(sh, s);
+    srm::launch_bin(sh, sh.f32, sh.f32, s);
+    if (ev) {
+        const int ncol = sh.has3d ? 27 : 9;
+        for (int chi = 0; chi < ncol; chi++) {
+            cudaEventRecordWithFlags((*ev)[1 + chi], s, cudaEventRecordExternal);
+            srm::launch_sweep_colour(sh, chi, s);
+        }
+        cudaEventRecordWithFlags((*ev)[1 + ncol], s, cudaEventRecordExternal);
+        srm::launch_check(sh, s);
+        cudaEventRecordWithFlags((*ev)[2 + ncol], s, cudaEventRecordExternal);
+        srm::launch_control(sh, s);
+        cudaEventRecordWithFlags((*ev)[3 + ncol], s, cudaEventRecordExternal);
+    } else {
+        srm::launch_sweep(sh, s);
+        srm::launch_check(sh, s);
+        srm::launch_control(sh, s);
+    }
+}
+
+// The graph is recorded on a private stream (recording runs nothing) and
+// launched on the caller's stream, which may be the legacy default stream.
+static srm_status capture(Group &g, int steps, cudaGraphExec_t *out, bool timed = false)
+{
+    cudaGraph_t gr = nullptr;
+    if (!g.cap_stream) CK(cudaStreamCreateWithFlags(&g.cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(g.cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < steps; i++) enqueue_superstep(g, g.cap_stream, timed ? &g.ev : nullptr);
+    CK(cudaStreamEndCapture(g.cap_stream, &gr));
+    cudaError_t e = cudaGraphInstantiate(out, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return fail(SRM_E_CUDA, std::string("graph: ") + cudaGetErrorString(e));
+    return SRM_OK;
+}
+
+// Builds the group descriptors and records the graphs (after the members
+// exist).
+srm_status group_finalize(Group &g)
+{
+    srm::sweep_configure();
+    srm::check_configure();
+    srm_status st = make_batchdev(g, g.m, &g.d, g.sh);
+    if (st != SRM_OK) return st;
+    for (Member *mb : g.m) {
+        std::vector<Member *> one{mb};
+        if ((st = make_batchdev(g, one, &mb->solo_d, mb->solo)) != SRM_OK) return st;
+    }
+    g.launches_per_step = kernels_per_superstep(g.sh.has3d);
+    const size_t B = g.m.size();
+    if (cudaMallocHost((void **)&g.pin, sizeof(RveDev) * B) != cudaSuccess ||
+        cudaMallocHost((void **)&g.pin_red, sizeof(unsigned long long) * 8) != cudaSuccess)
+        return fail(SRM_E_NOMEM, "pinned host allocation failed");
+    if ((st = capture(g, 1, &g.g1)) != SRM_OK) return st;
+    return capture(g, g.gN_steps, &g.gN);
+}
+
+srm_status pull_states(Group &g)
+{
+    CK(cudaStreamSynchronize(g.stream));
+    for (size_t r = 0; r < g.m.size(); r++)
+        CK(cudaMemcpyAsync(&g.pin[r], g.m[r]->d, sizeof(RveDev), cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    for (size_t r = 0; r < g.m.size(); r++)
+        if (g.pin[r].status != 0) return fail(SRM_E_STATE, "device state reports an error");
+    return SRM_OK;
+}
+
+srm_status pull_state(Group &g, size_t r)
+{
+    CK(cudaMemcpyAsync(&g.pin[r], g.m[r]->d, sizeof(RveDev), cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    if (g.pin[r].status != 0) return fail(SRM_E_STATE, "device state reports an error");
+    return SRM_OK;
+}
+
+static int64_t total_sweeps(const Group &g)
+{
+    int64_t s = 0;
+    for (size_t r = 0; r < g.m.size(); r++) s += g.pin[r].sweeps;
+    return s;
+}
+
+// Timing mode: one super-step per replay, with events between the stages;
+// the host waits for each replay and adds up the stage times.
+static srm_status run_timed(Group &g, int steps)
+{
+    const int ncol = g.sh.has3d ? 27 : 9;
+    if (g.ev.empty()) {
+        g.ev.resize((size_t)ncol + 4);
+        for (auto &e : g.ev) CK(cudaEventCreate(&e));
+    }
+    if (!g.gT) {
+        srm_status s = capture(g, 1, &g.gT, true);
+        if (s != SRM_OK) return s;
+    }
+    for (int i = 0; i < steps; i++) {
+        srm_status s = pull_states(g);
+        if (s != SRM_OK) return s;
+        const int64_t sw0 = total_sweeps(g);
+        CK(cudaGraphLaunch(g.gT, g.stream));
+        g.launches += g.launches_per_step;
+        if ((s = pull_states(g)) != SRM_OK) return s;
+        if (total_sweeps(g) == sw0) continue;  // nothing ran (targets reached or capped)
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]));
+        g.tm.ms_bin += ms;
+        for (int c = 0; c < ncol; c++) {
+            CK(cudaEventElapsedTime(&ms, g.ev[1 + c], g.ev[2 + c]));
+            g.tm.ms_sweep += ms;
+        }
+        g.tm.sweep_launches += ncol;
+        CK(cudaEventElapsedTime(&ms, g.ev[1 + ncol], g.ev[2 + ncol]));
+        g.tm.ms_check += ms;
+        bool checked = false;
+        for (size_t r = 0; r < g.m.size(); r++) checked = checked || g.pin[r].do_check;
+        if (checked) g.tm.check_launches += 1;
+        CK(cudaEventElapsedTime(&ms, g.ev[2 + ncol], g.ev[3 + ncol]));
+        g.tm.ms_control += ms;
+        g.tm.supersteps += 1;
+    }
+    return SRM_OK;
+}
+
+srm_status run_graph(Group &g, int steps)
+{
+    if (g.timing) return run_timed(g, steps == 1 ? 1 : g.gN_steps);
+    cudaGraphExec_t ge = steps == 1 ? g.g1 : g.gN;
+    CK(cudaGraphLaunch(ge, g.stream));
+    g.launches += g.launches_per_step * (steps == 1 ? 1 : g.gN_steps);
     return SRM_OK;
 }
 
@@ -167,108 +585,133 @@ __global__ void k_set_scale(RveDev *st, double lam)
 
 __global__ void k_set_cap(RveDev *st, int64_t cap) { st->iter_cap = cap; }
 
-// ---------------------------------------------------------------------------
-// super-step graphs
-// ---------------------------------------------------------------------------
-// kernels of one super-step: begin, binning (count, 3 scan passes, scatter,
-// stamp, in-cell sort), 3^d sweep colours, check, control
-static int64_t kernels_per_superstep(int dim) { return 1 + 7 + (dim == 3 ? 27 : 9) + 1 + 1; }
-
-static void enqueue_superstep(srm_rve *h, cudaStream_t s, const std::vector<cudaEvent_t> *ev = nullptr)
+void launch_set_cap(Group &g, size_t r, int64_t cap)
 {
-    srm::HostShape sh = h->sh;
-    sh.out_f32 = sh.f32;
-    if (ev) cudaEventRecordWithFlags((*ev)[0], s, cudaEventRecordExternal);
-    srm::launch_begin(h->d, s);
-    srm::launch_bin(h->d, sh, s);
-    if (ev) {
-        const int ncol = sh.dim == 3 ? 27 : 9;
-        for (int chi = 0; chi < ncol; chi++) {
-            cudaEventRecordWithFlags((*ev)[1 + chi], s, cudaEventRecordExternal);
-            srm::launch_sweep_colour(h->d, sh, chi, s);
-        }
-        cudaEventRecordWithFlags((*ev)[1 + ncol], s, cudaEventRecordExternal);
-        srm::launch_check(h->d, sh, s);
-        cudaEventRecordWithFlags((*ev)[2 + ncol], s, cudaEventRecordExternal);
-        srm::launch_control(h->d, s);
-        cudaEventRecordWithFlags((*ev)[3 + ncol], s, cudaEventRecordExternal);
-    } else {
-        srm::launch_sweep(h->d, sh, s);
-        srm::launch_check(h->d, sh, s);
-        srm::launch_control(h->d, s);
-    }
+    k_set_cap<<<1, 1, 0, g.stream>>>(g.m[r]->d, cap);
+    g.launches++;
 }
 
-// The graph is recorded on a private stream (recording runs nothing) and
-// launched on the caller's stream, which may be the legacy default stream.
-static srm_status capture(srm_rve *h, int steps, cudaGraphExec_t *out, bool timed = false)
-{
-    cudaGraph_t g = nullptr;
-    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < steps; i++) enqueue_superstep(h, h->cap_stream, timed ? &h->ev : nullptr);
-    CK(cudaStreamEndCapture(h->cap_stream, &g));
-    cudaError_t e = cudaGraphInstantiate(out, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(SRM_E_CUDA, std::string("graph: ") + cudaGetErrorString(e));
-    return SRM_OK;
-}
+bool idle_mode(int32_t m) { return m == srm::MODE_BEGIN || m == srm::MODE_DONE; }
 
-static srm_status pull_state(srm_rve *h);
-
-// Timing mode: one super-step per replay, with events between the stages;
-// the host waits for each replay and adds up the stage times.
-static srm_status run_timed(srm_rve *h, int steps)
+// Replays super-steps until every member is done, or until no member can
+// start a new iteration (iteration caps) -- then SRM_E_NOT_CONVERGED.
+srm_status run_group(Group &g, int64_t max_iters)
 {
-    const int ncol = h->sh.dim == 3 ? 27 : 9;
-    if (h->ev.empty()) {
-        h->ev.resize((size_t)ncol + 4);
-        for (auto &e : h->ev) CK(cudaEventCreate(&e));
+    srm_status st = pull_states(g);
+    if (st != SRM_OK) return st;
+    for (size_t r = 0; r < g.m.size(); r++)
+        if (!idle_mode(g.pin[r].mode)) return fail(SRM_E_STATE, "an RVE is inside an iteration");
+    for (size_t r = 0; r < g.m.size(); r++) {
+        const int64_t it0 = g.pin[r].iters;
+        launch_set_cap(g, r, max_iters > INT64_MAX - it0 ? INT64_MAX : it0 + max_iters);
     }
-    if (!h->gT) {
-        srm_status s = capture(h, 1, &h->gT, true);
-        if (s != SRM_OK) return s;
+    CK(cudaGetLastError());
+    int64_t last = -1;
+    const int launches_per_poll = 4;
+    for (;;) {
+        if ((st = pull_states(g)) != SRM_OK) return st;
+        bool all_done = true;
+        for (size_t r = 0; r < g.m.size(); r++) all_done = all_done && g.pin[r].mode == srm::MODE_DONE;
+        if (all_done) break;
+        const int64_t sw = total_sweeps(g);
+        if (sw == last) break;  // nothing moves: capped
+        last = sw;
+        for (int i = 0; i < launches_per_poll; i++)
+            if ((st = run_graph(g, g.gN_steps)) != SRM_OK) return st;
     }
-    for (int i = 0; i < steps; i++) {
-        const int64_t sw0 = h->pin->sweeps;
-        CK(cudaGraphLaunch(h->gT, h->stream));
-        h->launches += h->launches_per_step;
-        srm_status s = pull_state(h);
-        if (s != SRM_OK) return s;
-        if (h->pin->sweeps == sw0) continue;  // nothing ran (target reached or capped)
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
-        h->tm.ms_bin += ms;
-        for (int c = 0; c < ncol; c++) {
-            CK(cudaEventElapsedTime(&ms, h->ev[1 + c], h->ev[2 + c]));
-            h->tm.ms_sweep += ms;
-        }
-        h->tm.sweep_launches += ncol;
-        CK(cudaEventElapsedTime(&ms, h->ev[1 + ncol], h->ev[2 + ncol]));
-        h->tm.ms_check += ms;
-        if (h->pin->do_check) h->tm.check_launches += 1;
-        CK(cudaEventElapsedTime(&ms, h->ev[2 + ncol], h->ev[3 + ncol]));
-        h->tm.ms_control += ms;
-        h->tm.supersteps += 1;
-    }
-    return SRM_OK;
-}
-
-static srm_status run_graph(srm_rve *h, int steps)
-{
-    if (h->timing) return run_timed(h, steps == 1 ? 1 : h->gN_steps);
-    cudaGraphExec_t *g = steps == 1 ? &h->g1 : &h->gN;
-    if (!*g) {
-        srm_status s = capture(h, steps == 1 ? 1 : h->gN_steps, g);
-        if (s != SRM_OK) return s;
-    }
-    CK(cudaGraphLaunch(*g, h->stream));
-    h->launches += h->launches_per_step * (steps == 1 ? 1 : h->gN_steps);
+    for (size_t r = 0; r < g.m.size(); r++) launch_set_cap(g, r, INT64_MAX);
+    CK(cudaGetLastError());
+    if ((st = pull_states(g)) != SRM_OK) return st;
+    for (size_t r = 0; r < g.m.size(); r++)
+        if (g.pin[r].mode != srm::MODE_DONE)
+            return fail(SRM_E_NOT_CONVERGED, "iteration cap reached before the target volume fraction");
     return SRM_OK;
 }
 
 // ---------------------------------------------------------------------------
-// C interface
+// per-member operations (inspection and read-back)
+// ---------------------------------------------------------------------------
+srm_status member_idle(Group &g, size_t r)
+{
+    srm_status st = pull_state(g, r);
+    if (st != SRM_OK) return st;
+    if (!idle_mode(g.pin[r].mode)) return fail(SRM_E_STATE, "RVE is inside an iteration");
+    return SRM_OK;
+}
+
+srm_status member_certify(Group &g, size_t r, int64_t *overlap_pairs, double *min_gap, double *phi)
+{
+    Member &mb = *g.m[r];
+    srm_status st = member_idle(g, r);
+    if (st != SRM_OK) return st;
+    if (!mb.loaded) return fail(SRM_E_STATE, "empty slot");
+    srm::launch_inspect_bin(mb.d, mb.solo, g.stream);
+    srm::launch_pairs_count(mb.d, mb.dim, mb.n, 1, g.stream);
+    srm::launch_inspect_end(mb.d, g.stream);
+    g.launches += 1 + 7 + 1 + 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(g.pin_red, mb.h.red, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    const int64_t pairs = (int64_t)g.pin_red[1];
+    const unsigned long long key = g.pin_red[2];
+    const unsigned long long b = (key >> 63) ? (key & 0x7fffffffffffffffULL) : ~key;
+    double gap;
+    std::memcpy(&gap, &b, sizeof(gap));
+    if (overlap_pairs) *overlap_pairs = pairs;
+    if (min_gap) *min_gap = gap;
+    if (phi) *phi = phi_of(mb.dim, mb.S0, mb.V, g.pin[r].lam_P);
+    if (pairs > 0) return fail(SRM_E_CERTIFY_FAILED, "overlapping pairs in the final state");
+    return SRM_OK;
+}
+
+srm_status member_positions(Group &g, size_t r, double *xyz, double *radii)
+{
+    Member &mb = *g.m[r];
+    srm_status st = member_idle(g, r);
+    if (st != SRM_OK) return st;
+    if (!mb.loaded) return fail(SRM_E_STATE, "empty slot");
+    const size_t n = (size_t)mb.n, dim = (size_t)mb.dim;
+    if (!mb.d_xyz) {
+        mb.d_xyz = (double *)dev_alloc(g, sizeof(double) * (size_t)mb.n_cap * 3);
+        mb.d_rad = (double *)dev_alloc(g, sizeof(double) * (size_t)mb.n_cap);
+        if (!mb.d_xyz || !mb.d_rad) return fail(SRM_E_NOMEM, "read-back buffers");
+    }
+    srm::launch_gather(mb.d, mb.dim, g.f32, mb.n, mb.d_xyz, mb.d_rad, g.stream);
+    g.launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(xyz, mb.d_xyz, sizeof(double) * n * dim, cudaMemcpyDeviceToHost, g.stream));
+    if (radii) CK(cudaMemcpyAsync(radii, mb.d_rad, sizeof(double) * n, cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    return SRM_OK;
+}
+
+void fill_state(const Group &g, size_t r, srm_state_info *o)
+{
+    const RveDev &s = g.pin[r];
+    const Member &mb = *g.m[r];
+    o->dim = mb.dim;
+    o->precision = g.f32 ? SRM_PREC_F32 : SRM_PREC_F64;
+    o->n = mb.n;
+    o->lambda = s.lam_P;
+    o->lambda_t = s.lam_t;
+    o->phi = mb.loaded ? phi_of(mb.dim, mb.S0, mb.V, s.lam_P) : 0.0;
+    o->phi_t = mb.phi_t;
+    o->sweep = s.sweep;
+    o->iterations = s.iters;
+    o->accepted = s.accepted;
+    o->shaken = s.shaken;
+    o->sweeps = s.sweeps;
+    o->done = s.mode == srm::MODE_DONE;
+    for (int a = 0; a < 3; a++) o->grid[a] = s.gn[a];
+    o->kernel_launches = g.launches;
+    o->pairs_sweep = s.pairs_sweep;
+    o->pairs_check = s.pairs_check;
+    o->stage_overflow = s.stage_overflow;
+    o->stage_capacity = g.cap;
+}
+
+// ---------------------------------------------------------------------------
+// C interface: single RVE
 // ---------------------------------------------------------------------------
 extern "C" {
 
@@ -294,268 +737,31 @@ void srm_params_default(srm_params *p)
 
 const char *srm_last_error(void) { return g_err.c_str(); }
 
-srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_radii *radii,
-                    double phi_t, uint64_t seed, const srm_params *pin, void *cuda_stream,
-                    const srm_allocator *alloc)
+srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_radii *radii, double phi_t,
+                    uint64_t seed, const srm_params *p, void *cuda_stream, const srm_allocator *alloc)
 {
     g_err.clear();
-    if (!out || !box || !radii) return fail(SRM_E_ARG, "null argument");
+    if (!out) return fail(SRM_E_ARG, "null argument");
     *out = nullptr;
-    srm_params p;
-    if (pin) p = *pin;
-    else srm_params_default(&p);
-    if (dim != 2 && dim != 3) return fail(SRM_E_ARG, "dim must be 2 or 3");
-    const int64_t n = radii->n;
-    if (n < 1) return fail(SRM_E_ARG, "n must be >= 1");
-    if (n > 0x7fffffffLL) return fail(SRM_E_ARG, "n must be < 2^31");
-    for (int a = 0; a < dim; a++)
-        if (!(box[a] > 0.0)) return fail(SRM_E_ARG, "box lengths must be > 0");
-    if (!(phi_t > 0.0 && phi_t < 1.0)) return fail(SRM_E_ARG, "target phi must be in (0, 1)");
-    if (!(p.c_m > 0.0)) return fail(SRM_E_ARG, "c_m must be > 0");
-    if (!(p.c_w >= 0.0)) return fail(SRM_E_ARG, "c_w must be >= 0");
-    if (p.N_k < 1 || p.N_l < 1 || p.N_shake < 0) return fail(SRM_E_ARG, "N_k, N_l >= 1, N_shake >= 0");
-    if (p.precision != SRM_PREC_F64 && p.precision != SRM_PREC_F32)
-        return fail(SRM_E_ARG, "precision must be 32 or 64");
-    if (p.precision == SRM_PREC_F32 && !(p.guard > 0.0 && p.guard < 1e-2))
-        return fail(SRM_E_ARG, "FP32 guard must be in (0, 1e-2)");
-
-    // base radii
-    std::vector<double> r((size_t)n);
-    if (radii->kind == SRM_RADII_EXPLICIT) {
-        if (!radii->r) return fail(SRM_E_ARG, "explicit radii need r");
-        std::memcpy(r.data(), radii->r, sizeof(double) * (size_t)n);
-    } else if (radii->kind == SRM_RADII_MONO) {
-        for (auto &v : r) v = radii->mean;
-    } else if (radii->kind == SRM_RADII_LOGNORMAL) {
-        if (!(radii->mean > 0 && radii->sd >= 0 && radii->lo <= radii->hi))
-            return fail(SRM_E_ARG, "bad log-normal parameters");
-        if (inp_radii_lognormal(n, radii->mean, radii->sd, radii->lo, radii->hi, seed, r.data()))
-            return fail(SRM_E_ARG, "log-normal truncation window too narrow");
-    } else {
-        return fail(SRM_E_ARG, "unknown radii kind");
-    }
-    double rmax = 0.0;
-    for (double v : r) {
-        if (!(v > 0.0)) return fail(SRM_E_ARG, "radii must be > 0");
-        rmax = v > rmax ? v : rmax;
-    }
-
+    Prep q;
+    srm_status st = prepare(dim, box, radii, phi_t, seed, p, q);
+    if (st != SRM_OK) return st;
     srm_rve *h = new srm_rve();
-    h->stream = (cudaStream_t)cuda_stream;
-    if (alloc && alloc->alloc && alloc->free) {
-        h->alloc = *alloc;
-        h->has_alloc = true;
-    }
-    RveDev &s = h->h;
-    s.dim = dim;
-    s.prec = p.precision;
-    s.n = (int32_t)n;
-    s.N_k = p.N_k;
-    s.N_l = p.N_l;
-    s.N_shake = p.N_shake;
-    for (int a = 0; a < 3; a++) {
-        s.L[a] = a < dim ? box[a] : 1.0;
-        s.halfL[a] = 0.5 * s.L[a];
-        s.Lf[a] = (float)s.L[a];
-    }
-    s.rmax = rmax;
-    s.c_w = p.c_w;
-    s.c_m = p.c_m;
-    s.guard = (float)p.guard;
-    s.seed = seed;
-    s.iter_cap = INT64_MAX;
-    h->V = s.L[0] * s.L[1];
-    if (dim == 3) h->V = h->V * s.L[2];
-    h->S0 = base_measure(dim, r.data(), n);
-    h->phi_t = phi_t;
-    s.lam_t = p.lambda_t > 0.0 ? p.lambda_t : lam_of(dim, h->S0, h->V, phi_t);
-
-    // starting configuration
-    std::vector<double> x((size_t)n * dim);
-    double lam0 = 1.0;
-    if (p.init == SRM_INIT_EXPLICIT) {
-        if (!p.init_pos) {
-            delete h;
-            return fail(SRM_E_ARG, "explicit start needs init_pos");
-        }
-        std::memcpy(x.data(), p.init_pos, sizeof(double) * x.size());
-        for (size_t i = 0; i < x.size(); i++) {
-            const int a = (int)(i % dim);
-            if (!(x[i] >= 0.0 && x[i] < s.L[a])) {
-                delete h;
-                return fail(SRM_E_ARG, "start positions must lie in [0, L)");
-            }
-        }
-        lam0 = p.lambda0 > 0.0 ? p.lambda0 : 1.0;
-    } else if (p.init == SRM_INIT_RSA_UNIFORM || p.init == SRM_INIT_RSA_CLUSTERED) {
-        if (!(p.f0 > 0.0 && p.f0 <= phi_t)) {
-            delete h;
-            return fail(SRM_E_ARG, "f0 must be in (0, phi_t]");
-        }
-        lam0 = lam_of(dim, h->S0, h->V, p.f0);
-        std::vector<double> R0((size_t)n);
-        for (int64_t i = 0; i < n; i++) R0[(size_t)i] = lam0 * r[(size_t)i];
-        const int clustered = p.init == SRM_INIT_RSA_CLUSTERED;
-        if (inp_rsa(dim, s.L, n, R0.data(), seed, clustered, p.n_clusters, p.cluster_sigma,
-                    100000000LL, x.data())) {
-            delete h;
-            return fail(SRM_E_INIT, "random sequential addition could not place every particle");
-        }
-    } else {
-        delete h;
-        return fail(SRM_E_ARG, "unknown init kind");
-    }
-    s.lam_P = lam0;
-    s.lam_Q = lam0;
-
-    // the minimum-image search needs at least three cells of the final size
-    {
-        const double cs_t = 2.5 * (s.lam_t * rmax) + p.c_m;
-        for (int a = 0; a < dim; a++)
-            if (s.L[a] < 3.0 * cs_t) {
-                delete h;
-                return fail(SRM_E_ARG, "box narrower than three cells of size 2.5 R_max + c_m");
-            }
-    }
-
-    // capacities: the grid is finest at the smallest scale
-    h->lam_min = (lam0 < s.lam_t ? lam0 : s.lam_t) * (1.0 - 1e-9);
-    int64_t per[3];
-    const int64_t ncap = cells_for(h, h->lam_min, per);
-    if (ncap > 0x7ffffff0LL) {
-        delete h;
-        return fail(SRM_E_ARG, "too many cells (radii too small for the box)");
-    }
-    int64_t nsub = 1;
-    for (int a = 0; a < dim; a++) nsub *= per[a] / 3;
-    s.ncells_cap = (int32_t)ncap;
-    h->sh.dim = dim;
-    h->sh.n = n;
-    h->sh.ncells_cap = ncap;
-    h->sh.nsub_cap = nsub;
-    h->sh.f32 = p.precision == SRM_PREC_F32;
-    h->sh.out_f32 = h->sh.f32;
-    h->launches_per_step = kernels_per_superstep(dim);
-
-    // Staging capacity of the warp-per-cell sweep: the 95th percentile of
-    // the stencil population of the starting positions on the grid of the
-    // target scale (the coarsest grid of the run), times the part of the
-    // stencil volume within reach of the home cell, with slack.  Denser
-    // cells stage what fits and read the rest from global memory.
-    {
-        int64_t pa[3];
-        const int64_t nc = cells_for(h, s.lam_t, pa);
-        std::vector<uint32_t> occ((size_t)nc, 0u);
-        for (int64_t i = 0; i < n; i++) {
-            int64_t lin = 0, mul = 1;
-            for (int a = 0; a < dim; a++) {
-                const double wa = s.L[a] / (double)pa[a];
-                int64_t c = (int64_t)(x[(size_t)i * dim + a] / wa);
-                c = ((c % pa[a]) + pa[a]) % pa[a];
-                lin += c * mul;
-                mul *= pa[a];
-            }
-            occ[(size_t)lin]++;
-        }
-        std::vector<uint32_t> tpop;
-        tpop.reserve((size_t)n);
-        const int zr = dim == 3 ? 1 : 0;
-        for (int64_t c = 0; c < nc; c++) {
-            if (!occ[(size_t)c]) continue;
-            const int64_t cx = c % pa[0], cy = (c / pa[0]) % pa[1], cz = c / (pa[0] * pa[1]);
-            uint32_t t = 0;
-            for (int dz = -zr; dz <= zr; dz++)
-                for (int dy = -1; dy <= 1; dy++)
-                    for (int dx = -1; dx <= 1; dx++) {
-                        const int64_t ex = (cx + dx + pa[0]) % pa[0], ey = (cy + dy + pa[1]) % pa[1],
-                                      ez = (cz + dz + pa[2]) % pa[2];
-                        t += occ[(size_t)(ex + pa[0] * (ey + pa[1] * ez))];
-                    }
-            for (uint32_t k = 0; k < occ[(size_t)c]; k++) tpop.push_back(t);  // per particle
-        }
-        uint32_t t95 = 0;
-        if (!tpop.empty()) {
-            const size_t q = tpop.size() * 95 / 100;
-            std::nth_element(tpop.begin(), tpop.begin() + (ptrdiff_t)q, tpop.end());
-            t95 = tpop[q];
-        }
-        const double wt = s.L[0] / (double)pa[0];
-        const double reach = 2.0 * (2.0 * s.lam_t * rmax + 2.0 * p.c_m);
-        double frac = (wt + reach) / (3.0 * wt);
-        frac = frac > 1.0 ? 1.0 : frac;
-        frac = dim == 3 ? frac * frac * frac : frac * frac;
-        const bool f32 = p.precision == SRM_PREC_F32;
-        int64_t cap = (int64_t)(1.25 * frac * (double)t95) + 16;
-        cap = (cap + 31) / 32 * 32;
-        if (cap < 64) cap = 64;
-        h->sh.cap_sweep = (int)(cap < srm::sweep_cap_max(f32) ? cap : srm::sweep_cap_max(f32));
-        h->sh.cap_check = h->sh.cap_sweep;
-    }
-
-    // device buffers
-    bool ok = true;
-    auto A = [&](size_t bytes) -> void * {
-        void *q = dev_alloc(h, bytes);
-        if (!q) ok = false;
-        return q;
-    };
-    for (int k = 0; k < 3; k++) {
-        s.slot[k].pos = A(sizeof(double4_32a) * (size_t)n);
-        s.slot[k].rb = (double *)A(sizeof(double) * (size_t)n);
-        s.slot[k].pid = (uint32_t *)A(sizeof(uint32_t) * (size_t)n);
-        s.slot[k].cell = (uint32_t *)A(sizeof(uint32_t) * (size_t)n);
-    }
-    s.counts = (uint32_t *)A(sizeof(uint32_t) * (size_t)ncap);
-    s.cell_start = (uint32_t *)A(sizeof(uint32_t) * (size_t)(ncap + 1));
-    const int64_t parts = srm::scan_part_len((ncap > n + 1 ? ncap : n + 1));
-    s.scan_part = (uint32_t *)A(sizeof(uint32_t) * (size_t)(parts + 1));
-    s.src_cell = (uint32_t *)A(sizeof(uint32_t) * (size_t)n);
-    s.src_rank = (uint32_t *)A(sizeof(uint32_t) * (size_t)n);
-    s.flags = (uint8_t *)A((size_t)n);
-    s.pcount = (uint32_t *)A(sizeof(uint32_t) * (size_t)(n + 1));
-    s.red = (unsigned long long *)A(sizeof(unsigned long long) * 8);
-    h->d = (RveDev *)A(sizeof(RveDev));
-    double *d_x = (double *)A(sizeof(double) * x.size());
-    double *d_r = (double *)A(sizeof(double) * (size_t)n);
-    if (!ok) {
-        dev_free_all(h);
-        cudaStreamSynchronize(h->stream);
-        delete h;
-        return fail(SRM_E_NOMEM, "device allocation failed");
-    }
-    if (cudaMallocHost((void **)&h->pin, sizeof(RveDev)) != cudaSuccess ||
-        cudaMallocHost((void **)&h->pin_red, sizeof(unsigned long long) * 8) != cudaSuccess) {
-        dev_free_all(h);
-        delete h;
-        return fail(SRM_E_NOMEM, "pinned host allocation failed");
-    }
-    s.mode = s.lam_P >= s.lam_t ? srm::MODE_DONE : srm::MODE_BEGIN;
-    s.p_idx = 0;
-    s.dst_idx = 1;
-    s.sweep = p.sweep0;
-
-    srm::sweep_configure();
-    srm::check_configure();
-    srm_status st = SRM_OK;
-    auto chk = [&](cudaError_t e, const char *what) {
-        if (e != cudaSuccess && st == SRM_OK) st = fail(SRM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-    };
-    chk(cudaMemsetAsync(s.counts, 0, sizeof(uint32_t) * (size_t)ncap, h->stream), "memset");
-    chk(cudaMemsetAsync(s.red, 0, sizeof(unsigned long long) * 8, h->stream), "memset");
-    chk(cudaMemsetAsync(s.flags, 0, (size_t)n, h->stream), "memset");
-    *h->pin = s;
-    chk(cudaMemcpyAsync(h->d, h->pin, sizeof(RveDev), cudaMemcpyHostToDevice, h->stream), "state");
-    chk(cudaMemcpyAsync(d_x, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice, h->stream), "x");
-    chk(cudaMemcpyAsync(d_r, r.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream), "r");
-    srm::launch_import(h->d, h->sh, d_x, d_r, h->stream);
-    h->launches += 2;
-    chk(cudaGetLastError(), "import");
-    chk(cudaStreamSynchronize(h->stream), "sync");
-    // record the replayed graphs now, so that no later call pays for it
-    if (st == SRM_OK) st = capture(h, 1, &h->g1);
-    if (st == SRM_OK) st = capture(h, h->gN_steps, &h->gN);
+    Group &g = h->g;
+    group_setup(g, cuda_stream, alloc);
+    g.f32 = q.p.precision == SRM_PREC_F32;
+    g.cap = std::min(q.cap_est, srm::sweep_cap_max(g.f32));
+    Member *mb = new Member();
+    mb->dim = q.dim;
+    g.m.push_back(mb);
+    if ((st = member_alloc(g, *mb, q.n, q.ncells_need, q.nsub_need)) == SRM_OK &&
+        (st = member_load(g, *mb, q)) == SRM_OK)
+        st = group_finalize(g);
     if (st != SRM_OK) {
-        srm_destroy(h);
+        const std::string msg = g_err;
+        group_free(g);
+        delete h;
+        g_err = msg;
         return st;
     }
     *out = h;
@@ -565,51 +771,41 @@ srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_r
 void srm_destroy(srm_rve *h)
 {
     if (!h) return;
-    cudaStreamSynchronize(h->stream);
-    if (h->g1) cudaGraphExecDestroy(h->g1);
-    if (h->gN) cudaGraphExecDestroy(h->gN);
-    if (h->gT) cudaGraphExecDestroy(h->gT);
-    for (auto e : h->ev) cudaEventDestroy(e);
-    dev_free_all(h);
-    cudaStreamSynchronize(h->stream);
-    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    if (h->pin) cudaFreeHost(h->pin);
-    if (h->pin_red) cudaFreeHost(h->pin_red);
+    group_free(h->g);
     delete h;
-}
-
-static void fill_step(srm_rve *h, srm_step_info *o, int32_t result)
-{
-    const RveDev &s = *h->pin;
-    o->result = result;
-    o->k_sweeps = s.it_k;
-    o->shake_sweeps = s.it_shake;
-    o->overlapping = s.it_overlap;
-    o->phi = phi_of(h, s.lam_P);
-    o->lambda = s.lam_P;
-    o->sweep = s.sweep;
 }
 
 srm_status srm_step(srm_rve *h, srm_step_info *out)
 {
     if (!h) return fail(SRM_E_ARG, "null handle");
-    srm_status st = pull_state(h);
+    Group &g = h->g;
+    srm_status st = pull_state(g, 0);
     if (st != SRM_OK) return st;
-    if (h->pin->mode == srm::MODE_DONE) {
-        if (out) fill_step(h, out, 2);
+    const Member &mb = *g.m[0];
+    auto fill = [&](int32_t result) {
+        if (!out) return;
+        const RveDev &s = g.pin[0];
+        out->result = result;
+        out->k_sweeps = s.it_k;
+        out->shake_sweeps = s.it_shake;
+        out->overlapping = s.it_overlap;
+        out->phi = phi_of(mb.dim, mb.S0, mb.V, s.lam_P);
+        out->lambda = s.lam_P;
+        out->sweep = s.sweep;
+    };
+    if (g.pin[0].mode == srm::MODE_DONE) {
+        fill(2);
         return SRM_OK;
     }
-    if (h->pin->mode != srm::MODE_BEGIN) return fail(SRM_E_STATE, "handle is inside an iteration");
-    const int64_t it0 = h->pin->iters;
+    if (g.pin[0].mode != srm::MODE_BEGIN) return fail(SRM_E_STATE, "handle is inside an iteration");
+    const int64_t it0 = g.pin[0].iters;
     for (;;) {
-        if ((st = run_graph(h, 1)) != SRM_OK) return st;
-        if ((st = pull_state(h)) != SRM_OK) return st;
-        const int32_t m = h->pin->mode;
-        if ((m == srm::MODE_BEGIN || m == srm::MODE_DONE) && h->pin->iters > it0) break;
-        if (!h->pin->active && h->pin->iters == it0)
-            return fail(SRM_E_STATE, "no iteration could start");
+        if ((st = run_graph(g, 1)) != SRM_OK) return st;
+        if ((st = pull_state(g, 0)) != SRM_OK) return st;
+        if (idle_mode(g.pin[0].mode) && g.pin[0].iters > it0) break;
+        if (!g.pin[0].active && g.pin[0].iters == it0) return fail(SRM_E_STATE, "no iteration could start");
     }
-    if (out) fill_step(h, out, h->pin->it_result);
+    fill(g.pin[0].it_result);
     return SRM_OK;
 }
 
@@ -617,106 +813,61 @@ srm_status srm_run_to_target(srm_rve *h, int64_t max_iters, srm_run_info *out)
 {
     if (!h) return fail(SRM_E_ARG, "null handle");
     if (max_iters < 0) return fail(SRM_E_ARG, "max_iters must be >= 0");
-    srm_status st = pull_state(h);
-    if (st != SRM_OK) return st;
-    const int32_t m0 = h->pin->mode;
-    if (m0 != srm::MODE_BEGIN && m0 != srm::MODE_DONE) return fail(SRM_E_STATE, "handle is inside an iteration");
-    const int64_t it0 = h->pin->iters;
-    const int64_t cap = max_iters > INT64_MAX - it0 ? INT64_MAX : it0 + max_iters;
-    k_set_cap<<<1, 1, 0, h->stream>>>(h->d, cap);
-    h->launches++;
-    CK(cudaGetLastError());
-    int64_t last_sweeps = -1;
-    const int launches_per_poll = 4;
-    while (h->pin->mode != srm::MODE_DONE) {
-        for (int i = 0; i < launches_per_poll; i++)
-            if ((st = run_graph(h, h->gN_steps)) != SRM_OK) return st;
-        if ((st = pull_state(h)) != SRM_OK) return st;
-        if (h->pin->mode == srm::MODE_BEGIN && h->pin->iters >= cap && h->pin->sweeps == last_sweeps) break;
-        last_sweeps = h->pin->sweeps;
-    }
-    k_set_cap<<<1, 1, 0, h->stream>>>(h->d, INT64_MAX);
-    h->launches++;
-    CK(cudaGetLastError());
-    if ((st = pull_state(h)) != SRM_OK) return st;
+    Group &g = h->g;
+    const srm_status st = run_group(g, max_iters);
+    if (st != SRM_OK && st != SRM_E_NOT_CONVERGED) return st;
     if (out) {
-        const RveDev &s = *h->pin;
+        const RveDev &s = g.pin[0];
+        const Member &mb = *g.m[0];
         out->iterations = s.iters;
         out->accepted = s.accepted;
         out->shaken = s.shaken;
         out->sweeps = s.sweeps;
-        out->phi = phi_of(h, s.lam_P);
+        out->phi = phi_of(mb.dim, mb.S0, mb.V, s.lam_P);
         out->lambda = s.lam_P;
         out->sweep = s.sweep;
     }
-    if (h->pin->mode != srm::MODE_DONE)
-        return fail(SRM_E_NOT_CONVERGED, "iteration cap reached before the target volume fraction");
-    return SRM_OK;
-}
-
-static srm_status check_idle(srm_rve *h)
-{
-    srm_status st = pull_state(h);
-    if (st != SRM_OK) return st;
-    if (h->pin->mode != srm::MODE_BEGIN && h->pin->mode != srm::MODE_DONE)
-        return fail(SRM_E_STATE, "handle is inside an iteration");
-    return SRM_OK;
+    return st;
 }
 
 srm_status srm_certify(srm_rve *h, int64_t *overlap_pairs, double *min_gap, double *phi)
 {
     if (!h) return fail(SRM_E_ARG, "null handle");
-    srm_status st = check_idle(h);
-    if (st != SRM_OK) return st;
-    srm::launch_inspect_bin(h->d, h->sh, h->stream);
-    srm::launch_pairs_count(h->d, h->sh, 1, h->stream);
-    srm::launch_inspect_end(h->d, h->stream);
-    h->launches += 1 + 7 + 1 + 1;
-    CK(cudaGetLastError());
-    if ((st = pull_state(h)) != SRM_OK) return st;
-    CK(cudaMemcpyAsync(h->pin_red, h->h.red, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost,
-                       h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    const int64_t pairs = (int64_t)h->pin_red[1];
-    unsigned long long key = h->pin_red[2];
-    const unsigned long long b = (key >> 63) ? (key & 0x7fffffffffffffffULL) : ~key;
-    double gap;
-    std::memcpy(&gap, &b, sizeof(gap));
-    if (overlap_pairs) *overlap_pairs = pairs;
-    if (min_gap) *min_gap = gap;
-    if (phi) *phi = phi_of(h, h->pin->lam_P);
-    if (pairs > 0) return fail(SRM_E_CERTIFY_FAILED, "overlapping pairs in the final state");
-    return SRM_OK;
+    return member_certify(h->g, 0, overlap_pairs, min_gap, phi);
 }
 
 srm_status srm_overlap_pairs(srm_rve *h, int64_t *ij, int64_t cap, int64_t *n)
 {
     if (!h || !n || (cap > 0 && !ij)) return fail(SRM_E_ARG, "null argument");
-    srm_status st = check_idle(h);
+    Group &g = h->g;
+    Member &mb = *g.m[0];
+    srm_status st = member_idle(g, 0);
     if (st != SRM_OK) return st;
-    srm::launch_inspect_bin(h->d, h->sh, h->stream);
-    srm::launch_pairs_count(h->d, h->sh, 0, h->stream);
-    srm::launch_scan(h->d, 1, h->sh.n, h->stream);
-    h->launches += 1 + 7 + 1 + 3 + 2;
+    srm::launch_inspect_bin(mb.d, mb.solo, g.stream);
+    srm::launch_pairs_count(mb.d, mb.dim, mb.n, 0, g.stream);
+    srm::launch_scan(mb.solo, 1, g.stream);
+    g.launches += 1 + 7 + 1 + 3;
     CK(cudaGetLastError());
     uint32_t total = 0;
-    CK(cudaMemcpyAsync(h->pin_red, h->h.pcount + h->sh.n, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                       h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    std::memcpy(&total, h->pin_red, sizeof(uint32_t));
-    if ((int64_t)total > h->d_ij_cap) {
-        void *q = dev_alloc(h, sizeof(long long) * 2 * (size_t)total);
+    CK(cudaMemcpyAsync(g.pin_red, mb.h.pcount + mb.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    std::memcpy(&total, g.pin_red, sizeof(uint32_t));
+    if ((int64_t)total > mb.d_ij_cap) {
+        void *q = dev_alloc(g, sizeof(long long) * 2 * (size_t)total);
         if (!q) return fail(SRM_E_NOMEM, "pair buffer");
-        h->d_ij = (long long *)q;
-        h->d_ij_cap = total;
+        mb.d_ij = (long long *)q;
+        mb.d_ij_cap = total;
     }
-    if (total > 0) srm::launch_pairs_fill(h->d, h->sh, h->d_ij, h->stream);
-    srm::launch_inspect_end(h->d, h->stream);
+    if (total > 0) {
+        srm::launch_pairs_fill(mb.d, mb.dim, mb.n, mb.d_ij, g.stream);
+        g.launches++;
+    }
+    srm::launch_inspect_end(mb.d, g.stream);
+    g.launches++;
     CK(cudaGetLastError());
     const int64_t m = (int64_t)total < cap ? (int64_t)total : cap;
-    if (m > 0)
-        CK(cudaMemcpyAsync(ij, h->d_ij, sizeof(long long) * 2 * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    if (m > 0) CK(cudaMemcpyAsync(ij, mb.d_ij, sizeof(long long) * 2 * (size_t)m, cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
     *n = total;
     return SRM_OK;
 }
@@ -724,93 +875,62 @@ srm_status srm_overlap_pairs(srm_rve *h, int64_t *ij, int64_t cap, int64_t *n)
 srm_status srm_positions(srm_rve *h, double *xyz, double *radii)
 {
     if (!h || !xyz) return fail(SRM_E_ARG, "null argument");
-    srm_status st = check_idle(h);
-    if (st != SRM_OK) return st;
-    const size_t n = (size_t)h->sh.n, dim = (size_t)h->sh.dim;
-    if (!h->d_xyz) {
-        h->d_xyz = (double *)dev_alloc(h, sizeof(double) * n * dim);
-        h->d_rad = (double *)dev_alloc(h, sizeof(double) * n);
-        if (!h->d_xyz || !h->d_rad) return fail(SRM_E_NOMEM, "read-back buffers");
-    }
-    srm::launch_gather(h->d, h->sh, h->d_xyz, h->d_rad, h->stream);
-    h->launches++;
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(xyz, h->d_xyz, sizeof(double) * n * dim, cudaMemcpyDeviceToHost, h->stream));
-    if (radii) CK(cudaMemcpyAsync(radii, h->d_rad, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    return SRM_OK;
+    return member_positions(h->g, 0, xyz, radii);
 }
 
 srm_status srm_sweep(srm_rve *h, int32_t count, int64_t *moved)
 {
     if (!h || count < 0) return fail(SRM_E_ARG, "bad argument");
-    srm_status st = check_idle(h);
+    Group &g = h->g;
+    srm_status st = member_idle(g, 0);
     if (st != SRM_OK) return st;
-    if (h->pin->lam_P < h->lam_min) return fail(SRM_E_ARG, "scale below the grid capacity");
-    const int32_t resume = h->pin->mode;
+    if (g.pin[0].lam_P < g.m[0]->lam_min) return fail(SRM_E_ARG, "scale below the grid capacity");
+    const int32_t resume = g.pin[0].mode;
     for (int32_t c = 0; c < count; c++) {
-        k_set_mode<<<1, 1, 0, h->stream>>>(h->d, srm::MODE_SWEEP, resume);
-        h->launches++;
+        k_set_mode<<<1, 1, 0, g.stream>>>(g.m[0]->d, srm::MODE_SWEEP, resume);
+        g.launches++;
         CK(cudaGetLastError());
-        if ((st = run_graph(h, 1)) != SRM_OK) return st;
+        if ((st = run_graph(g, 1)) != SRM_OK) return st;
     }
-    if ((st = pull_state(h)) != SRM_OK) return st;
-    if (moved) *moved = h->pin->moved_last;
+    if ((st = pull_state(g, 0)) != SRM_OK) return st;
+    if (moved) *moved = g.pin[0].moved_last;
     return SRM_OK;
 }
 
 srm_status srm_set_scale(srm_rve *h, double lambda)
 {
     if (!h) return fail(SRM_E_ARG, "null handle");
-    if (!(lambda >= h->lam_min)) return fail(SRM_E_ARG, "scale below the grid capacity of this handle");
-    srm_status st = check_idle(h);
+    Group &g = h->g;
+    if (!(lambda >= g.m[0]->lam_min)) return fail(SRM_E_ARG, "scale below the grid capacity of this handle");
+    srm_status st = member_idle(g, 0);
     if (st != SRM_OK) return st;
-    k_set_scale<<<1, 1, 0, h->stream>>>(h->d, lambda);
-    h->launches++;
+    k_set_scale<<<1, 1, 0, g.stream>>>(g.m[0]->d, lambda);
+    g.launches++;
     CK(cudaGetLastError());
-    return pull_state(h);
+    return pull_state(g, 0);
 }
 
 srm_status srm_get_state(srm_rve *h, srm_state_info *o)
 {
     if (!h || !o) return fail(SRM_E_ARG, "null argument");
-    srm_status st = pull_state(h);
+    srm_status st = pull_state(h->g, 0);
     if (st != SRM_OK) return st;
-    const RveDev &s = *h->pin;
-    o->dim = s.dim;
-    o->precision = s.prec;
-    o->n = s.n;
-    o->lambda = s.lam_P;
-    o->lambda_t = s.lam_t;
-    o->phi = phi_of(h, s.lam_P);
-    o->phi_t = h->phi_t;
-    o->sweep = s.sweep;
-    o->iterations = s.iters;
-    o->accepted = s.accepted;
-    o->shaken = s.shaken;
-    o->sweeps = s.sweeps;
-    o->done = s.mode == srm::MODE_DONE;
-    for (int a = 0; a < 3; a++) o->grid[a] = s.gn[a];
-    o->kernel_launches = h->launches;
-    o->pairs_sweep = s.pairs_sweep;
-    o->pairs_check = s.pairs_check;
-    o->stage_overflow = s.stage_overflow;
-    o->stage_capacity = h->sh.cap_sweep;
+    fill_state(h->g, 0, o);
     return SRM_OK;
 }
 
 srm_status srm_set_timing(srm_rve *h, int32_t on)
 {
     if (!h) return fail(SRM_E_ARG, "null handle");
-    h->timing = on != 0;
-    std::memset(&h->tm, 0, sizeof(h->tm));
+    h->g.timing = on != 0;
+    std::memset(&h->g.tm, 0, sizeof(h->g.tm));
     return SRM_OK;
 }
 
 srm_status srm_get_timings(srm_rve *h, srm_timings *out)
 {
     if (!h || !out) return fail(SRM_E_ARG, "null argument");
-    *out = h->tm;
+    *out = h->g.tm;
     return SRM_OK;
 }
 

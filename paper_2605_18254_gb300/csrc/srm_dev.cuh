@@ -76,8 +76,46 @@ struct RveDev {
     // work counters: candidate pairs examined by the sweep and by the check
     unsigned long long pairs_sweep, pairs_check;
     unsigned long long stage_overflow;  // cells whose culled stencil exceeded the staging capacity
-    uint32_t wq[27];                    // per-colour work counters of the current sweep
 };
+
+// A group of RVEs advanced by the same launches (one RVE for a single
+// handle, many for a batch).  Kernels indexed by particles, cells or scan
+// tiles run one grid over all RVEs: each RVE owns a contiguous range of
+// blocks (offsets below, fixed by the RVE's capacities), so that a block
+// serves one RVE.  The sweep hands out (RVE, cell) work items from one
+// counter per colour.
+struct BatchDev {
+    int32_t B;
+    int32_t pad;
+    RveDev **rv;      // [B]
+    int32_t *blk_p;   // [B+1] first block of each RVE, particle-indexed launches
+    int32_t *blk_c;   // [B+1] first block of each RVE, cell-indexed launches
+    int32_t *tile_c;  // [B+1] first scan tile of each RVE over its cells
+    int32_t *tile_n;  // [B+1] first scan tile of each RVE over its particles
+    int32_t *sub;     // [B+1] first sweep work item of each RVE (cells of one colour)
+    uint32_t wq[27];  // sweep work counters, one per colour
+};
+
+// Largest r with off[r] <= x (off non-decreasing, off[0] = 0).
+__device__ __forceinline__ int find_seg(const int32_t *off, int B, int x)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// RVE served by this block (all threads of the block must call it).
+__device__ __forceinline__ int block_rve(const int32_t *off, int B)
+{
+    __shared__ int r_sh;
+    if (threadIdx.x == 0) r_sh = find_seg(off, B, (int)blockIdx.x);
+    __syncthreads();
+    return r_sh;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

@@ -7,39 +7,46 @@
 namespace srm {
 
 struct RveDev;
+struct BatchDev;
 
-// Sizes fixed at creation; the kernels read everything that changes between
-// iterations (grid, scale, buffer roles) from the device state, so that a
-// captured sequence of launches stays valid for the whole run.
-struct HostShape {
-    int dim;
-    int64_t n;
-    int64_t ncells_cap;  // largest number of cells of any iteration
-    int64_t nsub_cap;    // largest number of cells of one colour
-    bool f32;            // arithmetic of the working copies (input format of binning)
-    bool out_f32;        // format written by binning (false: absolute binary64)
-    int cap_sweep;       // candidates a warp stages in shared memory (sweep)
-    int cap_check;       // same for the check kernel
+// Launch shape of a group of RVEs (one RVE, or a batch).  The kernels read
+// everything that changes between iterations (grid, scale, buffer roles)
+// from the device state, so a captured sequence of launches stays valid for
+// the whole run.
+struct BatchShape {
+    BatchDev *d;        // device descriptor
+    int B;              // RVEs
+    int blocks_p;       // blocks of particle-indexed launches (256 threads)
+    int blocks_c;       // blocks of cell-indexed launches (256 threads)
+    int tiles_c;        // scan tiles over cells
+    int tiles_n;        // scan tiles over particles
+    int64_t sub_total;  // sweep work items per colour (sum of colour-cell capacities)
+    bool f32;           // arithmetic of the working copies
+    bool has3d;         // some RVE is 3D (27 colours), else 9
+    int cap;            // candidates a sweep warp stages in shared memory
 };
 
-void launch_begin(RveDev *d_st, cudaStream_t s);
-void launch_control(RveDev *d_st, cudaStream_t s);
-void launch_bin(RveDev *d_st, const HostShape &sh, cudaStream_t s);
-void launch_scan(RveDev *d_st, int which, int64_t max_len, cudaStream_t s);
+void launch_begin(const BatchShape &b, cudaStream_t s);
+void launch_control(const BatchShape &b, cudaStream_t s);
+void launch_bin(const BatchShape &b, bool in32, bool out32, cudaStream_t s);
+void launch_scan(const BatchShape &b, int which, cudaStream_t s);
 int64_t scan_part_len(int64_t max_len);
-void launch_sweep(RveDev *d_st, const HostShape &sh, cudaStream_t s);
+int scan_tile();
+void launch_sweep(const BatchShape &b, cudaStream_t s);
+void launch_sweep_colour(const BatchShape &b, int chi, cudaStream_t s);
 void sweep_configure();
 int sweep_cap_max(bool f32);
 int check_cap_max(bool f32);
-void launch_sweep_colour(RveDev *d_st, const HostShape &sh, int chi, cudaStream_t s);
-void launch_check(RveDev *d_st, const HostShape &sh, cudaStream_t s);
+void launch_check(const BatchShape &b, cudaStream_t s);
 void check_configure();
-void launch_inspect_bin(RveDev *d_st, const HostShape &sh, cudaStream_t s);
+
+// single RVE
+void launch_inspect_bin(RveDev *d_st, const BatchShape &solo, cudaStream_t s);
 void launch_inspect_end(RveDev *d_st, cudaStream_t s);
-void launch_pairs_count(RveDev *d_st, const HostShape &sh, int want_gap, cudaStream_t s);
-void launch_pairs_fill(RveDev *d_st, const HostShape &sh, long long *ij, cudaStream_t s);
-void launch_gather(RveDev *d_st, const HostShape &sh, double *xyz, double *rad, cudaStream_t s);
-void launch_import(RveDev *d_st, const HostShape &sh, const double *xyz, const double *rb,
+void launch_pairs_count(RveDev *d_st, int dim, int64_t n, int want_gap, cudaStream_t s);
+void launch_pairs_fill(RveDev *d_st, int dim, int64_t n, long long *ij, cudaStream_t s);
+void launch_gather(RveDev *d_st, int dim, bool f32, int64_t n, double *xyz, double *rad, cudaStream_t s);
+void launch_import(RveDev *d_st, int dim, bool f32, int64_t n, const double *xyz, const double *rb,
                    cudaStream_t s);
 
 }  // namespace srm

@@ -40,6 +40,7 @@ STRUCTS = {
     "srm_run_info": srm.srm_run_info,
     "srm_state_info": srm.srm_state_info,
     "srm_timings": srm.srm_timings,
+    "srm_job": srm.srm_job,
 }
 
 
