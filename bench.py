@@ -353,6 +353,161 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched ensemble: many RVEs of uneven size and dimension in one batch
+# ---------------------------------------------------------------------------
+def _place_worker(args):
+    import srm_inputs
+    dim, n, r0, seed = args
+    import numpy as np
+    return srm_inputs.rsa(dim, (1.0,) * dim, np.full(n, r0), seed)
+
+
+def run_ensemble(args, rank, world, local_rank):
+    """256 RVEs (half disks, half spheres, N log-uniform 1e3..1e5, targets
+    uniform 0.30..0.55, seeds 0..255) advanced by the same launches; a step
+    runs the whole batch to its targets and certifies every member."""
+    import multiprocessing as mp
+    import numpy as np
+    import srm_inputs
+    count = args.ensemble_count
+    ws = srm_inputs.ensemble(count=count, seed0=1000 * rank)
+    import torch
+    import paper_2605_18254_gb300 as srm
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    jobs = [srm.make_job(w.dim, w.box, w.radii, w.target_phi, w.seed, c_m=w.c_m, c_w=w.c_w,
+                         precision=args.precision, init="explicit", positions=w.x) for w in ws]
+    n_total = sum(w.n for w in ws)
+
+    def one_step():
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        b = srm.Batch(jobs, stream=stream.cuda_stream)
+        e[1].record(stream)
+        ok = b.run(args.max_iters)
+        cert = [b.certify(i) for i in range(len(ws))]
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        sweeps = [b.state(i)["sweeps"] for i in range(len(ws))]
+        launches = b.state(0)["kernel_launches"]
+        b.close()
+        upd = float(sum(w.n * s for w, s in zip(ws, sweeps)))
+        return dict(dev_s=e[1].elapsed_time(e[2]) / 1e3, e2e_s=e[0].elapsed_time(e[2]) / 1e3, upd=upd,
+                    ok=ok and all(c[0] == 0 and abs(c[2] - w.target_phi) < 1e-9 for c, w in zip(cert, ws)),
+                    launches=launches, max_sweeps=max(sweeps))
+
+    for _ in range(args.warmup):
+        one_step()
+    res = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            res.append(one_step())
+    dev = sum(r["dev_s"] for r in res)
+    e2e = sum(r["e2e_s"] for r in res)
+    upd = sum(r["upd"] for r in res)
+    if rank != 0:
+        return
+    line = {
+        "metric": "particle-updates/s, batched ensemble of RVEs", "value": upd / dev, "unit": "particle-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+        "config": {"workload": f"ensemble: {count} RVEs, first half 2D disks, second half 3D spheres, N "
+                               f"log-uniform in [1e3, 1e5] (total {n_total}), targets uniform in [0.30, 0.55], "
+                               "monodisperse, RSA start at 0.1, seeds 0..255, one batch (every kernel serves "
+                               "all RVEs), captured graph",
+                   "rves": count, "particles": n_total, "stage_capacity": "from the densest job",
+                   "l2": "256 MiB buffer written between timed steps (L2 flushed)"},
+        "time_to_target_s": dev / args.steps, "certified": all(r["ok"] for r in res),
+        "e2e": {"value": upd / e2e, "unit": "particle-updates/s",
+                "h2d_bytes_per_step": int(sum(w.n * (w.dim + 1) * 8 for w in ws)), "d2h_bytes_per_step": 0},
+        "gpu_launches": int(sum(r["launches"] for r in res)),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving: one 1e7-sphere job beside a Poisson stream of smaller jobs
+# ---------------------------------------------------------------------------
+def run_serve(args, rank, world, local_rank):
+    """The 1e7-sphere RVE (unit cube, target 0.30) submitted to the serving
+    loop beside a Poisson stream of 2D/3D jobs (N log-uniform 1e4..1e6,
+    targets 0.30..0.50), arrival rate about 70% of the measured capacity of
+    the small-job pool; p50/p99 time-to-target and throughput."""
+    import math
+    import multiprocessing as mp
+    import numpy as np
+    import srm_inputs
+    n_jobs = args.serve_jobs
+    rng = np.random.default_rng(5 + 1000 * rank)
+    specs = []
+    for i in range(n_jobs):
+        dim = 2 if rng.random() < 0.5 else 3
+        n = int(math.floor(1e4 * 100.0 ** rng.random()))
+        phi = 0.30 + 0.20 * rng.random()
+        r_t = math.sqrt(phi / (n * math.pi)) if dim == 2 else (phi * 3.0 / (4.0 * math.pi * n)) ** (1 / 3)
+        specs.append((dim, n, phi, r_t, r_t * (0.1 / phi) ** (1.0 / dim), 2000 + i))
+    big_n = args.serve_big
+    big_rt = (0.30 * 3.0 / (4.0 * math.pi * big_n)) ** (1 / 3)
+    big_r0 = big_rt * (0.1 / 0.30) ** (1 / 3)
+    # starting configurations are placed ahead of time, in parallel on the host
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 4)) as pool:
+        xs = pool.map(_place_worker, [(d, n, r0, sd) for d, n, _, _, r0, sd in specs] + [(3, big_n, big_r0, 5)])
+    import torch
+    import paper_2605_18254_gb300 as srm
+    from paper_2605_18254_gb300 import serve
+    torch.cuda.set_device(local_rank)
+
+    def job(i):
+        d, n, phi, r_t, r0, sd = specs[i]
+        return srm.make_job(d, (1.0, 1.0, 1.0), np.full(n, r0), phi, sd, c_m=0.1 * r_t, c_w=0.01,
+                            precision=args.precision, init="explicit", positions=xs[i])
+
+    big_job = srm.make_job(3, (1.0, 1.0, 1.0), np.full(big_n, big_r0), 0.30, 5, c_m=0.1 * big_rt, c_w=0.01,
+                           precision=args.precision, init="explicit", positions=xs[-1])
+    big_cells = srm.srm_job_footprint(big_job[0])[1]
+    small_cells = 0
+    for i in range(n_jobs):
+        j = job(i)  # keep the arrays the job points to alive while it is used
+        small_cells = max(small_cells, srm.srm_job_footprint(j[0])[1])
+    pools = [serve.PoolSpec(slots=args.serve_slots, max_particles=1_000_000, max_cells=small_cells),
+             serve.PoolSpec(slots=1, max_particles=big_n, max_cells=big_cells)]
+    server = serve.Server(pools, precision=args.precision, advance=16)
+    # capacity of the small-job pool: a burst of jobs all arriving at t = 0
+    calib = [serve.Request(rid=i, arrival=0.0, job=job(i)) for i in range(min(16, n_jobs))]
+    done, wall = server.run(calib)
+    rate = 0.7 * len(done) / wall
+    reqs = serve.poisson_stream(n_jobs, rate, 5, lambda i, r: job(i))
+    reqs.append(serve.Request(rid=n_jobs, arrival=0.0, job=big_job))
+    with ClockSampler(local_rank) as clk:
+        done, wall = server.run(reqs)
+    server.close()
+    summ = serve.summarize(done, wall)
+    big = [r for r in done if r.rid == n_jobs][0]
+    line = {
+        "metric": "p50/p99 time-to-target and particle-updates/s under continuous batching",
+        "value": summ["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+        "config": {"workload": f"serving: 1 RVE of {big_n} 3D spheres (unit cube, target 0.30) submitted at t=0 "
+                               f"beside {n_jobs} jobs (2D/3D, N log-uniform 1e4..1e6, targets 0.30..0.50) "
+                               f"arriving as a Poisson stream at {rate:.2f} jobs/s (70% of the measured "
+                               "capacity of the small-job pool); pools: "
+                               f"{args.serve_slots} slots of 1e6 particles + 1 slot of {big_n}, each pool one batch "
+                               "on its own stream"},
+        "serving": summ, "big_job_time_to_target_s": big.finished - big.arrival,
+        "big_job_sweeps": big.sweeps, "arrival_rate_jobs_per_s": rate,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,6 +520,10 @@ def main():
     ap.add_argument("--timing-iters", type=int, default=20)
     ap.add_argument("--compare-fp64", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble-count", type=int, default=256)
+    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-big", type=int, default=10_000_000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -378,7 +537,12 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "ensemble":
+            run_ensemble(args, rank, world, local_rank)
+        elif args.workload == "serve":
+            run_serve(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

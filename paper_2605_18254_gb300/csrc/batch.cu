@@ -16,10 +16,10 @@
 
 namespace {
 
-srm_status job_prepare(const srm_job *job, Prep &q)
+srm_status job_prepare(const srm_job *job, Prep &q, bool place = true)
 {
     if (!job) return fail(SRM_E_ARG, "null job");
-    return prepare(job->dim, job->box, &job->radii, job->phi_t, job->seed, &job->params, q);
+    return prepare(job->dim, job->box, &job->radii, job->phi_t, job->seed, &job->params, q, place);
 }
 
 bool valid_slot(const srm_batch *b, int32_t slot) { return b && slot >= 0 && (size_t)slot < b->g.m.size(); }
@@ -98,7 +98,7 @@ srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_
 srm_status srm_job_footprint(const srm_job *job, int64_t *particles, int64_t *cells)
 {
     Prep q;
-    srm_status st = job_prepare(job, q);
+    srm_status st = job_prepare(job, q, false);
     if (st != SRM_OK) return st;
     if (particles) *particles = q.n;
     if (cells) *cells = q.ncells_need;

@@ -101,6 +101,76 @@ __global__ void k_control(BatchDev *bd)
     }
 }
 
+// Work plan of the sweep for this super-step: offsets of the colour cells of
+// the RVEs at work (all of them for colours 0..8, the 3D ones for 9..26), so
+// that finished RVEs of a batch cost nothing in the sweep.  One block.
+__global__ void __launch_bounds__(1024) k_plan(BatchDev *bd)
+{
+    const int B = bd->B;
+    __shared__ int32_t carry[2];
+    if (threadIdx.x == 0) {
+        carry[0] = 0;
+        carry[1] = 0;
+    }
+    __syncthreads();
+    for (int base = 0; base < B; base += blockDim.x) {
+        const int r = base + threadIdx.x;
+        int32_t w = 0, w3 = 0;
+        if (r < B) {
+            const RveDev *st = bd->rv[r];
+            if (st->active) {
+                w = st->nsub;
+                w3 = st->dim == 3 ? st->nsub : 0;
+            }
+        }
+        // block-wide inclusive scans of w and w3
+        __shared__ int32_t ws[32], ws3[32];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int32_t x = w, x3 = w3;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o), y3 = __shfl_up_sync(0xffffffffu, x3, o);
+            if (lane >= o) {
+                x += y;
+                x3 += y3;
+            }
+        }
+        if (lane == 31) {
+            ws[wid] = x;
+            ws3[wid] = x3;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = blockDim.x >> 5;
+            int32_t t = lane < nw ? ws[lane] : 0, t3 = lane < nw ? ws3[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, t, o), y3 = __shfl_up_sync(0xffffffffu, t3, o);
+                if (lane >= o) {
+                    t += y;
+                    t3 += y3;
+                }
+            }
+            ws[lane] = t;
+            ws3[lane] = t3;
+        }
+        __syncthreads();
+        const int32_t before = wid ? ws[wid - 1] : 0, before3 = wid ? ws3[wid - 1] : 0;
+        if (r < B) {
+            bd->act[r] = carry[0] + before + x - w;
+            bd->act3[r] = carry[1] + before3 + x3 - w3;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) {
+            carry[0] += before + x;
+            carry[1] += before3 + x3;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bd->act[B] = carry[0];
+        bd->act3[B] = carry[1];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Binning.  The source slot (P or the previous working copy) is read in its
 // stored order; each particle gets its cell and a rank from an atomic
@@ -449,7 +519,11 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(BatchDev *bd, int which)
 // ---------------------------------------------------------------------------
 static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-void launch_begin(const BatchShape &b, cudaStream_t s) { k_begin<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d); }
+void launch_begin(const BatchShape &b, cudaStream_t s)
+{
+    k_begin<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d);
+    k_plan<<<1, 1024, 0, s>>>(b.d);
+}
 void launch_control(const BatchShape &b, cudaStream_t s) { k_control<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d); }
 
 void launch_scan(const BatchShape &b, int which, cudaStream_t s)

@@ -342,18 +342,19 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(BatchDev *bd, int chi, 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
     const int B = bd->B;
-    const int total = bd->sub[B];
+    const int32_t *off = chi < 9 ? bd->act : bd->act3;  // RVEs at work with this colour
+    const int total = off[B];
     for (;;) {
         int tg = 0, r = 0;
         if (lane == 0) {
             tg = (int)atomicAdd(&bd->wq[chi], 1u);
-            if (tg < total) r = find_seg(bd->sub, B, tg);
+            if (tg < total) r = find_seg(off, B, tg);
         }
         tg = __shfl_sync(0xffffffffu, tg, 0);
         if (tg >= total) break;
         r = __shfl_sync(0xffffffffu, r, 0);
         RveDev *st = bd->rv[r];
-        const int t = tg - bd->sub[r];
+        const int t = tg - off[r];
         if (!st->active || t >= st->nsub) continue;
         int moved = 0;
         unsigned examined = 0;

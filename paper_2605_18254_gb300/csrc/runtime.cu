@@ -138,7 +138,7 @@ static int staging_estimate(const Prep &q)
 }
 
 srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, double phi_t, uint64_t seed,
-                   const srm_params *pin, Prep &q)
+                   const srm_params *pin, Prep &q, bool place)
 {
     if (!box || !radii) return fail(SRM_E_ARG, "null argument");
     if (pin) q.p = *pin;
@@ -189,9 +189,15 @@ srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, dou
     q.S0 = base_measure(dim, q.r.data(), n);
     q.lam_t = p.lambda_t > 0.0 ? p.lambda_t : lam_of(dim, q.S0, q.V, phi_t);
 
-    // starting configuration (Algorithm 1 line 2)
-    q.x.assign((size_t)n * dim, 0.0);
-    if (p.init == SRM_INIT_EXPLICIT) {
+    // starting configuration (Algorithm 1 line 2); without `place` only the
+    // scales and capacities are computed
+    q.x.assign(place ? (size_t)n * dim : 0, 0.0);
+    if (p.init == SRM_INIT_EXPLICIT && !place) {
+        q.lam0 = p.lambda0 > 0.0 ? p.lambda0 : 1.0;
+    } else if ((p.init == SRM_INIT_RSA_UNIFORM || p.init == SRM_INIT_RSA_CLUSTERED) && !place) {
+        if (!(p.f0 > 0.0 && p.f0 <= phi_t)) return fail(SRM_E_ARG, "f0 must be in (0, phi_t]");
+        q.lam0 = lam_of(dim, q.S0, q.V, p.f0);
+    } else if (p.init == SRM_INIT_EXPLICIT) {
         if (!p.init_pos) return fail(SRM_E_ARG, "explicit start needs init_pos");
         std::memcpy(q.x.data(), p.init_pos, sizeof(double) * q.x.size());
         for (size_t i = 0; i < q.x.size(); i++) {
@@ -224,7 +230,7 @@ srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, dou
     if (q.ncells_need > 0x7ffffff0LL) return fail(SRM_E_ARG, "too many cells (radii too small for the box)");
     q.nsub_need = 1;
     for (int a = 0; a < dim; a++) q.nsub_need *= per[a] / 3;
-    q.cap_est = staging_estimate(q);
+    q.cap_est = place ? staging_estimate(q) : 64;
     return SRM_OK;
 }
 
@@ -400,7 +406,7 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
         has3d = has3d || mb.dim == 3 || mb.slot3d;
     }
     BatchDev *d = (BatchDev *)dev_alloc(g, sizeof(BatchDev));
-    int32_t *d_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * off.size());
+    int32_t *d_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * (off.size() + 2 * (size_t)(B + 1)));
     RveDev **d_rv = (RveDev **)dev_alloc(g, sizeof(RveDev *) * (size_t)B);
     if (!d || !d_off || !d_rv) return fail(SRM_E_NOMEM, "device allocation failed");
     std::vector<RveDev *> rv((size_t)B);
@@ -413,6 +419,9 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     hb.tile_c = d_off + 2 * (B + 1);
     hb.tile_n = d_off + 3 * (B + 1);
     hb.sub = d_off + 4 * (B + 1);
+    hb.act = d_off + 5 * (B + 1);
+    hb.act3 = d_off + 6 * (B + 1);
+    CK(cudaMemsetAsync(hb.act, 0, sizeof(int32_t) * 2 * (size_t)(B + 1), g.stream));
     CK(cudaMemcpyAsync(d_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(d_rv, rv.data(), sizeof(RveDev *) * (size_t)B, cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(d, &hb, sizeof(BatchDev), cudaMemcpyHostToDevice, g.stream));
@@ -431,9 +440,9 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     return SRM_OK;
 }
 
-// kernels of one super-step: begin, binning (count, 3 scan passes, scatter,
-// stamp, in-cell sort), 3^d sweep colours, check, control
-static int64_t kernels_per_superstep(bool has3d) { return 1 + 7 + (has3d ? 27 : 9) + 1 + 1; }
+// kernels of one super-step: begin and plan, binning (count, 3 scan passes,
+// scatter, stamp, in-cell sort), 3^d sweep colours, check, control
+static int64_t kernels_per_superstep(bool has3d) { return 2 + 7 + (has3d ? 27 : 9) + 1 + 1; }
 
 static void enqueue_superstep(Group &g, cudaStream_t s, const std::vector<cudaEvent_t> *ev = nullptr)
 {

@@ -97,7 +97,7 @@ inline void group_setup(Group &g, void *stream, const srm_allocator *alloc)
 double phi_of(int dim, double S0, double V, double lam);
 int64_t cells_for(int dim, const double L[3], double rmax, double c_m, double lam, int64_t per_axis[3]);
 srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, double phi_t, uint64_t seed,
-                   const srm_params *pin, Prep &q);
+                   const srm_params *pin, Prep &q, bool place = true);
 void *dev_alloc(Group &g, size_t bytes);
 void group_free(Group &g);
 srm_status member_alloc(Group &g, Member &mb, int64_t n_cap, int64_t ncells_cap, int64_t nsub_cap);

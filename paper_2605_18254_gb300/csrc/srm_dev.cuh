@@ -93,6 +93,8 @@ struct BatchDev {
     int32_t *tile_c;  // [B+1] first scan tile of each RVE over its cells
     int32_t *tile_n;  // [B+1] first scan tile of each RVE over its particles
     int32_t *sub;     // [B+1] first sweep work item of each RVE (cells of one colour)
+    int32_t *act;     // [B+1] the same over the RVEs at work in this super-step
+    int32_t *act3;    // [B+1] the same over the 3D RVEs at work (colours 9..26)
     uint32_t wq[27];  // sweep work counters, one per colour
 };
 
