@@ -189,6 +189,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def combine_ranks(dev_s, e2e_s, updates, dist=None, device="cpu"):
+    """Whole-job numbers of replicas: the slowest rank's times, the sum of
+    the particle updates of all ranks (host-side reduction only; the ranks
+    exchange no simulation data)."""
+    if dist is None:
+        return dev_s, e2e_s, updates
+    import torch
+    t = torch.tensor([dev_s, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(u[0])
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -249,14 +263,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = sum(r["e2e_s"] for r in res)
     sweeps = sum(r["sweeps"] for r in res)
     updates = float(w.n) * sweeps
-    if dist:
-        t = torch.tensor([dev_s, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([updates], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        dev_max, e2e_max, updates_all = float(t[0]), float(t[1]), float(u[0])
-    else:
-        dev_max, e2e_max, updates_all = dev_s, e2e_s, updates
+    dev_max, e2e_max, updates_all = combine_ranks(dev_s, e2e_s, updates, dist, dev)
     if rank != 0:
         return
     ok = all(r["pairs"] == 0 and r["info"]["converged"] and abs(r["phi"] - w.target_phi) < 1e-9

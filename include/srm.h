@@ -20,7 +20,7 @@
  *     particle (x, y[, z]), double precision.
  *   - Radii: each particle has a base radius r_i; its radius is R_i =
  *     lambda * r_i with one scale factor lambda per RVE (the swelling of
- *     Algorithm 1 line 8, read as a multiplicative factor (1 + c_w) per
+ *     Algorithm 1, read as a multiplicative factor (1 + c_w) per
  *     iteration).
  */
 #ifndef SRM_H
@@ -58,7 +58,7 @@ typedef struct srm_radii {
     double mean, sd, lo, hi;
 } srm_radii;
 
-/* Starting configuration (Algorithm 1 line 2).  RSA: random sequential
+/* Starting configuration (Algorithm 1).  RSA: random sequential
  * addition at volume fraction f0, proposals uniform in the box or Gaussian
  * around n_clusters uniform centres (standard deviation cluster_sigma).
  * EXPLICIT: init_pos holds non-overlapping positions at scale lambda0. */
@@ -87,6 +87,11 @@ typedef struct srm_params {
     double lambda_t;         /* > 0: target scale instead of the one of phi      */
     double guard;            /* SRM_PREC_F32: relative guard on squared distance */
     uint64_t sweep0;         /* first value of the sweep counter (resume)        */
+    int32_t wait_limit;      /* polls of one cell-to-cell dependency inside a    */
+                             /* sweep before the run fails with                  */
+                             /* SRM_E_DEVICE_TIMEOUT (0: 2^22; < 0: give up at   */
+                             /* the first dependency -- for tests of the path)   */
+    int32_t reserved;
 } srm_params;
 
 /* Fills p with the defaults: c_w = 0.01, c_m = 0 (must be set), N_k = N_l =
@@ -110,7 +115,7 @@ typedef struct srm_rve srm_rve;
  * parameters (NULL: defaults, which leaves c_m = 0 and fails), CUDA stream
  * (NULL: the legacy default stream), allocator (NULL: cudaMallocAsync).
  * The target scale is lambda_t = (phi_t prod L / S0)^(1/d), S0 = sum of the
- * base disk areas or sphere volumes (Algorithm 1 line 3).
+ * base disk areas or sphere volumes (Algorithm 1).
  * Rejects (SRM_E_ARG): dim not 2 or 3, n < 1, L <= 0, phi_t outside (0, 1),
  * c_m <= 0, N_k, N_l < 1, N_shake < 0, and boxes narrower than three cells of
  * the final cell size 2.5 lambda_t max r + c_m on some axis (the minimum-image
@@ -130,7 +135,7 @@ typedef struct srm_step_info {
     uint64_t sweep;        /* sweep counter after the iteration                              */
 } srm_step_info;
 
-/* One iteration of Algorithm 1 (lines 4-23): swell the copy Q, up to N_k
+/* One iteration of Algorithm 1: swell the copy Q, up to N_k
  * rounds of (bin, sweep of Algorithm 3, check of Algorithm 6); accept Q if it
  * is collision-free, else discard it and shake P with N_shake sweeps. */
 srm_status srm_step(srm_rve *h, srm_step_info *out);
@@ -192,12 +197,12 @@ srm_status srm_get_state(srm_rve *h, srm_state_info *out);
 /* Per-stage device time of the super-steps run while timing is on, from CUDA
  * events recorded between the launches of each super-step (one host
  * synchronisation per super-step while on, so use it for measurement only).
- * Stages: begin + binning (Algorithm 2), each colour launch of the sweep
- * (Algorithm 3), the check (Algorithm 6), the control step. */
+ * Stages: begin + binning (Algorithm 2), the sweep (Algorithm 3, one launch
+ * for all colours), the check (Algorithm 6), the control step. */
 typedef struct srm_timings {
     double ms_bin, ms_sweep, ms_check, ms_control;
     int64_t supersteps;       /* super-steps that did work while timing was on */
-    int64_t sweep_launches;   /* colour launches of the sweep kernel            */
+    int64_t sweep_launches;   /* launches of the sweep kernel                   */
     int64_t check_launches;   /* launches of the check kernel that did work     */
 } srm_timings;
 

@@ -15,18 +15,18 @@
  *
  * Readings of the paper that this file fixes (the paper is silent or loose):
  *   - swelling is multiplicative, R_i = lambda * r_i, lambda <- lambda(1+c_w),
- *     capped at the target scale lambda_t (Alg 1 line 8, Section 2 step a,
+ *     capped at the target scale lambda_t (Alg 1, Section 2 step a,
  *     "minor adjustments" of the last iteration);
  *   - cell size uses the post-swell radius; the grid has n = 3*max(1,
  *     floor(L/(3*cellSize))) cells per axis of width w = L/n, so that cells
- *     can be coloured by (cell index mod 3) (Alg 1 lines 4-5, Alg 2);
+ *     can be coloured by (cell index mod 3) (Alg 1, Alg 2);
  *   - a particle never collides with itself (Alg 5 skips t == q);
  *   - touching counts as a collision: sqrt(dx^2+dy^2[+dz^2]) <= R_q + R_t
  *     (Alg 5);
  *   - "unit random vector" is a uniform direction: rejection sampling from
  *     the cube [-1,1)^d on a 2^-53 lattice, then division by the norm, with
  *     the draws taken from Philox4x64-10 keyed by (seed, move tag) at counter
- *     (particle id, sweep index, try, candidate) (Alg 3 line 4);
+ *     (particle id, sweep index, try, candidate) (Alg 3);
  *   - the shake step runs N_shake sweeps of Alg 3 on the unswollen P, each
  *     preceded by a fresh binning, on the grid of the iteration (Alg 1 lines
  *     19-22, Section 2 step d);
@@ -78,7 +78,7 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 #define ORC_TAG_MOVE 0x53524D2D4D4F5645ULL
 #define ORC_MAX_CAND 32
 
-/* Uniform direction on the unit circle / sphere (Alg 3 line 4).  Candidate m
+/* Uniform direction on the unit circle / sphere (Alg 3).  Candidate m
  * takes one Philox block at counter (pid, sweep, try, m); coordinate a is
  * ((word_a >> 10) - 2^53) * 2^-53, a point of the cube [-1,1) on a 2^-53
  * lattice, exact in binary64.  The first candidate with 0 < |v|^2 <= 1 is
@@ -116,7 +116,7 @@ double orc_wrap(double x, double L)
     return x;
 }
 
-/* Alg 1 lines 4-5 with the coloured-grid reading: cellSize from the swollen
+/* Alg 1 with the coloured-grid reading: cellSize from the swollen
  * maximum radius, n a multiple of 3, w = L / n. */
 void orc_grid(int dim, const double L[3], double lam, double rmax, double c_m,
               int64_t n[3], double w[3])
@@ -131,7 +131,7 @@ void orc_grid(int dim, const double L[3], double lam, double rmax, double c_m,
     }
 }
 
-/* Alg 2 lines 2-5: cell coordinate of one position. */
+/* Alg 2: cell coordinate of one position. */
 static int64_t cell_coord(double x, double w, int64_t n)
 {
     int64_t c = (int64_t)(x / w);
@@ -370,7 +370,7 @@ void orc_get_counters(const orc_sys *s, int64_t out[5])
 }
 
 /* Volume (area) fraction of P: lambda^d sum v(r_i) / prod L, with v the disk
- * area or sphere volume, summed in id order (Alg 1 line 17). */
+ * area or sphere volume, summed in id order (Alg 1). */
 double orc_phi(const orc_sys *s, double lam)
 {
     double S0 = 0.0;
@@ -386,7 +386,7 @@ double orc_phi(const orc_sys *s, double lam)
 }
 
 /* Scale at which P reaches volume fraction phi: (phi prod L / S0)^(1/d),
- * square root in 2D and cube root in 3D (Alg 1 line 3 with the
+ * square root in 2D and cube root in 3D (Alg 1 with the
  * multiplicative swelling reading). */
 double orc_lambda_for_phi(const orc_sys *s, double phi)
 {
@@ -457,7 +457,7 @@ int64_t orc_pairs(orc_sys *s, int64_t *ij, int64_t cap)
     return cnt;
 }
 
-/* One iteration of Alg 1 (lines 4-23).  Returns 1 if the swollen
+/* One iteration of Alg 1.  Returns 1 if the swollen
  * configuration was accepted, 0 if it was discarded and P shaken, 2 if P was
  * already at the target scale (nothing to do).  info (may be NULL) receives
  * {k sweeps used, colliding count after the last check, shake sweeps}. */

@@ -53,7 +53,8 @@ class srm_params(Structure):
                 ("N_shake", c_int32), ("precision", c_int32), ("init", c_int32),
                 ("n_clusters", c_int32), ("cluster_sigma", c_double), ("f0", c_double),
                 ("init_pos", c_void_p), ("lambda0", c_double), ("lambda_t", c_double),
-                ("guard", c_double), ("sweep0", c_uint64)]
+                ("guard", c_double), ("sweep0", c_uint64), ("wait_limit", c_int32),
+                ("reserved", c_int32)]
 
 
 ALLOC_FN = CFUNCTYPE(c_void_p, c_void_p, c_size_t, c_void_p)
@@ -305,7 +306,7 @@ class Rve:
     def __init__(self, dim, box, radii, target_phi, seed=1, *, n=None, c_m, c_w=0.01, N_k=10,
                  N_l=10, N_shake=10, precision=PREC_F64, init="rsa", positions=None, f0=0.1,
                  n_clusters=0, cluster_sigma=0.0, lambda0=0.0, lambda_t=0.0, guard=4e-6,
-                 sweep0=0, stream=None, torch_memory=True):
+                 sweep0=0, wait_limit=0, stream=None, torch_memory=True):
         import torch
         lib = load()
         self.dim = int(dim)
@@ -336,6 +337,7 @@ class Rve:
             p.init_pos = x.ctypes.data
         p.f0, p.n_clusters, p.cluster_sigma = f0, n_clusters, cluster_sigma
         p.lambda0, p.lambda_t, p.guard, p.sweep0 = lambda0, lambda_t, guard, sweep0
+        p.wait_limit = wait_limit
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)

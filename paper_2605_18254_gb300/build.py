@@ -25,6 +25,9 @@ LIB = os.path.join(OUT_DIR, "libsrm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
               "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC] + ARCH
+# tuning knob: blocks per SM the sweep kernel's register allocation must allow
+if os.environ.get("SRM_SWEEP_MIN_BLOCKS"):
+    NVCC_FLAGS += [f"-DSRM_SWEEP_MIN_BLOCKS={int(os.environ['SRM_SWEEP_MIN_BLOCKS'])}"]
 
 
 def _nvcc() -> str:
@@ -46,6 +49,10 @@ def needs_build() -> bool:
         return True
     cu, hdr = sources()
     t = os.path.getmtime(LIB)
+    stamp = os.path.join(OUT_DIR, "flags.txt")
+    flags = " ".join(NVCC_FLAGS)
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        return True
     return any(os.path.getmtime(f) > t for f in cu + hdr + [GEN_C, __file__])
 
 
@@ -75,6 +82,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".{os.getpid()}.tmp"
     run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lm"])
     os.replace(tmp, LIB)
+    with open(os.path.join(OUT_DIR, "flags.txt"), "w") as f:
+        f.write(" ".join(NVCC_FLAGS))
     return LIB
 
 

@@ -168,6 +168,13 @@ __global__ void __launch_bounds__(1024) k_plan(BatchDev *bd)
     if (threadIdx.x == 0) {
         bd->act[B] = carry[0];
         bd->act3[B] = carry[1];
+        // one-launch sweep: colours in ascending order, 2D RVEs in 0..8 only
+        int32_t o = 0;
+        for (int c = 0; c < 27; c++) {
+            bd->coff[c] = o;
+            o += c < 9 ? carry[0] : carry[1];
+        }
+        bd->coff[27] = o;
     }
 }
 

@@ -10,7 +10,7 @@
 // other's particles: the parallel sweep equals the serial sweep in
 // colour -> cell -> id order, whatever the scheduling.
 //
-// A trial move (Algorithm 3 lines 4-10) is q = wrap(q_old + c_m u) with u the
+// A trial move (Algorithm 3) is q = wrap(q_old + c_m u) with u the
 // Philox-drawn direction; the collision test (Algorithm 5) covers the cells
 // within H of the home cell, which contain every particle that can touch any
 // trial position (cells are at least 2.5 R_max + c_m wide and the lists are
@@ -72,10 +72,53 @@ __device__ __forceinline__ float box_dist2(const float4 &t, const float w[3], in
     return ex * ex + ey * ey + ez * ez;
 }
 
+// One-launch sweep: before a cell of colour chi is staged, every non-empty
+// cell within reach (home +-H) whose colour is lower must have finished this
+// sweep -- exactly the cells of lower colour whose moves the serial order
+// lets it see; cells of higher colour wait for this one in turn, so they are
+// still unmoved.  Cells are handed out in colour order, so every cell waited
+// for is already held by a running warp.  A wait gives up after wait_limit
+// polls and sets the RVE's status (the host reports SRM_E_DEVICE_TIMEOUT).
+template <int DIM>
+__device__ __forceinline__ void wait_lower_colours(RveDev *st, const uint32_t *cs, int hx, int hy, int hz, int chi,
+                                                   uint32_t epoch)
+{
+    const int lane = threadIdx.x & 31;
+    const int H0 = st->H[0], H1 = st->H[1], H2 = st->H[2];
+    const int w0 = 2 * H0 + 1, w1 = 2 * H1 + 1, w2 = 2 * H2 + 1;
+    const int nst = w0 * w1 * w2;
+    const int n0 = st->gn[0], n1 = st->gn[1], n2 = st->gn[2];
+    const int limit = st->wait_limit;
+    for (int j = lane; j < nst; j += 32) {
+        const int dx = j % w0 - H0, dy = (j / w0) % w1 - H1, dz = j / (w0 * w1) - H2;
+        int cx = hx + dx, cy = hy + dy, cz = hz + dz;
+        cx = cx < 0 ? cx + n0 : (cx >= n0 ? cx - n0 : cx);
+        cy = cy < 0 ? cy + n1 : (cy >= n1 ? cy - n1 : cy);
+        cz = cz < 0 ? cz + n2 : (cz >= n2 ? cz - n2 : cz);
+        const int col = cx % 3 + 3 * (cy % 3) + (DIM == 3 ? 9 * (cz % 3) : 0);
+        if (col >= chi) continue;
+        const int c = cx + n0 * (cy + n1 * cz);
+        if (cs[c + 1] == cs[c]) continue;
+        if (limit < 0) {
+            atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
+            continue;
+        }
+        for (int it = 0; ld_acquire(&st->done[c]) != epoch; it++) {
+            if (it >= limit) {
+                atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    __syncwarp();
+    __threadfence();
+}
+
 // One cell of colour chi (work item t of its RVE), processed by one warp.
 template <int DIM, bool F32>
 __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned char *base, int cap,
-                                           int &moved, unsigned &examined)
+                                           int &moved, unsigned &examined, bool dataflow)
 {
     using PT = typename SweepSmem<F32>::PT;
     using DT = typename SweepSmem<F32>::DT;
@@ -102,7 +145,9 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
         const int hz = DIM == 3 ? 3 * (t / (s0 * s1)) + chi / 9 : 0;
         const int cell = hx + st->gn[0] * (hy + st->gn[1] * hz);
         const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
-        if (nh == 0) return;
+        if (nh == 0) return;  // nothing moves: nobody waits for an empty cell
+        const uint32_t epoch = (uint32_t)(st->sweep + 1);
+        if (dataflow) wait_lower_colours<DIM>(st, cs, hx, hy, hz, chi, epoch);
         int nst, center;
         const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
         // home corner (FP64 form: the binary32 copies are relative to it)
@@ -235,37 +280,38 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
             // trials in batches, one per lane: 2 first (most particles take
             // the first trial), then 8 at a time
             for (int l0 = 0; l0 < N_l && !done;) {
-                const int bsz = l0 == 0 ? PRE_TRIALS : 8;
+                const int bsz = (l0 == 0 && m < (uint32_t)PRE_NH) ? PRE_TRIALS : 8;
                 const int lmax = N_l - l0 < bsz ? N_l - l0 : bsz;
                 double qt[3] = {0.0, 0.0, 0.0};
                 float qs[3] = {0.f, 0.f, 0.f};
-                if (lane < lmax) {
-                    const bool have = l0 == 0 && m < (uint32_t)PRE_NH;
-                    const DT *up = pre + 3 * (m * PRE_TRIALS + lane);
-                    if constexpr (F32) {
-                        float u[3];
-                        if (have) {
-                            u[0] = up[0];
-                            u[1] = up[1];
-                            u[2] = up[2];
+                if (l0 == 0 && m < (uint32_t)PRE_NH) {
+                    // first trials: drawn up front for the whole cell
+                    if (lane < lmax) {
+                        const DT *up = pre + 3 * (m * PRE_TRIALS + lane);
+                        if constexpr (F32) {
+                            qs[0] = p.x + cmf * up[0];
+                            qs[1] = p.y + cmf * up[1];
+                            qs[2] = DIM == 3 ? p.z + cmf * up[2] : p.z;
                         } else {
-                            unit_dir_f32<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), u);
+                            qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, up[0])), st->L[0]);
+                            qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, up[1])), st->L[1]);
+                            qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, up[2])), st->L[2]) : p.z;
                         }
-                        qs[0] = p.x + cmf * u[0];
-                        qs[1] = p.y + cmf * u[1];
-                        qs[2] = DIM == 3 ? p.z + cmf * u[2] : p.z;
-                    } else {
-                        double u[3];
-                        if (have) {
-                            u[0] = up[0];
-                            u[1] = up[1];
-                            u[2] = up[2];
+                    }
+                } else {
+                    // later trials: eight at a time, candidates drawn by all lanes
+                    DT u[3];
+                    draw8<DIM, F32>(seed, sweep, pid, l0, u);
+                    if (lane < lmax) {
+                        if constexpr (F32) {
+                            qs[0] = p.x + cmf * u[0];
+                            qs[1] = p.y + cmf * u[1];
+                            qs[2] = DIM == 3 ? p.z + cmf * u[2] : p.z;
                         } else {
-                            unit_dir<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), u);
+                            qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, u[0])), st->L[0]);
+                            qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, u[1])), st->L[1]);
+                            qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, u[2])), st->L[2]) : p.z;
                         }
-                        qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, u[0])), st->L[0]);
-                        qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, u[1])), st->L[1]);
-                        qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, u[2])), st->L[2]) : p.z;
                     }
                 }
                 l0 += lmax;
@@ -330,13 +376,23 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
             if (lane == 0) st->flags[gi] = done ? 1 : 0;
             __syncwarp();
         }
+        if (dataflow && lane == 0) {
+            __threadfence();
+            st_release(&st->done[cell], epoch);
+        }
+        __syncwarp();
     }
 }
 
 // One launch per colour over all RVEs of the batch: each warp takes the next
 // (RVE, cell) work item from the colour's counter.  2D RVEs have 9 colours.
+// Blocks per SM the register allocation must allow (a build-time knob).
+#ifndef SRM_SWEEP_MIN_BLOCKS
+#define SRM_SWEEP_MIN_BLOCKS 1
+#endif
+
 template <bool F32>
-__global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(BatchDev *bd, int chi, int cap)
+__global__ void __launch_bounds__(SW_WARPS * 32, SRM_SWEEP_MIN_BLOCKS) k_sweep(BatchDev *bd, int chi, int cap)
 {
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -359,11 +415,53 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sweep(BatchDev *bd, int chi, 
         int moved = 0;
         unsigned examined = 0;
         if (st->dim == 3) {
-            sweep_cell<3, F32>(st, chi, t, base, cap, moved, examined);
+            sweep_cell<3, F32>(st, chi, t, base, cap, moved, examined, false);
         } else {
             if (chi >= 9) continue;
-            sweep_cell<2, F32>(st, chi, t, base, cap, moved, examined);
+            sweep_cell<2, F32>(st, chi, t, base, cap, moved, examined, false);
         }
+        examined = __reduce_add_sync(0xffffffffu, examined);
+        if (lane == 0) {
+            if (moved) atomicAdd(&st->red[3], (unsigned long long)moved);
+            if (examined) atomicAdd(&st->pairs_sweep, (unsigned long long)examined);
+        }
+    }
+}
+
+// All colours in one launch: work items are handed out in colour order from
+// one counter; each cell waits for its lower-colour neighbours
+// (wait_lower_colours) and stamps itself when done.
+template <bool F32>
+__global__ void __launch_bounds__(SW_WARPS * 32, SRM_SWEEP_MIN_BLOCKS) k_sweep_df(BatchDev *bd, int cap)
+{
+    extern __shared__ __align__(32) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
+    const int B = bd->B;
+    const int total = bd->coff[27];
+    for (;;) {
+        int tg = 0, chi = 0, r = 0, t = 0;
+        if (lane == 0) {
+            tg = (int)atomicAdd(&bd->wq[0], 1u);
+            if (tg < total) {
+                chi = find_seg(bd->coff, 27, tg);
+                const int local = tg - bd->coff[chi];
+                const int32_t *off = chi < 9 ? bd->act : bd->act3;
+                r = find_seg(off, B, local);
+                t = local - off[r];
+            }
+        }
+        tg = __shfl_sync(0xffffffffu, tg, 0);
+        if (tg >= total) break;
+        chi = __shfl_sync(0xffffffffu, chi, 0);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        RveDev *st = bd->rv[r];
+        if (!st->active || t >= st->nsub) continue;
+        int moved = 0;
+        unsigned examined = 0;
+        if (st->dim == 3) sweep_cell<3, F32>(st, chi, t, base, cap, moved, examined, true);
+        else sweep_cell<2, F32>(st, chi, t, base, cap, moved, examined, true);
         examined = __reduce_add_sync(0xffffffffu, examined);
         if (lane == 0) {
             if (moved) atomicAdd(&st->red[3], (unsigned long long)moved);
@@ -407,8 +505,16 @@ void launch_sweep_colour(const BatchShape &b, int chi, cudaStream_t s)
 
 void launch_sweep(const BatchShape &b, cudaStream_t s)
 {
-    const int ncol = b.has3d ? 27 : 9;
-    for (int chi = 0; chi < ncol; chi++) launch_sweep_colour(b, chi, s);
+    const int cap = b.cap;
+    const size_t smem = sweep_smem(b.f32, cap);
+    const int64_t want64 = (b.sub_total * (b.has3d ? 27 : 9) + SW_WARPS - 1) / SW_WARPS;
+    const int want = (int)(want64 > 0x7fffffff ? 0x7fffffff : want64);
+    auto shape = [&](auto kern) {
+        const int res = resident_blocks(kern, smem) * (g_sms > 0 ? g_sms : 1);
+        return want < res ? want : res;
+    };
+    if (b.f32) k_sweep_df<true><<<shape(k_sweep_df<true>), SW_WARPS * 32, smem, s>>>(b.d, cap);
+    else k_sweep_df<false><<<shape(k_sweep_df<false>), SW_WARPS * 32, smem, s>>>(b.d, cap);
 }
 
 // Dynamic shared memory above 48 KB needs an opt-in per kernel.
@@ -422,6 +528,10 @@ void sweep_configure()
     cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sweep_smem(true, sweep_cap_max(true)));
     cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep_smem(false, sweep_cap_max(false)));
+    cudaFuncSetAttribute(k_sweep_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep_smem(true, sweep_cap_max(true)));
+    cudaFuncSetAttribute(k_sweep_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sweep_smem(false, sweep_cap_max(false)));
 }
 

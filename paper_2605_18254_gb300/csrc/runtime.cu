@@ -189,7 +189,7 @@ srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, dou
     q.S0 = base_measure(dim, q.r.data(), n);
     q.lam_t = p.lambda_t > 0.0 ? p.lambda_t : lam_of(dim, q.S0, q.V, phi_t);
 
-    // starting configuration (Algorithm 1 line 2); without `place` only the
+    // starting configuration (Algorithm 1); without `place` only the
     // scales and capacities are computed
     q.x.assign(place ? (size_t)n * dim : 0, 0.0);
     if (p.init == SRM_INIT_EXPLICIT && !place) {
@@ -302,6 +302,7 @@ srm_status member_alloc(Group &g, Member &mb, int64_t n_cap, int64_t ncells_cap,
     s.flags = (uint8_t *)A(n);
     s.pcount = (uint32_t *)A(sizeof(uint32_t) * (n + 1));
     s.red = (unsigned long long *)A(sizeof(unsigned long long) * 8);
+    s.done = (uint32_t *)A(sizeof(uint32_t) * (size_t)ncells_cap);
     mb.d = (RveDev *)A(sizeof(RveDev));
     mb.stage_x = (double *)A(sizeof(double) * 3 * n);
     mb.stage_r = (double *)A(sizeof(double) * n);
@@ -369,12 +370,15 @@ srm_status member_load(Group &g, Member &mb, const Prep &q)
     s.it_overlap = s.moved_last = 0;
     s.status = 0;
     s.pairs_sweep = s.pairs_check = s.stage_overflow = 0;
+    s.wait_limit = q.p.wait_limit == 0 ? (1 << 22) : q.p.wait_limit;
     mb.dim = q.dim;
     mb.n = q.n;
     mb.S0 = q.S0;
     mb.V = q.V;
     mb.phi_t = q.phi_t;
     mb.lam_min = q.lam_min;
+    // completion stamps of an earlier job in this slot must not match
+    CK(cudaMemsetAsync(s.done, 0, sizeof(uint32_t) * (size_t)mb.ncells_cap, g.stream));
     CK(cudaMemcpyAsync(mb.d, &s, sizeof(RveDev), cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(mb.stage_x, q.x.data(), sizeof(double) * q.x.size(), cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(mb.stage_r, q.r.data(), sizeof(double) * (size_t)q.n, cudaMemcpyHostToDevice, g.stream));
@@ -441,31 +445,25 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
 }
 
 // kernels of one super-step: begin and plan, binning (count, 3 scan passes,
-// scatter, stamp, in-cell sort), 3^d sweep colours, check, control
-static int64_t kernels_per_superstep(bool has3d) { return 2 + 7 + (has3d ? 27 : 9) + 1 + 1; }
+// scatter, stamp, in-cell sort), the sweep (all colours), check, control
+static int64_t kernels_per_superstep(bool) { return 2 + 7 + 1 + 1 + 1; }
 
 static void enqueue_superstep(Group &g, cudaStream_t s, const std::vector<cudaEvent_t> *ev = nullptr)
 {
     const BatchShape &sh = g.sh;
-    if (ev) cudaEventRecordWithFlags((*ev)[0], s, cudaEventRecordExternal);
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecordWithFlags((*ev)[(size_t)k], s, cudaEventRecordExternal);
+    };
+    mark(0);
     srm::launch_begin(sh, s);
     srm::launch_bin(sh, sh.f32, sh.f32, s);
-    if (ev) {
-        const int ncol = sh.has3d ? 27 : 9;
-        for (int chi = 0; chi < ncol; chi++) {
-            cudaEventRecordWithFlags((*ev)[1 + chi], s, cudaEventRecordExternal);
-            srm::launch_sweep_colour(sh, chi, s);
-        }
-        cudaEventRecordWithFlags((*ev)[1 + ncol], s, cudaEventRecordExternal);
-        srm::launch_check(sh, s);
-        cudaEventRecordWithFlags((*ev)[2 + ncol], s, cudaEventRecordExternal);
-        srm::launch_control(sh, s);
-        cudaEventRecordWithFlags((*ev)[3 + ncol], s, cudaEventRecordExternal);
-    } else {
-        srm::launch_sweep(sh, s);
-        srm::launch_check(sh, s);
-        srm::launch_control(sh, s);
-    }
+    mark(1);
+    srm::launch_sweep(sh, s);
+    mark(2);
+    srm::launch_check(sh, s);
+    mark(3);
+    srm::launch_control(sh, s);
+    mark(4);
 }
 
 // The graph is recorded on a private stream (recording runs nothing) and
@@ -504,6 +502,13 @@ srm_status group_finalize(Group &g)
     return capture(g, g.gN_steps, &g.gN);
 }
 
+static srm_status device_status(int32_t code)
+{
+    if (code == srm::STATUS_WAIT_TIMEOUT)
+        return fail(SRM_E_DEVICE_TIMEOUT, "a sweep gave up waiting for a neighbouring cell (wait_limit polls)");
+    return fail(SRM_E_STATE, "device state reports an error");
+}
+
 srm_status pull_states(Group &g)
 {
     CK(cudaStreamSynchronize(g.stream));
@@ -511,7 +516,7 @@ srm_status pull_states(Group &g)
         CK(cudaMemcpyAsync(&g.pin[r], g.m[r]->d, sizeof(RveDev), cudaMemcpyDeviceToHost, g.stream));
     CK(cudaStreamSynchronize(g.stream));
     for (size_t r = 0; r < g.m.size(); r++)
-        if (g.pin[r].status != 0) return fail(SRM_E_STATE, "device state reports an error");
+        if (g.pin[r].status != 0) return device_status(g.pin[r].status);
     return SRM_OK;
 }
 
@@ -519,7 +524,7 @@ srm_status pull_state(Group &g, size_t r)
 {
     CK(cudaMemcpyAsync(&g.pin[r], g.m[r]->d, sizeof(RveDev), cudaMemcpyDeviceToHost, g.stream));
     CK(cudaStreamSynchronize(g.stream));
-    if (g.pin[r].status != 0) return fail(SRM_E_STATE, "device state reports an error");
+    if (g.pin[r].status != 0) return device_status(g.pin[r].status);
     return SRM_OK;
 }
 
@@ -534,9 +539,8 @@ static int64_t total_sweeps(const Group &g)
 // the host waits for each replay and adds up the stage times.
 static srm_status run_timed(Group &g, int steps)
 {
-    const int ncol = g.sh.has3d ? 27 : 9;
     if (g.ev.empty()) {
-        g.ev.resize((size_t)ncol + 4);
+        g.ev.resize(5);
         for (auto &e : g.ev) CK(cudaEventCreate(&e));
     }
     if (!g.gT) {
@@ -554,17 +558,15 @@ static srm_status run_timed(Group &g, int steps)
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]));
         g.tm.ms_bin += ms;
-        for (int c = 0; c < ncol; c++) {
-            CK(cudaEventElapsedTime(&ms, g.ev[1 + c], g.ev[2 + c]));
-            g.tm.ms_sweep += ms;
-        }
-        g.tm.sweep_launches += ncol;
-        CK(cudaEventElapsedTime(&ms, g.ev[1 + ncol], g.ev[2 + ncol]));
+        CK(cudaEventElapsedTime(&ms, g.ev[1], g.ev[2]));
+        g.tm.ms_sweep += ms;
+        g.tm.sweep_launches += 1;
+        CK(cudaEventElapsedTime(&ms, g.ev[2], g.ev[3]));
         g.tm.ms_check += ms;
         bool checked = false;
         for (size_t r = 0; r < g.m.size(); r++) checked = checked || g.pin[r].do_check;
         if (checked) g.tm.check_launches += 1;
-        CK(cudaEventElapsedTime(&ms, g.ev[2 + ncol], g.ev[3 + ncol]));
+        CK(cudaEventElapsedTime(&ms, g.ev[3], g.ev[4]));
         g.tm.ms_control += ms;
         g.tm.supersteps += 1;
     }

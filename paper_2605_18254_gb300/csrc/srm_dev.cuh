@@ -17,8 +17,8 @@ namespace srm {
 // Modes of the per-RVE state machine of Algorithm 1.
 enum Mode : int32_t {
     MODE_BEGIN = 0,  // next super-step starts an iteration (swell, new grid)
-    MODE_KLOOP = 1,  // inside the N_k loop (Alg 1 lines 9-14)
-    MODE_SHAKE = 2,  // shake sweeps on P (Alg 1 lines 19-22)
+    MODE_KLOOP = 1,  // inside the N_k loop (Alg 1)
+    MODE_SHAKE = 2,  // shake sweeps on P (Alg 1)
     MODE_DONE = 3,   // P at the target scale
     MODE_SWEEP = 4   // standalone sweep of P at its own scale
 };
@@ -76,7 +76,12 @@ struct RveDev {
     // work counters: candidate pairs examined by the sweep and by the check
     unsigned long long pairs_sweep, pairs_check;
     unsigned long long stage_overflow;  // cells whose culled stencil exceeded the staging capacity
+    uint32_t *done;       // [ncells_cap] epoch stamp of the last sweep that finished the cell
+    int32_t wait_limit;   // polls of one dependency before the sweep gives up (< 0: none)
 };
+
+// Device status codes (RveDev::status), reported by the host as srm_status.
+constexpr int32_t STATUS_WAIT_TIMEOUT = 5;
 
 // A group of RVEs advanced by the same launches (one RVE for a single
 // handle, many for a batch).  Kernels indexed by particles, cells or scan
@@ -96,7 +101,22 @@ struct BatchDev {
     int32_t *act;     // [B+1] the same over the RVEs at work in this super-step
     int32_t *act3;    // [B+1] the same over the 3D RVEs at work (colours 9..26)
     uint32_t wq[27];  // sweep work counters, one per colour
+    int32_t coff[28]; // first work item of each colour in the one-launch sweep
 };
+
+// Acquire load / release store of a 32-bit word in global memory (the
+// per-cell completion stamps of the one-launch sweep).
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Largest r with off[r] <= x (off non-decreasing, off[0] = 0).
 __device__ __forceinline__ int find_seg(const int32_t *off, int B, int x)
@@ -227,6 +247,109 @@ __device__ __forceinline__ void unit_dir_f32(uint64_t seed, uint64_t sweep, uint
     u[2] = 0.f;
 }
 
+// One candidate m of trial l: the binary64 lattice point and the acceptance
+// test of unit_dir.
+template <int DIM>
+__device__ __forceinline__ bool cand_f64(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint64_t m,
+                                         double v[3], double &s)
+{
+    uint64_t c[4] = {pid, sweep, l, m};
+    philox4x64(c, seed, TAG_MOVE);
+    v[2] = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) v[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
+    s = __dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1]));
+    if (DIM == 3) s = __dadd_rn(s, __dmul_rn(v[2], v[2]));
+    return s > 0.0 && s <= 1.0;
+}
+
+// The same candidate for the FP32 form (see unit_dir_f32): binary32 lattice
+// point, acceptance decided as in binary64.
+template <int DIM>
+__device__ __forceinline__ bool cand_f32(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint64_t m,
+                                         float v[3], float &s)
+{
+    uint64_t c[4] = {pid, sweep, l, m};
+    philox4x64(c, seed, TAG_MOVE);
+    v[2] = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) v[a] = (float)((int32_t)(c[a] >> 40) - (1 << 23)) * 0x1p-23f;
+    s = v[0] * v[0] + v[1] * v[1];
+    if (DIM == 3) s += v[2] * v[2];
+    if (s > 1.0f + 2e-6f) return false;
+    if (s < 1.0f - 2e-6f && s > 2e-6f) return true;
+    double vd[3];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) vd[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
+    double sd = __dadd_rn(__dmul_rn(vd[0], vd[0]), __dmul_rn(vd[1], vd[1]));
+    if (DIM == 3) sd = __dadd_rn(sd, __dmul_rn(vd[2], vd[2]));
+    const bool ok = sd > 0.0 && sd <= 1.0;
+    if (ok && !(s > 0.f)) s = (float)sd;
+    return ok;
+}
+
+// Directions of trials l0 .. l0+7 of one particle, drawn by a whole warp:
+// lane k evaluates candidate k % 4 of trial l0 + k / 4, a ballot picks for
+// every trial its first accepted candidate (the one unit_dir would take),
+// and a trial whose four candidates are all rejected continues with
+// candidates 4, 5, ... in its own lane.  Lane t (t < 8) returns the direction
+// of trial l0 + t.  All lanes of the warp must call it.
+template <int DIM, bool F32, typename DT>
+__device__ __noinline__ void draw8(uint64_t seed, uint64_t sweep, uint64_t pid, int l0, DT u[3])
+{
+    const int lane = threadIdx.x & 31, t = lane >> 2, cidx = lane & 3;
+    DT v[3], s;
+    bool ok;
+    if constexpr (F32) ok = cand_f32<DIM>(seed, sweep, pid, (uint64_t)(l0 + t), (uint64_t)cidx, v, s);
+    else ok = cand_f64<DIM>(seed, sweep, pid, (uint64_t)(l0 + t), (uint64_t)cidx, v, s);
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    // normalise in the lane that holds the chosen candidate
+    DT w[3] = {(DT)0, (DT)0, (DT)0};
+    const unsigned mine = (bal >> (4 * t)) & 15u;
+    const bool chosen = ok && (__ffs(mine) - 1) == cidx;
+    if (chosen) {
+        if constexpr (F32) {
+            const float inv = rsqrtf(s);
+#pragma unroll
+            for (int a = 0; a < DIM; a++) w[a] = v[a] * inv;
+        } else {
+            const double nrm = __dsqrt_rn(s);
+#pragma unroll
+            for (int a = 0; a < DIM; a++) w[a] = __ddiv_rn(v[a], nrm);
+        }
+    }
+    // lane t collects trial t from lane 4t + (first accepted candidate)
+    const unsigned mt = lane < 8 ? (bal >> (4 * lane)) & 15u : 1u;
+    const int src = 4 * (lane & 7) + (mt ? __ffs(mt) - 1 : 0);
+#pragma unroll
+    for (int a = 0; a < 3; a++) u[a] = __shfl_sync(0xffffffffu, w[a], src);
+    if (lane < 8 && !mt) {
+        // all four rejected (about 5% of 3D trials): continue in this lane
+        u[0] = (DT)1;
+        u[1] = (DT)0;
+        u[2] = (DT)0;
+        for (int m = 4; m < MAX_CAND; m++) {
+            DT vv[3], ss;
+            bool okk;
+            if constexpr (F32) okk = cand_f32<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), (uint64_t)m, vv, ss);
+            else okk = cand_f64<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), (uint64_t)m, vv, ss);
+            if (okk) {
+                if constexpr (F32) {
+                    const float inv = rsqrtf(ss);
+#pragma unroll
+                    for (int a = 0; a < DIM; a++) u[a] = vv[a] * inv;
+                } else {
+                    const double nrm = __dsqrt_rn(ss);
+#pragma unroll
+                    for (int a = 0; a < DIM; a++) u[a] = __ddiv_rn(vv[a], nrm);
+                }
+                if (DIM == 2) u[2] = (DT)0;
+                break;
+            }
+        }
+    }
+}
+
 // Algorithm 4: "< 0" first, then ">= L".
 __device__ __forceinline__ double wrap_d(double x, double L)
 {
@@ -235,7 +358,7 @@ __device__ __forceinline__ double wrap_d(double x, double L)
     return x;
 }
 
-// Algorithm 2 lines 2-5: int(x / w), then ((c % n) + n) % n.
+// Algorithm 2: int(x / w), then ((c % n) + n) % n.
 __device__ __forceinline__ int32_t cell_coord_d(double x, double w, int32_t n)
 {
     long long c = __double2ll_rz(__ddiv_rn(x, w));
@@ -243,7 +366,7 @@ __device__ __forceinline__ int32_t cell_coord_d(double x, double w, int32_t n)
     return (int32_t)(((c % nn) + nn) % nn);
 }
 
-// Algorithm 5 lines 10-18 for one pair: minimum-image difference, then
+// Algorithm 5 for one pair: minimum-image difference, then
 // sqrt(dx^2 + dy^2 [+ dz^2]) <= Rq + Rt, in binary64.  Most pairs are decided
 // from the squared distance against (Rq + Rt)^2 with a relative margin that
 // covers every rounding of both sides; only pairs inside that band take the
@@ -294,7 +417,7 @@ __device__ __forceinline__ bool gap_exact(const double q[3], double Rq, const do
     return S <= rs;
 }
 
-// Grid of Algorithm 1 lines 4-5 for scale lam: cellSize = 2.5 lam rmax + c_m,
+// Grid of Algorithm 1 for scale lam: cellSize = 2.5 lam rmax + c_m,
 // n = 3 max(1, int(L / (3 cellSize))), w = L / n.  Also the reach H of the
 // neighbour search: cells within one of the home cell cover every possible
 // partner of any trial move when 2 (lam rmax) + 2 c_m < w; otherwise two.

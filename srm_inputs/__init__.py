@@ -3,7 +3,7 @@
 This module holds no step of the SRM method.  It builds the starting state
 that the paper's main loop takes as given (Section 2: non-overlapping
 particles at a low initial volume fraction f0 placed by random sequential
-addition; Algorithm 1 line 2) and the workload recipes used by the tests and
+addition; Algorithm 1) and the workload recipes used by the tests and
 the benchmark.  The FP64 reference and the CUDA library are both fed from
 here, so that they receive identical inputs; neither is imported by it.
 

@@ -1,5 +1,5 @@
 """Pins of the reference's geometry: periodic wrap (Algorithm 4), the grid
-rule (Algorithm 1 lines 4-5, Algorithm 2), and the cell-list overlap search
+rule (Algorithm 1, Algorithm 2), and the cell-list overlap search
 (Algorithms 5 and 6) against O(N^2) brute force and periodic-image
 invariance."""
 import numpy as np

@@ -3,7 +3,7 @@
 * Philox4x64-10 against numpy's independent implementation of the same
   generator (numpy.random.Philox, which advances the counter by one before
   each block).
-* The unit-vector sampler (Algorithm 3 line 4, read as a uniform direction)
+* The unit-vector sampler (Algorithm 3, read as a uniform direction)
   against its definition: unit norm, the first accepted lattice point of the
   cube drawn from numpy's Philox stream, and uniformity of the angle (2D) and
   of cos(theta) and the azimuth (3D).
