@@ -55,6 +55,16 @@ def workload_desc(w, precision):
     }
 
 
+def hbm_side(w, precision, ms, pk):
+    """The sweep against HBM: its algorithmic bytes per launch are one read
+    and one write of every particle's position and radius and one moved
+    flag (FP32 form: 16 + 16 + 1 bytes; FP64 form: 32 + 32 + 1)."""
+    per = 33 if precision == 32 else 65
+    gbs = per * w.n / (ms * 1e-3) / 1e9
+    return {"bytes_per_launch": per * w.n, "achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"],
+            "frac": gbs / pk["hbm_gbs"]}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -236,7 +246,7 @@ def run_ours(args, rank, world, local_rank):
         ev[0].record(stream)
         g = new_rve()                       # host -> device copies of the inputs
         ev[1].record(stream)
-        info = g.run_to_target(args.max_iters)
+        info = g.run_to_target()
         pairs, gap, phi = g.certify()
         ev[2].record(stream)
         xo, ro = g.positions()               # device -> host copy of the result
@@ -269,11 +279,13 @@ def run_ours(args, rank, world, local_rank):
     ok = all(r["pairs"] == 0 and r["info"]["converged"] and abs(r["phi"] - w.target_phi) < 1e-9
              for r in res)
 
-    # ---- roofline of the dominant kernel: timing pass over the first sweeps
+    # ---- roofline of the dominant kernel: a timing pass over the same
+    # generation to target (CUDA events between the stages of every
+    # super-step, on the handle's stream)
     g = new_rve()
     g.set_timing(True)
     st0 = g.state()
-    info = g.run_to_target(args.timing_iters)
+    info = g.run_to_target()
     tm = g.timings()
     st1 = g.state()
     g.close()
@@ -287,7 +299,11 @@ def run_ours(args, rank, world, local_rank):
     pk, pk_kind = peaks()
     flops_per_pair = 11.0 if w.dim == 3 else 8.0
     if dom in ("sweep", "check"):
-        pairs = (st1["pairs_sweep"] - st0["pairs_sweep"]) if dom == "sweep" else (st1["pairs_check"] - st0["pairs_check"])
+        # algorithmic work: the pairs Algorithm 5 examines (every trial
+        # against the particles of the 3^d cells around the home cell) for
+        # the sweep; the pairs the check tests for Algorithm 6
+        pairs = (st1["pairs_alg5"] - st0["pairs_alg5"]) if dom == "sweep" else (st1["pairs_check"] - st0["pairs_check"])
+        tested = (st1["pairs_sweep"] - st0["pairs_sweep"]) if dom == "sweep" else pairs
         launches = tm["sweep_launches"] if dom == "sweep" else tm["check_launches"]
         flops = flops_per_pair * pairs / max(1, launches)
         achieved = flops / (per_launch[dom] * 1e-3) / 1e12
@@ -298,8 +314,12 @@ def run_ours(args, rank, world, local_rank):
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": committed_traffic(f"k_{dom}{args.precision}"),
                 "per_launch_ms": per_launch[dom],
-                "work": f"{flops_per_pair:.0f} flops per candidate pair tested x {pairs / max(1, launches):.4g} "
-                        f"pairs per launch (counted by the kernel)",
+                "work": (f"{flops_per_pair:.0f} flops per pair x {pairs / max(1, launches):.4g} pairs per launch: "
+                         + ("every trial of Algorithm 3 against the particles of the 3^d cells around its home cell "
+                            f"(Algorithm 5's candidate set; {(st1['trials'] - st0['trials']) / max(1, launches):.4g} "
+                            f"trials per launch); after culling the kernel tests {tested / max(1, launches):.4g} pairs"
+                            if dom == "sweep" else "pairs tested by the check")),
+                "hbm_side": hbm_side(w, args.precision, per_launch[dom], pk) if dom == "sweep" else None,
                 "peak_basis": (f"FP32 lanes: {N_SM} SMs x {FP32_LANES_PER_SM} x 2 flops x "
                                f"{pk.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz" + (" / 64 (FP64 rate)" if args.precision == 64 else "")),
                 "stage_ms_total": totals, "supersteps": tm["supersteps"]}
@@ -321,13 +341,13 @@ def run_ours(args, rank, world, local_rank):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            inf = g.run_to_target(args.timing_iters)
+            inf = g.run_to_target(args.compare_iters)
             e1.record(stream)
             torch.cuda.synchronize()
             cmp[f"fp{prec}"] = {"particle_updates_per_s": w.n * inf["sweeps"] / (e0.elapsed_time(e1) / 1e3),
                                 "sweeps": inf["sweeps"], "iterations": inf["iterations"]}
             g.close()
-        cmp["sample"] = f"first {args.timing_iters} iterations of Algorithm 1 from the RSA start"
+        cmp["sample"] = f"first {args.compare_iters} iterations of Algorithm 1 from the RSA start"
         cmp["fp32_over_fp64"] = cmp["fp32"]["particle_updates_per_s"] / cmp["fp64"]["particle_updates_per_s"]
 
     cpu = None
@@ -395,7 +415,7 @@ def run_ensemble(args, rank, world, local_rank):
         e[0].record(stream)
         b = srm.Batch(jobs, stream=stream.cuda_stream)
         e[1].record(stream)
-        ok = b.run(args.max_iters)
+        ok = b.run()
         cert = [b.certify(i) for i in range(len(ws))]
         e[2].record(stream)
         torch.cuda.synchronize()
@@ -523,8 +543,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poly_1m")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
-    ap.add_argument("--max-iters", type=int, default=1 << 40)
-    ap.add_argument("--timing-iters", type=int, default=20)
+    ap.add_argument("--compare-iters", type=int, default=20)
     ap.add_argument("--compare-fp64", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble-count", type=int, default=256)

@@ -190,6 +190,12 @@ typedef struct srm_state_info {
     uint64_t pairs_check;       /* candidate pairs tested by the checks (Alg 6)      */
     uint64_t stage_overflow;    /* sweep cells whose candidates exceeded the staging */
     int32_t stage_capacity;     /* candidates a sweep warp stages in shared memory   */
+    int32_t reserved0;
+    uint64_t trials;            /* trial moves evaluated by the sweeps (Alg 3)       */
+    uint64_t pairs_alg5;        /* pairs Alg 5 examines for those trials: for each,
+                                   the particles of the 3^d cells around the home
+                                   cell other than the mover (the method's own
+                                   candidate set, before any culling)               */
 } srm_state_info;
 
 srm_status srm_get_state(srm_rve *h, srm_state_info *out);

@@ -81,7 +81,7 @@ srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_
     srm_status st = SRM_OK;
     for (int32_t i = 0; i < n_slots && st == SRM_OK; i++) {
         Member *mb = new Member();
-        mb->slot3d = true;  // a slot may take 3D jobs: launch all 27 colours
+        mb->any_dim = true;  // a slot may take 2D or 3D jobs: launch both sweeps
         g.m.push_back(mb);
         st = member_alloc(g, *mb, max_particles, max_cells, max_cells / 9);
     }

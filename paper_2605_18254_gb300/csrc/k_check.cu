@@ -62,15 +62,17 @@ __device__ __forceinline__ void check_one(RveDev *st, int i, int &hit, unsigned 
                         const PT t = pos[j];
                         bool h;
                         if constexpr (F32) {
-                            const float ex = p.x - (t.x + (float)dx * w0);
-                            const float ey = p.y - (t.y + (float)dy * w1);
-                            float d2 = ex * ex + ey * ey;
+                            // the sweep's arithmetic: shifted candidate, then
+                            // the guarded predicate, with explicit roundings
+                            const float ex = __fsub_rn(p.x, __fmaf_rn((float)dx, w0, t.x));
+                            const float ey = __fsub_rn(p.y, __fmaf_rn((float)dy, w1, t.y));
+                            float d2 = __fmaf_rn(ey, ey, __fmul_rn(ex, ex));
                             if (DIM == 3) {
-                                const float ez = p.z - (t.z + (float)dz * w2);
-                                d2 += ez * ez;
+                                const float ez = __fsub_rn(p.z, __fmaf_rn((float)dz, w2, t.z));
+                                d2 = __fmaf_rn(ez, ez, d2);
                             }
-                            const float rs = p.w + t.w;
-                            h = d2 <= rs * rs * g1;
+                            const float rs = __fadd_rn(p.w, t.w);
+                            h = d2 <= __fmul_rn(__fmul_rn(rs, rs), g1);
                         } else {
                             const double q[3] = {p.x, p.y, p.z};
                             h = collide_exact<DIM>(q, p.w, t.x, t.y, t.z, t.w, st->L, st->halfL);

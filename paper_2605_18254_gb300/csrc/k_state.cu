@@ -11,8 +11,10 @@ namespace srm {
 __global__ void k_begin(BatchDev *bd)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == 0)
-        for (int c = 0; c < 27; c++) bd->wq[c] = 0u;
+    if (r == 0) {
+        bd->wq[0] = 0u;
+        bd->wq[1] = 0u;
+    }
     if (r >= bd->B) return;
     RveDev *st = bd->rv[r];
     st->active = 0;
@@ -102,8 +104,8 @@ __global__ void k_control(BatchDev *bd)
 }
 
 // Work plan of the sweep for this super-step: offsets of the colour cells of
-// the RVEs at work (all of them for colours 0..8, the 3D ones for 9..26), so
-// that finished RVEs of a batch cost nothing in the sweep.  One block.
+// the 2D and of the 3D RVEs at work, so that finished RVEs of a batch cost
+// nothing in the sweep.  One block.
 __global__ void __launch_bounds__(1024) k_plan(BatchDev *bd)
 {
     const int B = bd->B;
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(1024) k_plan(BatchDev *bd)
         if (r < B) {
             const RveDev *st = bd->rv[r];
             if (st->active) {
-                w = st->nsub;
+                w = st->dim == 2 ? st->nsub : 0;
                 w3 = st->dim == 3 ? st->nsub : 0;
             }
         }
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(1024) k_plan(BatchDev *bd)
         __syncthreads();
         const int32_t before = wid ? ws[wid - 1] : 0, before3 = wid ? ws3[wid - 1] : 0;
         if (r < B) {
-            bd->act[r] = carry[0] + before + x - w;
+            bd->act2[r] = carry[0] + before + x - w;
             bd->act3[r] = carry[1] + before3 + x3 - w3;
         }
         __syncthreads();
@@ -166,15 +168,8 @@ __global__ void __launch_bounds__(1024) k_plan(BatchDev *bd)
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        bd->act[B] = carry[0];
+        bd->act2[B] = carry[0];
         bd->act3[B] = carry[1];
-        // one-launch sweep: colours in ascending order, 2D RVEs in 0..8 only
-        int32_t o = 0;
-        for (int c = 0; c < 27; c++) {
-            bd->coff[c] = o;
-            o += c < 9 ? carry[0] : carry[1];
-        }
-        bd->coff[27] = o;
     }
 }
 
@@ -234,7 +229,7 @@ __device__ __forceinline__ uint32_t shift_cell_f32(const RveDev *st, const Slot 
         const float w = (float)st->gw[a];
         const int32_t n = st->gn[a];
         const int32_t sh = (int32_t)floorf(o[a] / w);
-        o[a] -= (float)sh * w;
+        o[a] = __fmaf_rn(-(float)sh, w, o[a]);  // one rounding, wherever inlined
         int32_t ca = (cc[a] + sh) % n;
         ca += ca < 0 ? n : 0;
         lin += (uint32_t)ca * mul;

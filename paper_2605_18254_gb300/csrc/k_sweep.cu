@@ -1,20 +1,26 @@
-// k_sweep.cu -- Algorithm 3 (random migration of every particle) as a
-// coloured parallel sweep.
+// k_sweep.cu -- Algorithm 3 (random migration of every particle) as one
+// parallel sweep in the canonical colour order.
 //
-// Cells are coloured by (c_x mod 3, c_y mod 3[, c_z mod 3]); the sweep runs
-// the 3^d colours in ascending order, one launch per colour.  Within a
-// colour every cell is handled by one warp, which moves the particles of its
-// cell one after the other in ascending id.  Two cells of one colour are at
-// least three cells apart along some axis, while a particle reads only cells
-// within H <= 2 of its home cell, so the cells of one colour never read each
-// other's particles: the parallel sweep equals the serial sweep in
-// colour -> cell -> id order, whatever the scheduling.
+// Cells are coloured by (c_x mod 3, c_y mod 3[, c_z mod 3]); the canonical
+// order visits the colours in ascending order, the cells of one colour in
+// any order and the particles of a cell in ascending id.  Two cells of one
+// colour are at least three cells apart along some axis, while a particle
+// reads only cells within H <= 2 of its home cell, so the cells of one colour
+// never read each other's particles.  The sweep of a group of RVEs is one
+// launch per dimension: warps take (RVE, cell) work items from one counter,
+// colour by colour, and a cell starts once every non-empty cell of lower
+// colour within its reach has finished (per-cell epoch stamps).  The result
+// equals the serial sweep in colour -> cell -> id order, whatever the
+// scheduling.
 //
 // A trial move (Algorithm 3) is q = wrap(q_old + c_m u) with u the
 // Philox-drawn direction; the collision test (Algorithm 5) covers the cells
 // within H of the home cell, which contain every particle that can touch any
 // trial position (cells are at least 2.5 R_max + c_m wide and the lists are
-// at most one move stale).
+// at most one move stale).  The directions of trials 0 and 1 depend on the
+// particle id and the counters only; k_draw draws them for every particle
+// before the sweep, so that the sweep itself draws only the later trials of
+// the few particles whose first two trials collide.
 //
 // Per cell, one warp:
 //  1. lists the stencil cells (home cell first) and stages in shared memory
@@ -22,11 +28,13 @@
 //     cell box <= R_home,max + R_t + 2 c_m (a conservative bound: trials stay
 //     within c_m of positions that stay within c_m of the box).  FP32 form:
 //     positions relative to the home cell corner; FP64 form: absolute
-//     binary64 positions plus binary32 copies relative to the corner;
+//     binary64 positions plus binary32 copies relative to the corner (the
+//     next chunk's loads are in flight while a chunk is culled);
 //  2. for each particle of the cell, in ascending id: builds its near list,
 //     the candidates within R_i + R_t + c_m of it (superset of everything a
-//     trial can touch), as copies in shared memory; lane l draws trial l of a
-//     batch; for each trial the lanes test the near list and vote;
+//     trial can touch), as copies in shared memory; the two pre-drawn trials,
+//     then batches of eight trials drawn by the lanes, are tested against
+//     the near list and the first clean one is taken;
 //  3. an accepted move updates the staged copy (later particles of the cell
 //     see it) and the slot in global memory, and marks the particle moved.
 // If the culled candidates exceed the staging capacity, the near lists are
@@ -39,9 +47,9 @@
 
 namespace srm {
 
-constexpr int NEAR_CAP = 128;
-constexpr int PRE_NH = 64;    // home particles whose first trials are drawn up front
-constexpr int PRE_TRIALS = 2; // trials drawn up front per particle
+constexpr int NEAR_CAP = 64;
+constexpr int PRE_NH = 64;    // home particles whose first trials are copied up front
+constexpr int PRE_TRIALS = 2; // trials drawn ahead of the sweep per particle
 
 template <bool F32>
 struct SweepSmem {
@@ -50,7 +58,7 @@ struct SweepSmem {
     static __host__ __device__ constexpr size_t bytes(int cap)
     {
         return (ST_HDR + (size_t)cap * sizeof(PT) + (F32 ? 0 : (size_t)cap * sizeof(float4)) +
-                (size_t)NEAR_CAP * sizeof(PT) + (size_t)PRE_NH * PRE_TRIALS * 3 * sizeof(DT) + 31) /
+                (size_t)NEAR_CAP * sizeof(PT) + (size_t)PRE_NH * PRE_TRIALS * sizeof(PT) + 31) /
                32 * 32;
     }
 };
@@ -72,13 +80,162 @@ __device__ __forceinline__ float box_dist2(const float4 &t, const float w[3], in
     return ex * ex + ey * ey + ez * ez;
 }
 
-// One-launch sweep: before a cell of colour chi is staged, every non-empty
-// cell within reach (home +-H) whose colour is lower must have finished this
-// sweep -- exactly the cells of lower colour whose moves the serial order
-// lets it see; cells of higher colour wait for this one in turn, so they are
-// still unmoved.  Cells are handed out in colour order, so every cell waited
-// for is already held by a running warp.  A wait gives up after wait_limit
-// polls and sets the RVE's status (the host reports SRM_E_DEVICE_TIMEOUT).
+// FP32 form of Algorithm 5 for one pair: trial q of a particle of radius Rq
+// against candidate c (both relative to the same corner), with the guard g1.
+// Explicit roundings (no contraction left to the compiler), so that the
+// decision is the same wherever the test is inlined.
+template <int DIM>
+__device__ __forceinline__ bool hit_f32(const float q[3], float Rq, const float4 &c, float g1)
+{
+    const float ex = __fsub_rn(q[0], c.x), ey = __fsub_rn(q[1], c.y);
+    float d2 = __fmaf_rn(ey, ey, __fmul_rn(ex, ex));
+    if (DIM == 3) {
+        const float ez = __fsub_rn(q[2], c.z);
+        d2 = __fmaf_rn(ez, ez, d2);
+    }
+    const float rs = __fadd_rn(Rq, c.w);
+    return d2 <= __fmul_rn(__fmul_rn(rs, rs), g1);
+}
+
+// Trial position of the FP32 form: p + c_m u per axis, one rounding.
+__device__ __forceinline__ float trial_f32(float p, float cm, float u) { return __fmaf_rn(cm, u, p); }
+
+// 16-byte asynchronous copy global -> shared (completes at cp_async_wait).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Position of the k-th (from 0) set bit of m; m has more than k set bits.
+__device__ __forceinline__ int nth_set(unsigned m, int k)
+{
+    for (int i = 0; i < k; i++) m &= m - 1u;
+    return __ffs(m) - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Directions of trials 0 and 1 of particles g0 .. g0+31 of one RVE (slot
+// order), drawn by one warp.  Trial t (0..63) is try t & 1 of particle
+// g0 + (t >> 1); lane l owns trials l and 32 + l.  Each round every lane
+// evaluates one candidate of a pending trial -- when fewer than 32 trials are
+// pending, several lanes take consecutive candidates of one trial -- and a
+// trial takes its first accepted candidate, which is the candidate unit_dir
+// (unit_dir_f32 in the FP32 form) accepts, normalised the same way.
+// ---------------------------------------------------------------------------
+template <int DIM, bool F32>
+__device__ __forceinline__ void draw_warp(const RveDev *st, const Slot &d, int64_t g0, int np_w)
+{
+    using PT = typename SweepSmem<F32>::PT;
+    using DT = typename SweepSmem<F32>::DT;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const uint64_t seed = st->seed, sweep = st->sweep;
+    const uint64_t pidv = lane < np_w ? (uint64_t)d.pid[g0 + lane] : 0ull;
+    int nm[2] = {0, 0};
+    bool pend[2] = {(lane >> 1) < np_w, ((32 + lane) >> 1) < np_w};
+    DT res[2][3] = {{(DT)1, (DT)0, (DT)0}, {(DT)1, (DT)0, (DT)0}};
+    for (;;) {
+        const unsigned m0 = __ballot_sync(0xffffffffu, pend[0]), m1 = __ballot_sync(0xffffffffu, pend[1]);
+        const int c0 = __popc(m0), np = c0 + __popc(m1);
+        if (np == 0) break;
+        // the trial this lane evaluates (rank k among the pending ones) and
+        // its candidate index
+        const int k = lane % np, rep = lane / np;
+        const int tr = k < c0 ? nth_set(m0, k) : 32 + nth_set(m1, k - c0);
+        const int nmA = __shfl_sync(0xffffffffu, nm[0], tr & 31), nmB = __shfl_sync(0xffffffffu, nm[1], tr & 31);
+        const int mc = (tr < 32 ? nmA : nmB) + rep;
+        const uint64_t pidt = __shfl_sync(0xffffffffu, pidv, tr >> 1);
+        DT v[3] = {(DT)0, (DT)0, (DT)0}, s = (DT)0;
+        bool ok = false;
+        if (mc < MAX_CAND) {
+            if constexpr (F32) ok = cand_f32<DIM>(seed, sweep, pidt, (uint64_t)(tr & 1), (uint64_t)mc, v, s);
+            else ok = cand_f64<DIM>(seed, sweep, pidt, (uint64_t)(tr & 1), (uint64_t)mc, v, s);
+        }
+        DT w[3] = {(DT)0, (DT)0, (DT)0};
+        if (ok) {
+            if constexpr (F32) {
+                const float inv = rsqrtf(s);
+#pragma unroll
+                for (int a = 0; a < DIM; a++) w[a] = v[a] * inv;
+            } else {
+                const double nrm = __dsqrt_rn(s);
+#pragma unroll
+                for (int a = 0; a < DIM; a++) w[a] = __ddiv_rn(v[a], nrm);
+            }
+        }
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            // lanes rank, rank + np, ... evaluated candidates nm, nm + 1, ...
+            const int rank = h == 0 ? __popc(m0 & below) : c0 + __popc(m1 & below);
+            const bool mine = pend[h] && rank < 32;
+            int src = -1, nas = 0;
+            if (mine) {
+                for (int i = rank; i < 32; i += np) {
+                    nas++;
+                    if (src < 0 && ((okm >> i) & 1u)) src = i;
+                }
+            }
+            DT x[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) x[a] = __shfl_sync(0xffffffffu, w[a], src < 0 ? lane : src);
+            if (mine) {
+                if (src >= 0) {
+                    res[h][0] = x[0];
+                    res[h][1] = x[1];
+                    res[h][2] = DIM == 3 ? x[2] : (DT)0;
+                    pend[h] = false;
+                } else {
+                    nm[h] += nas;
+                    if (nm[h] >= MAX_CAND) pend[h] = false;  // no candidate accepted: e_0
+                }
+            }
+        }
+    }
+    PT *out = reinterpret_cast<PT *>(st->dirs) + 2 * g0;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int t = 32 * h + lane;
+        if ((t >> 1) < np_w) {
+            PT e;
+            e.x = res[h][0];
+            e.y = res[h][1];
+            e.z = res[h][2];
+            e.w = (DT)0;
+            out[t] = e;
+        }
+    }
+}
+
+// One thread block per 256 particles of one RVE (the particle-indexed block
+// ranges of the group), eight warps of 32 particles.
+template <bool F32>
+__global__ void __launch_bounds__(256) k_draw(BatchDev *bd)
+{
+    const int r = block_rve(bd->blk_p, bd->B);
+    const RveDev *st = bd->rv[r];
+    if (!st->active) return;
+    const int64_t g0 = (int64_t)(blockIdx.x - bd->blk_p[r]) * 256 + (threadIdx.x & ~31);
+    const int n = st->n;
+    if (g0 >= n) return;
+    const int np_w = n - g0 < 32 ? (int)(n - g0) : 32;
+    const Slot d = st->slot[st->dst_idx];
+    if (st->dim == 3) draw_warp<3, F32>(st, d, g0, np_w);
+    else draw_warp<2, F32>(st, d, g0, np_w);
+}
+
+// ---------------------------------------------------------------------------
+// Dependencies of a cell in the one-launch sweep: before a cell of colour chi
+// is staged, every non-empty cell within reach (home +-H) whose colour is
+// lower must have finished this sweep -- exactly the cells of lower colour
+// whose moves the serial order lets it see; cells of higher colour wait for
+// this one in turn, so they are still unmoved.  Cells are handed out in
+// colour order, so every cell waited for is already held by a running warp.
+// A wait gives up after wait_limit polls and sets the RVE's status (the host
+// reports SRM_E_DEVICE_TIMEOUT).
+// ---------------------------------------------------------------------------
 template <int DIM>
 __device__ __forceinline__ void wait_lower_colours(RveDev *st, const uint32_t *cs, int hx, int hy, int hz, int chi,
                                                    uint32_t epoch)
@@ -111,14 +268,23 @@ __device__ __forceinline__ void wait_lower_colours(RveDev *st, const uint32_t *c
             __nanosleep(64);
         }
     }
+    // the producer's writes happen before its release store, which
+    // synchronises with this lane's acquire load; the warp barrier orders
+    // that load before every lane's later reads
     __syncwarp();
-    __threadfence();
 }
+
+// Work counters of one cell, reduced per warp after the cell.
+struct CellCount {
+    int moved = 0;
+    unsigned examined = 0;          // pairs tested (this lane)
+    unsigned long long trials = 0;  // trials evaluated (warp-uniform)
+    unsigned long long alg5 = 0;    // trials x (3^d stencil population - 1)
+};
 
 // One cell of colour chi (work item t of its RVE), processed by one warp.
 template <int DIM, bool F32>
-__device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned char *base, int cap,
-                                           int &moved, unsigned &examined, bool dataflow)
+__device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned char *base, int cap, CellCount &cc)
 {
     using PT = typename SweepSmem<F32>::PT;
     using DT = typename SweepSmem<F32>::DT;
@@ -127,7 +293,7 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
     PT *cpos = reinterpret_cast<PT *>(base + ST_HDR);
     float4 *capx = reinterpret_cast<float4 *>(cpos + cap);  // FP64 form only
     PT *nbuf = reinterpret_cast<PT *>(F32 ? (void *)(cpos + cap) : (void *)(capx + cap));
-    DT *pre = reinterpret_cast<DT *>(nbuf + NEAR_CAP);      // [PRE_NH][PRE_TRIALS][3]
+    PT *pre = nbuf + NEAR_CAP;                               // [PRE_NH][PRE_TRIALS]
 
     const Slot d = st->slot[st->dst_idx];
     PT *pos = reinterpret_cast<PT *>(d.pos);
@@ -139,333 +305,293 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
     const float cmf = (float)c_m;
     const float g1 = 1.0f + st->guard;
     const int N_l = st->N_l;
+
+    const int hx = 3 * (t % s0) + chi % 3;
+    const int hy = 3 * ((t / s0) % s1) + (chi / 3) % 3;
+    const int hz = DIM == 3 ? 3 * (t / (s0 * s1)) + chi / 9 : 0;
+    const int cell = hx + st->gn[0] * (hy + st->gn[1] * hz);
+    const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
+    if (nh == 0) return;  // nothing moves: nobody waits for an empty cell
+    const uint32_t epoch = (uint32_t)(st->sweep + 1);
+    wait_lower_colours<DIM>(st, cs, hx, hy, hz, chi, epoch);
+    // the pre-drawn directions of the cell's particles (slot order = the
+    // cell's particles in ascending id), copied while the stencil is staged
+    const uint32_t npre = nh < (uint32_t)PRE_NH ? nh : (uint32_t)PRE_NH;
     {
-        const int hx = 3 * (t % s0) + chi % 3;
-        const int hy = 3 * ((t / s0) % s1) + (chi / 3) % 3;
-        const int hz = DIM == 3 ? 3 * (t / (s0 * s1)) + chi / 9 : 0;
-        const int cell = hx + st->gn[0] * (hy + st->gn[1] * hz);
-        const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
-        if (nh == 0) return;  // nothing moves: nobody waits for an empty cell
-        const uint32_t epoch = (uint32_t)(st->sweep + 1);
-        if (dataflow) wait_lower_colours<DIM>(st, cs, hx, hy, hz, chi, epoch);
-        int nst, center;
-        const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
-        // home corner (FP64 form: the binary32 copies are relative to it)
-        const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
-        auto fetch = [&](uint32_t k, uint32_t &g) -> PT {
-            const int j = find_cell(S, nst, k);
-            g = S.b[j] + (k - S.o[j]);
-            PT c = pos[g];
-            if constexpr (F32) {
-                c.x += (float)S.sh[j][0] * w[0];
-                c.y += (float)S.sh[j][1] * w[1];
-                c.z += (float)S.sh[j][2] * w[2];
-            }
-            return c;
-        };
-        auto approx = [&](const PT &c) -> float4 {
-            if constexpr (F32) {
-                return c;
-            } else {
-                double ex = c.x - ox, ey = c.y - oy, ez = DIM == 3 ? c.z - oz : 0.0;
-                if (ex > st->halfL[0]) ex -= st->L[0];
-                if (ex < -st->halfL[0]) ex += st->L[0];
-                if (ey > st->halfL[1]) ey -= st->L[1];
-                if (ey < -st->halfL[1]) ey += st->L[1];
-                if (DIM == 3) {
-                    if (ez > st->halfL[2]) ez -= st->L[2];
-                    if (ez < -st->halfL[2]) ez += st->L[2];
-                }
-                return make_float4((float)ex, (float)ey, (float)ez, (float)c.w);
-            }
-        };
-        // largest radius among the particles of the home cell
-        float rh = 0.f;
-        for (uint32_t m = lane; m < nh; m += 32) rh = fmaxf(rh, (float)pos[hb + m].w);
-        for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
-        // 1. stage the candidates that can reach the home cell (home first)
-        // Staging stops at the first 32-candidate chunk that would overflow
-        // the capacity; candidates from kstop on are read from global memory
-        // (culled the same way) when the near lists are built.
-        uint32_t Tk = 0, kstop = T;
-        for (uint32_t k0 = 0; k0 < T; k0 += 32) {
-            const uint32_t k = k0 + lane;
-            bool keep = false;
-            PT c;
-            float4 ca;
-            if (k < T) {
-                uint32_t g;
-                c = fetch(k, g);
-                ca = approx(c);
-                const float r = rh + ca.w + 2.f * cmf;
-                keep = k < nh || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (Tk + __popc(bal) > (uint32_t)cap) {
-                kstop = k0;
-                break;
-            }
-            const uint32_t at = Tk + __popc(bal & ((1u << lane) - 1u));
-            if (keep) {
-                cpos[at] = c;
-                if constexpr (!F32) capx[at] = ca;
-            }
-            Tk += __popc(bal);
+        const PT *src = reinterpret_cast<const PT *>(st->dirs) + 2 * (size_t)hb;
+        constexpr int PIECES = (int)(sizeof(PT) / 16);
+        for (uint32_t e = lane; e < npre * PRE_TRIALS * PIECES; e += 32)
+            cp_async16(reinterpret_cast<unsigned char *>(pre) + 16 * (size_t)e,
+                       reinterpret_cast<const unsigned char *>(src) + 16 * (size_t)e);
+    }
+    int nst, center;
+    const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
+    // population of the 3^d cells around the home cell (Algorithm 5's own
+    // candidate set; the listed stencil is larger when H = 2)
+    uint32_t T3 = 0;
+    for (int j = lane; j < nst; j += 32)
+        if (S.sh[j][0] >= -1 && S.sh[j][0] <= 1 && S.sh[j][1] >= -1 && S.sh[j][1] <= 1 && S.sh[j][2] >= -1 &&
+            S.sh[j][2] <= 1)
+            T3 += S.o[j + 1] - S.o[j];
+    T3 = __reduce_add_sync(0xffffffffu, T3);
+    // home corner (FP64 form: the binary32 copies are relative to it)
+    const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
+    auto locate = [&](uint32_t k, int &j) -> uint32_t {
+        j = find_cell(S, nst, k);
+        return S.b[j] + (k - S.o[j]);
+    };
+    auto shift = [&](PT c, int j) -> PT {
+        if constexpr (F32) {
+            c.x = __fmaf_rn((float)S.sh[j][0], w[0], c.x);
+            c.y = __fmaf_rn((float)S.sh[j][1], w[1], c.y);
+            c.z = __fmaf_rn((float)S.sh[j][2], w[2], c.z);
         }
-        const bool staged = kstop == T;
-        if (!staged && lane == 0) atomicAdd(&st->stage_overflow, 1ull);
-        // the first trial directions of every home particle, drawn in
-        // parallel (they depend on the particle id and the counters only)
-        const uint32_t npre = nh < (uint32_t)PRE_NH ? nh : (uint32_t)PRE_NH;
-        for (uint32_t e = lane; e < npre * PRE_TRIALS; e += 32) {
-            const uint32_t m = e / PRE_TRIALS, l = e % PRE_TRIALS;
-            const uint64_t pid = d.pid[hb + m];
-            DT *u = pre + 3 * e;
-            if constexpr (F32) {
-                float v[3];
-                unit_dir_f32<DIM>(seed, sweep, pid, l, v);
-                u[0] = v[0];
-                u[1] = v[1];
-                u[2] = v[2];
-            } else {
-                double v[3];
-                unit_dir<DIM>(seed, sweep, pid, l, v);
-                u[0] = v[0];
-                u[1] = v[1];
-                u[2] = v[2];
+        return c;
+    };
+    auto fetch = [&](uint32_t k, uint32_t &g) -> PT {
+        int j;
+        g = locate(k, j);
+        return shift(pos[g], j);
+    };
+    auto approx = [&](const PT &c) -> float4 {
+        if constexpr (F32) {
+            return c;
+        } else {
+            double ex = c.x - ox, ey = c.y - oy, ez = DIM == 3 ? c.z - oz : 0.0;
+            if (ex > st->halfL[0]) ex -= st->L[0];
+            if (ex < -st->halfL[0]) ex += st->L[0];
+            if (ey > st->halfL[1]) ey -= st->L[1];
+            if (ey < -st->halfL[1]) ey += st->L[1];
+            if (DIM == 3) {
+                if (ez > st->halfL[2]) ez -= st->L[2];
+                if (ez < -st->halfL[2]) ez += st->L[2];
             }
+            return make_float4((float)ex, (float)ey, (float)ez, (float)c.w);
+        }
+    };
+
+    // 1. stage the candidates that can reach the home cell (home first).
+    // The load of the next 32-candidate chunk is issued before the current
+    // one is culled.  Staging stops at the first chunk that would overflow
+    // the capacity; candidates from kstop on are read from global memory
+    // (culled the same way) when the near lists are built.
+    float rh = 0.f;
+    for (uint32_t m = lane; m < nh; m += 32) rh = fmaxf(rh, (float)pos[hb + m].w);
+    for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
+    uint32_t Tk = 0, kstop = T;
+    bool stop = false;
+    PT cn;
+    int jn = 0;
+    if (lane < T) cn = pos[locate(lane, jn)];
+    for (uint32_t k0 = 0; k0 < T; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        const PT c = k < T ? shift(cn, jn) : cn;
+        if (k + 32 < T) cn = pos[locate(k + 32, jn)];
+        bool keep = false;
+        float4 ca;
+        if (k < T) {
+            ca = approx(c);
+            const float r = rh + ca.w + 2.f * cmf;
+            keep = k < nh || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (Tk + __popc(bal) > (uint32_t)cap) {
+            kstop = k0;
+            stop = true;
+            break;
+        }
+        const uint32_t at = Tk + __popc(bal & ((1u << lane) - 1u));
+        if (keep) {
+            cpos[at] = c;
+            if constexpr (!F32) capx[at] = ca;
+        }
+        Tk += __popc(bal);
+    }
+    if (stop && lane == 0) atomicAdd(&st->stage_overflow, 1ull);
+    cp_async_wait();
+    __syncwarp();
+
+    // 2. the particles of the home cell, ascending id
+    const uint32_t scan = Tk + (T - kstop);
+    for (uint32_t m = 0; m < nh; m++) {
+        const uint32_t gi = hb + m;
+        // home particles lead the candidate list and are always kept, so
+        // the first ones are staged at their own index
+        const PT p = m < Tk ? cpos[m] : pos[gi];
+        const float4 pa = approx(p);
+        const bool have_pre = m < (uint32_t)PRE_NH;
+        // near list: copies of every candidate within R_i + R_t + c_m
+        // (staged candidates, then the unstaged remainder from global)
+        uint32_t nn = 0;
+        for (uint32_t k0 = 0; k0 < scan; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            bool nb = false;
+            PT c;
+            if (k < scan) {
+                float4 ca;
+                bool self;
+                if (k < Tk) {
+                    self = k == m;
+                    c = cpos[k];
+                    if constexpr (F32) ca = c;
+                    else ca = capx[k];
+                } else {
+                    uint32_t g;
+                    c = fetch(kstop + (k - Tk), g);
+                    self = g == gi;
+                    ca = approx(c);
+                }
+                nb = !self && within_f32(pa, ca, pa.w + ca.w + cmf, DIM);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, nb);
+            const uint32_t at = nn + __popc(bal & ((1u << lane) - 1u));
+            if (nb && at < NEAR_CAP) nbuf[at] = c;
+            nn += __popc(bal);
         }
         __syncwarp();
-
-        // 2. the particles of the home cell, ascending id
-        for (uint32_t m = 0; m < nh; m++) {
-            const uint32_t gi = hb + m;
-            // home particles lead the candidate list and are always kept, so
-            // the first ones are staged at their own index
-            const PT p = m < Tk ? cpos[m] : pos[gi];
-            const float4 pa = approx(p);
-            const uint64_t pid = d.pid[gi];
-            // near list: copies of every candidate within R_i + R_t + c_m
-            // (staged candidates, then the unstaged remainder from global)
-            uint32_t nn = 0;
-            const uint32_t scan = Tk + (T - kstop);
-            for (uint32_t k0 = 0; k0 < scan; k0 += 32) {
-                const uint32_t k = k0 + lane;
-                bool nb = false;
-                PT c;
-                if (k < scan) {
-                    float4 ca;
-                    bool self;
-                    if (k < Tk) {
-                        self = k == m;
-                        c = cpos[k];
-                        if constexpr (F32) ca = c;
-                        else ca = capx[k];
+        const bool use_near = nn <= NEAR_CAP;
+        bool done = false;
+        int l0 = 0;
+        PT np;
+        // trials in batches, one trial per lane -- the two pre-drawn ones
+        // first (most particles take the first trial), then eight at a time
+        // drawn by all lanes -- each tested against the near list
+        while (!done && l0 < N_l) {
+            const bool first = l0 == 0 && have_pre;
+            const int bsz = first ? PRE_TRIALS : 8;
+            const int lmax = N_l - l0 < bsz ? N_l - l0 : bsz;
+            double qt[3] = {0.0, 0.0, 0.0};
+            float qs[3] = {0.f, 0.f, 0.f};
+            DT u[3] = {(DT)0, (DT)0, (DT)0};
+            if (first) {
+                if (lane < lmax) {
+                    const PT e = pre[PRE_TRIALS * m + lane];
+                    u[0] = e.x;
+                    u[1] = e.y;
+                    u[2] = e.z;
+                }
+            } else {
+                draw8<DIM, F32>(seed, sweep, (uint64_t)d.pid[gi], l0, u);
+            }
+            if (lane < lmax) {
+                if constexpr (F32) {
+                    qs[0] = trial_f32(p.x, cmf, u[0]);
+                    qs[1] = trial_f32(p.y, cmf, u[1]);
+                    qs[2] = DIM == 3 ? trial_f32(p.z, cmf, u[2]) : p.z;
+                } else {
+                    qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, u[0])), st->L[0]);
+                    qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, u[1])), st->L[1]);
+                    qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, u[2])), st->L[2]) : p.z;
+                }
+            }
+            l0 += lmax;
+            for (int l = 0; l < lmax; l++) {
+                double q[3] = {0.0, 0.0, 0.0};
+                float qf[3] = {0.f, 0.f, 0.f};
+                if constexpr (F32) {
+                    qf[0] = __shfl_sync(0xffffffffu, qs[0], l);
+                    qf[1] = __shfl_sync(0xffffffffu, qs[1], l);
+                    qf[2] = __shfl_sync(0xffffffffu, qs[2], l);
+                } else {
+                    q[0] = __shfl_sync(0xffffffffu, qt[0], l);
+                    q[1] = __shfl_sync(0xffffffffu, qt[1], l);
+                    q[2] = __shfl_sync(0xffffffffu, qt[2], l);
+                }
+                cc.trials++;
+                bool hit = false;
+                const uint32_t L = use_near ? nn : scan;
+                for (uint32_t kk = lane; kk < L && !hit; kk += 32) {
+                    PT c;
+                    if (use_near) {
+                        c = nbuf[kk];
+                    } else if (kk < Tk) {
+                        if (kk == m) continue;
+                        c = cpos[kk];
                     } else {
                         uint32_t g;
-                        c = fetch(kstop + (k - Tk), g);
-                        self = g == gi;
-                        ca = approx(c);
+                        c = fetch(kstop + (kk - Tk), g);
+                        if (g == gi) continue;
                     }
-                    nb = !self && within_f32(pa, ca, pa.w + ca.w + cmf, DIM);
+                    cc.examined++;
+                    if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
+                    else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, nb);
-                const uint32_t at = nn + __popc(bal & ((1u << lane) - 1u));
-                if (nb && at < NEAR_CAP) nbuf[at] = c;
-                nn += __popc(bal);
-            }
-            __syncwarp();
-            const bool use_near = nn <= NEAR_CAP;
-            bool done = false;
-            // trials in batches, one per lane: 2 first (most particles take
-            // the first trial), then 8 at a time
-            for (int l0 = 0; l0 < N_l && !done;) {
-                const int bsz = (l0 == 0 && m < (uint32_t)PRE_NH) ? PRE_TRIALS : 8;
-                const int lmax = N_l - l0 < bsz ? N_l - l0 : bsz;
-                double qt[3] = {0.0, 0.0, 0.0};
-                float qs[3] = {0.f, 0.f, 0.f};
-                if (l0 == 0 && m < (uint32_t)PRE_NH) {
-                    // first trials: drawn up front for the whole cell
-                    if (lane < lmax) {
-                        const DT *up = pre + 3 * (m * PRE_TRIALS + lane);
-                        if constexpr (F32) {
-                            qs[0] = p.x + cmf * up[0];
-                            qs[1] = p.y + cmf * up[1];
-                            qs[2] = DIM == 3 ? p.z + cmf * up[2] : p.z;
-                        } else {
-                            qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, up[0])), st->L[0]);
-                            qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, up[1])), st->L[1]);
-                            qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, up[2])), st->L[2]) : p.z;
-                        }
-                    }
-                } else {
-                    // later trials: eight at a time, candidates drawn by all lanes
-                    DT u[3];
-                    draw8<DIM, F32>(seed, sweep, pid, l0, u);
-                    if (lane < lmax) {
-                        if constexpr (F32) {
-                            qs[0] = p.x + cmf * u[0];
-                            qs[1] = p.y + cmf * u[1];
-                            qs[2] = DIM == 3 ? p.z + cmf * u[2] : p.z;
-                        } else {
-                            qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, u[0])), st->L[0]);
-                            qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, u[1])), st->L[1]);
-                            qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, u[2])), st->L[2]) : p.z;
-                        }
-                    }
-                }
-                l0 += lmax;
-                for (int l = 0; l < lmax; l++) {
-                    double q[3] = {0.0, 0.0, 0.0};
-                    float qf[3] = {0.f, 0.f, 0.f};
-                    if constexpr (F32) {
-                        qf[0] = __shfl_sync(0xffffffffu, qs[0], l);
-                        qf[1] = __shfl_sync(0xffffffffu, qs[1], l);
-                        qf[2] = __shfl_sync(0xffffffffu, qs[2], l);
-                    } else {
-                        q[0] = __shfl_sync(0xffffffffu, qt[0], l);
-                        q[1] = __shfl_sync(0xffffffffu, qt[1], l);
-                        q[2] = __shfl_sync(0xffffffffu, qt[2], l);
-                    }
-                    bool hit = false;
-                    const uint32_t L = use_near ? nn : scan;
-                    for (uint32_t kk = lane; kk < L && !hit; kk += 32) {
-                        PT c;
-                        if (use_near) {
-                            c = nbuf[kk];
-                        } else if (kk < Tk) {
-                            if (kk == m) continue;
-                            c = cpos[kk];
-                        } else {
-                            uint32_t g;
-                            c = fetch(kstop + (kk - Tk), g);
-                            if (g == gi) continue;
-                        }
-                        examined++;
-                        if constexpr (F32) {
-                            const float ex = qf[0] - c.x, ey = qf[1] - c.y;
-                            float d2 = ex * ex + ey * ey;
-                            if (DIM == 3) {
-                                const float ez = qf[2] - c.z;
-                                d2 += ez * ez;
-                            }
-                            const float rs = p.w + c.w;
-                            hit = d2 <= rs * rs * g1;
-                        } else {
-                            hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
-                        }
-                    }
-                    if (!__any_sync(0xffffffffu, hit)) {
-                        if (lane == 0) {
-                            PT np;
-                            if constexpr (F32) np = make_float4(qf[0], qf[1], qf[2], p.w);
-                            else np = make_double4_32a(q[0], q[1], q[2], p.w);
-                            if (m < Tk) {
-                                cpos[m] = np;
-                                if constexpr (!F32) capx[m] = approx(np);
-                            }
-                            pos[gi] = np;
-                        }
-                        moved++;
-                        done = true;
-                        __syncwarp();
-                        break;
-                    }
+                if (!__any_sync(0xffffffffu, hit)) {
+                    if constexpr (F32) np = make_float4(qf[0], qf[1], qf[2], p.w);
+                    else np = make_double4_32a(q[0], q[1], q[2], p.w);
+                    done = true;
+                    break;
                 }
             }
-            if (lane == 0) st->flags[gi] = done ? 1 : 0;
-            __syncwarp();
         }
-        if (dataflow && lane == 0) {
-            __threadfence();
-            st_release(&st->done[cell], epoch);
+        if (done) {
+            if (lane == 0) {
+                if (m < Tk) {
+                    cpos[m] = np;
+                    if constexpr (!F32) capx[m] = approx(np);
+                }
+                pos[gi] = np;
+            }
+            cc.moved++;
         }
+        if (lane == 0) st->flags[gi] = done ? 1 : 0;
         __syncwarp();
     }
+    cc.alg5 += cc.trials * (unsigned long long)(T3 - 1);
+    // lane 0 wrote every global update of this cell (positions, flags), so
+    // its release store publishes them
+    if (lane == 0) st_release(&st->done[cell], epoch);
+    __syncwarp();
 }
 
-// One launch per colour over all RVEs of the batch: each warp takes the next
-// (RVE, cell) work item from the colour's counter.  2D RVEs have 9 colours.
-// Blocks per SM the register allocation must allow (a build-time knob).
+// Blocks per SM the register allocation must allow (build-time knobs; the
+// defaults are the fastest measured without spills: 96 registers for the
+// FP32 form, 128 for the FP64 form).
 #ifndef SRM_SWEEP_MIN_BLOCKS
-#define SRM_SWEEP_MIN_BLOCKS 1
+#define SRM_SWEEP_MIN_BLOCKS 5
+#endif
+#ifndef SRM_SWEEP_MIN_BLOCKS_F64
+#define SRM_SWEEP_MIN_BLOCKS_F64 4
 #endif
 
-template <bool F32>
-__global__ void __launch_bounds__(SW_WARPS * 32, SRM_SWEEP_MIN_BLOCKS) k_sweep(BatchDev *bd, int chi, int cap)
+// The sweep of the DIM-dimensional RVEs of the group, all colours in one
+// launch: work item tg is cell tg mod W of colour tg / W, W the colour cells
+// of all DIM-dimensional RVEs at work (offsets act), so items are handed out
+// in colour order.
+template <int DIM, bool F32>
+__global__ void __launch_bounds__(SW_WARPS * 32, F32 ? SRM_SWEEP_MIN_BLOCKS : SRM_SWEEP_MIN_BLOCKS_F64)
+    k_sweep_df(BatchDev *bd, int cap)
 {
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
     const int B = bd->B;
-    const int32_t *off = chi < 9 ? bd->act : bd->act3;  // RVEs at work with this colour
-    const int total = off[B];
+    const int32_t *off = DIM == 3 ? bd->act3 : bd->act2;
+    uint32_t *wq = &bd->wq[DIM == 3 ? 0 : 1];
+    const int W = off[B];
+    const int total = W * (DIM == 3 ? 27 : 9);
     for (;;) {
         int tg = 0, r = 0;
         if (lane == 0) {
-            tg = (int)atomicAdd(&bd->wq[chi], 1u);
-            if (tg < total) r = find_seg(off, B, tg);
+            tg = (int)atomicAdd(wq, 1u);
+            if (tg < total) r = find_seg(off, B, tg % W);
         }
         tg = __shfl_sync(0xffffffffu, tg, 0);
         if (tg >= total) break;
         r = __shfl_sync(0xffffffffu, r, 0);
+        const int chi = tg / W, t = tg % W - off[r];
         RveDev *st = bd->rv[r];
-        const int t = tg - off[r];
-        if (!st->active || t >= st->nsub) continue;
-        int moved = 0;
-        unsigned examined = 0;
-        if (st->dim == 3) {
-            sweep_cell<3, F32>(st, chi, t, base, cap, moved, examined, false);
-        } else {
-            if (chi >= 9) continue;
-            sweep_cell<2, F32>(st, chi, t, base, cap, moved, examined, false);
-        }
-        examined = __reduce_add_sync(0xffffffffu, examined);
+        if (!st->active || st->dim != DIM || t >= st->nsub) continue;
+        CellCount cc;
+        sweep_cell<DIM, F32>(st, chi, t, base, cap, cc);
+        const unsigned examined = __reduce_add_sync(0xffffffffu, cc.examined);
         if (lane == 0) {
-            if (moved) atomicAdd(&st->red[3], (unsigned long long)moved);
+            if (cc.moved) atomicAdd(&st->red[3], (unsigned long long)cc.moved);
             if (examined) atomicAdd(&st->pairs_sweep, (unsigned long long)examined);
-        }
-    }
-}
-
-// All colours in one launch: work items are handed out in colour order from
-// one counter; each cell waits for its lower-colour neighbours
-// (wait_lower_colours) and stamps itself when done.
-template <bool F32>
-__global__ void __launch_bounds__(SW_WARPS * 32, SRM_SWEEP_MIN_BLOCKS) k_sweep_df(BatchDev *bd, int cap)
-{
-    extern __shared__ __align__(32) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
-    const int B = bd->B;
-    const int total = bd->coff[27];
-    for (;;) {
-        int tg = 0, chi = 0, r = 0, t = 0;
-        if (lane == 0) {
-            tg = (int)atomicAdd(&bd->wq[0], 1u);
-            if (tg < total) {
-                chi = find_seg(bd->coff, 27, tg);
-                const int local = tg - bd->coff[chi];
-                const int32_t *off = chi < 9 ? bd->act : bd->act3;
-                r = find_seg(off, B, local);
-                t = local - off[r];
+            if (cc.trials) {
+                atomicAdd(&st->trials, cc.trials);
+                atomicAdd(&st->pairs_alg5, cc.alg5);
             }
-        }
-        tg = __shfl_sync(0xffffffffu, tg, 0);
-        if (tg >= total) break;
-        chi = __shfl_sync(0xffffffffu, chi, 0);
-        r = __shfl_sync(0xffffffffu, r, 0);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        RveDev *st = bd->rv[r];
-        if (!st->active || t >= st->nsub) continue;
-        int moved = 0;
-        unsigned examined = 0;
-        if (st->dim == 3) sweep_cell<3, F32>(st, chi, t, base, cap, moved, examined, true);
-        else sweep_cell<2, F32>(st, chi, t, base, cap, moved, examined, true);
-        examined = __reduce_add_sync(0xffffffffu, examined);
-        if (lane == 0) {
-            if (moved) atomicAdd(&st->red[3], (unsigned long long)moved);
-            if (examined) atomicAdd(&st->pairs_sweep, (unsigned long long)examined);
         }
     }
 }
@@ -489,33 +615,32 @@ static int resident_blocks(K kern, size_t smem)
     return nb > 0 ? nb : 1;
 }
 
-void launch_sweep_colour(const BatchShape &b, int chi, cudaStream_t s)
+template <int DIM, bool F32>
+static void launch_sweep_dim(const BatchShape &b, cudaStream_t s)
 {
-    const int cap = b.cap;
-    const size_t smem = sweep_smem(b.f32, cap);
-    const int64_t want64 = (b.sub_total + SW_WARPS - 1) / SW_WARPS;
+    const size_t smem = sweep_smem(F32, b.cap);
+    const int64_t want64 = (b.sub_total * (DIM == 3 ? 27 : 9) + SW_WARPS - 1) / SW_WARPS;
     const int want = (int)(want64 > 0x7fffffff ? 0x7fffffff : want64);
-    auto shape = [&](auto kern) {
-        const int res = resident_blocks(kern, smem) * (g_sms > 0 ? g_sms : 1);
-        return want < res ? want : res;
-    };
-    if (b.f32) k_sweep<true><<<shape(k_sweep<true>), SW_WARPS * 32, smem, s>>>(b.d, chi, cap);
-    else k_sweep<false><<<shape(k_sweep<false>), SW_WARPS * 32, smem, s>>>(b.d, chi, cap);
+    const int res = resident_blocks(k_sweep_df<DIM, F32>, smem) * (g_sms > 0 ? g_sms : 1);
+    k_sweep_df<DIM, F32><<<want < res ? want : res, SW_WARPS * 32, smem, s>>>(b.d, b.cap);
 }
 
+// Trial directions (k_draw), then the sweep of the 3D and of the 2D RVEs.
 void launch_sweep(const BatchShape &b, cudaStream_t s)
 {
-    const int cap = b.cap;
-    const size_t smem = sweep_smem(b.f32, cap);
-    const int64_t want64 = (b.sub_total * (b.has3d ? 27 : 9) + SW_WARPS - 1) / SW_WARPS;
-    const int want = (int)(want64 > 0x7fffffff ? 0x7fffffff : want64);
-    auto shape = [&](auto kern) {
-        const int res = resident_blocks(kern, smem) * (g_sms > 0 ? g_sms : 1);
-        return want < res ? want : res;
-    };
-    if (b.f32) k_sweep_df<true><<<shape(k_sweep_df<true>), SW_WARPS * 32, smem, s>>>(b.d, cap);
-    else k_sweep_df<false><<<shape(k_sweep_df<false>), SW_WARPS * 32, smem, s>>>(b.d, cap);
+    if (b.f32) k_draw<true><<<b.blocks_p, 256, 0, s>>>(b.d);
+    else k_draw<false><<<b.blocks_p, 256, 0, s>>>(b.d);
+    if (b.has3d) {
+        if (b.f32) launch_sweep_dim<3, true>(b, s);
+        else launch_sweep_dim<3, false>(b, s);
+    }
+    if (b.has2d) {
+        if (b.f32) launch_sweep_dim<2, true>(b, s);
+        else launch_sweep_dim<2, false>(b, s);
+    }
 }
+
+int sweep_launches(const BatchShape &b) { return 1 + (b.has3d ? 1 : 0) + (b.has2d ? 1 : 0); }
 
 // Dynamic shared memory above 48 KB needs an opt-in per kernel.
 void sweep_configure()
@@ -525,14 +650,11 @@ void sweep_configure()
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep_smem(true, sweep_cap_max(true)));
-    cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep_smem(false, sweep_cap_max(false)));
-    cudaFuncSetAttribute(k_sweep_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep_smem(true, sweep_cap_max(true)));
-    cudaFuncSetAttribute(k_sweep_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep_smem(false, sweep_cap_max(false)));
+    const int s32 = (int)sweep_smem(true, sweep_cap_max(true)), s64 = (int)sweep_smem(false, sweep_cap_max(false));
+    cudaFuncSetAttribute(k_sweep_df<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    cudaFuncSetAttribute(k_sweep_df<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    cudaFuncSetAttribute(k_sweep_df<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    cudaFuncSetAttribute(k_sweep_df<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
 }
 
 }  // namespace srm

@@ -127,8 +127,14 @@ static int staging_estimate(const Prep &q)
         std::nth_element(tpop.begin(), tpop.begin() + (ptrdiff_t)qi, tpop.end());
         t95 = tpop[qi];
     }
+    // staged = candidates within R_home,max + R_t + 2 c_m of the home box;
+    // radii taken as 1.2 x the mean (capped at the largest), since a cell
+    // holds few particles and most candidates are of typical size
+    double rsum = 0.0;
+    for (double v : q.r) rsum += v;
+    const double rtyp = std::min(q.rmax, 1.2 * rsum / (double)(q.r.empty() ? 1 : q.r.size()));
     const double wt = q.L[0] / (double)pa[0];
-    const double reach = 2.0 * (2.0 * q.lam_t * q.rmax + 2.0 * q.p.c_m);
+    const double reach = 2.0 * (2.0 * q.lam_t * rtyp + 2.0 * q.p.c_m);
     double frac = (wt + reach) / (3.0 * wt);
     frac = frac > 1.0 ? 1.0 : frac;
     frac = q.dim == 3 ? frac * frac * frac : frac * frac;
@@ -303,6 +309,7 @@ srm_status member_alloc(Group &g, Member &mb, int64_t n_cap, int64_t ncells_cap,
     s.pcount = (uint32_t *)A(sizeof(uint32_t) * (n + 1));
     s.red = (unsigned long long *)A(sizeof(unsigned long long) * 8);
     s.done = (uint32_t *)A(sizeof(uint32_t) * (size_t)ncells_cap);
+    s.dirs = A((g.f32 ? sizeof(float4) : sizeof(double4_32a)) * 2 * n);
     mb.d = (RveDev *)A(sizeof(RveDev));
     mb.stage_x = (double *)A(sizeof(double) * 3 * n);
     mb.stage_r = (double *)A(sizeof(double) * n);
@@ -369,7 +376,7 @@ srm_status member_load(Group &g, Member &mb, const Prep &q)
     s.it_result = s.it_k = s.it_shake = 0;
     s.it_overlap = s.moved_last = 0;
     s.status = 0;
-    s.pairs_sweep = s.pairs_check = s.stage_overflow = 0;
+    s.pairs_sweep = s.pairs_check = s.stage_overflow = s.trials = s.pairs_alg5 = 0;
     s.wait_limit = q.p.wait_limit == 0 ? (1 << 22) : q.p.wait_limit;
     mb.dim = q.dim;
     mb.n = q.n;
@@ -399,7 +406,7 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     const int B = (int)ms.size();
     std::vector<int32_t> off(5 * (size_t)(B + 1), 0);
     int32_t *bp = off.data(), *bc = bp + B + 1, *tc = bc + B + 1, *tn = tc + B + 1, *sb = tn + B + 1;
-    bool has3d = false;
+    bool has3d = false, has2d = false;
     for (int r = 0; r < B; r++) {
         const Member &mb = *ms[(size_t)r];
         bp[r + 1] = bp[r] + blocks(mb.n_cap, 256);
@@ -407,7 +414,8 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
         tc[r + 1] = tc[r] + blocks(mb.ncells_cap, srm::scan_tile());
         tn[r + 1] = tn[r] + blocks(mb.n_cap, srm::scan_tile());
         sb[r + 1] = sb[r] + (int32_t)mb.nsub_cap;
-        has3d = has3d || mb.dim == 3 || mb.slot3d;
+        has3d = has3d || mb.dim == 3 || mb.any_dim;
+        has2d = has2d || mb.dim == 2 || mb.any_dim;
     }
     BatchDev *d = (BatchDev *)dev_alloc(g, sizeof(BatchDev));
     int32_t *d_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * (off.size() + 2 * (size_t)(B + 1)));
@@ -423,9 +431,9 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     hb.tile_c = d_off + 2 * (B + 1);
     hb.tile_n = d_off + 3 * (B + 1);
     hb.sub = d_off + 4 * (B + 1);
-    hb.act = d_off + 5 * (B + 1);
+    hb.act2 = d_off + 5 * (B + 1);
     hb.act3 = d_off + 6 * (B + 1);
-    CK(cudaMemsetAsync(hb.act, 0, sizeof(int32_t) * 2 * (size_t)(B + 1), g.stream));
+    CK(cudaMemsetAsync(hb.act2, 0, sizeof(int32_t) * 2 * (size_t)(B + 1), g.stream));
     CK(cudaMemcpyAsync(d_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(d_rv, rv.data(), sizeof(RveDev *) * (size_t)B, cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(d, &hb, sizeof(BatchDev), cudaMemcpyHostToDevice, g.stream));
@@ -440,13 +448,15 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     sh.sub_total = sb[B];
     sh.f32 = g.f32;
     sh.has3d = has3d;
+    sh.has2d = has2d;
     sh.cap = g.cap;
     return SRM_OK;
 }
 
 // kernels of one super-step: begin and plan, binning (count, 3 scan passes,
-// scatter, stamp, in-cell sort), the sweep (all colours), check, control
-static int64_t kernels_per_superstep(bool) { return 2 + 7 + 1 + 1 + 1; }
+// scatter, stamp, in-cell sort), the trial draws and the sweep (one launch
+// per dimension present), check, control
+static int64_t kernels_per_superstep(const BatchShape &sh) { return 2 + 7 + srm::sweep_launches(sh) + 1 + 1; }
 
 static void enqueue_superstep(Group &g, cudaStream_t s, const std::vector<cudaEvent_t> *ev = nullptr)
 {
@@ -493,7 +503,7 @@ srm_status group_finalize(Group &g)
         std::vector<Member *> one{mb};
         if ((st = make_batchdev(g, one, &mb->solo_d, mb->solo)) != SRM_OK) return st;
     }
-    g.launches_per_step = kernels_per_superstep(g.sh.has3d);
+    g.launches_per_step = kernels_per_superstep(g.sh);
     const size_t B = g.m.size();
     if (cudaMallocHost((void **)&g.pin, sizeof(RveDev) * B) != cudaSuccess ||
         cudaMallocHost((void **)&g.pin_red, sizeof(unsigned long long) * 8) != cudaSuccess)
@@ -718,6 +728,8 @@ void fill_state(const Group &g, size_t r, srm_state_info *o)
     o->pairs_sweep = s.pairs_sweep;
     o->pairs_check = s.pairs_check;
     o->stage_overflow = s.stage_overflow;
+    o->trials = s.trials;
+    o->pairs_alg5 = s.pairs_alg5;
     o->stage_capacity = g.cap;
 }
 

@@ -76,8 +76,14 @@ struct RveDev {
     // work counters: candidate pairs examined by the sweep and by the check
     unsigned long long pairs_sweep, pairs_check;
     unsigned long long stage_overflow;  // cells whose culled stencil exceeded the staging capacity
+    unsigned long long trials;          // trial moves evaluated by the sweeps
+    unsigned long long pairs_alg5;      // trials x (particles of the 3^d cells around the home cell - 1)
     uint32_t *done;       // [ncells_cap] epoch stamp of the last sweep that finished the cell
     int32_t wait_limit;   // polls of one dependency before the sweep gives up (< 0: none)
+    // directions of trials 0 and 1 of every particle for the coming sweep,
+    // in the cell-sorted order of the destination slot: [2 n] float4 (FP32
+    // form) or double4_32a (FP64 form), entry 2 g + l for slot g, trial l
+    void *dirs;
 };
 
 // Device status codes (RveDev::status), reported by the host as srm_status.
@@ -88,7 +94,7 @@ constexpr int32_t STATUS_WAIT_TIMEOUT = 5;
 // tiles run one grid over all RVEs: each RVE owns a contiguous range of
 // blocks (offsets below, fixed by the RVE's capacities), so that a block
 // serves one RVE.  The sweep hands out (RVE, cell) work items from one
-// counter per colour.
+// counter per dimension, colour by colour.
 struct BatchDev {
     int32_t B;
     int32_t pad;
@@ -98,10 +104,9 @@ struct BatchDev {
     int32_t *tile_c;  // [B+1] first scan tile of each RVE over its cells
     int32_t *tile_n;  // [B+1] first scan tile of each RVE over its particles
     int32_t *sub;     // [B+1] first sweep work item of each RVE (cells of one colour)
-    int32_t *act;     // [B+1] the same over the RVEs at work in this super-step
-    int32_t *act3;    // [B+1] the same over the 3D RVEs at work (colours 9..26)
-    uint32_t wq[27];  // sweep work counters, one per colour
-    int32_t coff[28]; // first work item of each colour in the one-launch sweep
+    int32_t *act2;    // [B+1] first work item of each 2D RVE at work in this super-step
+    int32_t *act3;    // [B+1] the same over the 3D RVEs at work
+    uint32_t wq[2];   // sweep work counters: [0] 3D RVEs, [1] 2D RVEs
 };
 
 // Acquire load / release store of a 32-bit word in global memory (the
@@ -144,117 +149,69 @@ __device__ __forceinline__ int block_rve(const int32_t *off, int B)
 // 64x64 -> 128-bit products; the key is advanced by the Weyl constants
 // between rounds.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1)
+// One round: two 64x64 -> 128-bit products, words permuted and keyed.
+__device__ __forceinline__ void philox_round(uint64_t c[4], uint64_t k0, uint64_t k1)
 {
     const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+    const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+// COMPACT keeps the ten rounds as a loop: fewer registers, for the rare
+// draws inside the sweep (whose register budget sets its occupancy).
+template <bool COMPACT = false>
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1)
+{
     const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-#pragma unroll
-    for (int r = 0; r < 10; r++) {
-        if (r) {
+    if constexpr (COMPACT) {
+#pragma unroll 1
+        for (int r = 0; r < 10; r++) {
+            philox_round(c, k0, k1);
             k0 += W0;
             k1 += W1;
         }
-        const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
-        const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
-        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 10; r++) {
+            philox_round(c, k0, k1);
+            k0 += W0;
+            k1 += W1;
+        }
     }
 }
 
 constexpr uint64_t TAG_MOVE = 0x53524D2D4D4F5645ULL;  // "SRM-MOVE"
 constexpr int MAX_CAND = 32;
 
-// Uniform direction in DIM dimensions for (seed, sweep, particle, try):
-// candidate m is the Philox block at counter (pid, sweep, try, m), mapped to
-// the lattice point ((w_a >> 10) - 2^53) 2^-53 of [-1, 1)^DIM; the first with
-// 0 < |v|^2 <= 1 is divided by its norm.  All steps are exact or correctly
-// rounded binary64 operations.
-template <int DIM>
-__device__ __forceinline__ void unit_dir(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l,
-                                         double u[3])
-{
-    for (int m = 0; m < MAX_CAND; m++) {
-        uint64_t c[4] = {pid, sweep, l, (uint64_t)m};
-        philox4x64(c, seed, TAG_MOVE);
-        double v[3];
-#pragma unroll
-        for (int a = 0; a < DIM; a++)
-            v[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
-        double s = __dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1]));
-        if (DIM == 3) s = __dadd_rn(s, __dmul_rn(v[2], v[2]));
-        if (s > 0.0 && s <= 1.0) {
-            const double nrm = __dsqrt_rn(s);
-#pragma unroll
-            for (int a = 0; a < DIM; a++) u[a] = __ddiv_rn(v[a], nrm);
-            if (DIM == 2) u[2] = 0.0;
-            return;
-        }
-    }
-    u[0] = 1.0;
-    u[1] = 0.0;
-    u[2] = 0.0;
-}
+// Uniform direction in DIM dimensions for (seed, sweep, particle, try l):
+// candidate m is the Philox block at counter (pid, sweep, l, m), mapped to
+// the lattice point ((w_a >> 10) - 2^53) 2^-53 of [-1, 1)^DIM; the first
+// candidate with 0 < |v|^2 <= 1 is divided by its norm, and after MAX_CAND
+// rejected candidates the direction is e_0.  cand_f64 evaluates one
+// candidate in binary64 (exact or correctly rounded operations only; the
+// direction is v / sqrt(|v|^2), correctly rounded).  cand_f32 is the same
+// draw for the FP32 form, without binary64 arithmetic in the common case
+// (binary64 runs at 1/64 of the binary32 rate on this GPU): coordinate a is
+// the top 24 bits of the Philox word, v_a = ((w_a >> 40) - 2^23) 2^-23, the
+// binary64 lattice point truncated by less than 2^-23, so |v|^2 in binary32
+// is within 1e-6 of the binary64 value and the acceptance test is decided in
+// binary32 outside a band of +-2e-6 around 1 (and 0) and by the binary64
+// computation inside it -- the accepted candidate is always the one the
+// binary64 draw accepts.  Its direction is v rsqrt(|v|^2) in binary32, with
+// |v|^2 summed by explicit fused multiply-adds (the same rounding wherever
+// the compiler inlines it).
 
-// Direction of the same draw for the FP32 form, without binary64 arithmetic
-// in the common case (binary64 runs at 1/64 of the binary32 rate on this
-// GPU).  Coordinate a of candidate m is taken from the top 24 bits of the
-// Philox word, v_a = ((w_a >> 40) - 2^23) 2^-23, which is the binary64
-// lattice point truncated by less than 2^-23; |v|^2 in binary32 is then
-// within 1e-6 of the binary64 value, so the acceptance test 0 < |v|^2 <= 1 is
-// decided in binary32 outside a band of +-2e-6 around 1 (and 0) and by the
-// binary64 computation of the reference inside it: the accepted candidate is
-// always the one the reference accepts.  The normalisation is binary32.
-template <int DIM>
-__device__ __forceinline__ void unit_dir_f32(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l,
-                                             float u[3])
-{
-    for (int m = 0; m < MAX_CAND; m++) {
-        uint64_t c[4] = {pid, sweep, l, (uint64_t)m};
-        philox4x64(c, seed, TAG_MOVE);
-        float v[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int a = 0; a < DIM; a++) v[a] = (float)((int32_t)(c[a] >> 40) - (1 << 23)) * 0x1p-23f;
-        float s = v[0] * v[0] + v[1] * v[1];
-        if (DIM == 3) s += v[2] * v[2];
-        bool ok;
-        if (s > 1.0f + 2e-6f) {
-            ok = false;
-        } else if (s < 1.0f - 2e-6f && s > 2e-6f) {
-            ok = true;
-        } else {
-            double vd[3];
-#pragma unroll
-            for (int a = 0; a < DIM; a++)
-                vd[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
-            double sd = __dadd_rn(__dmul_rn(vd[0], vd[0]), __dmul_rn(vd[1], vd[1]));
-            if (DIM == 3) sd = __dadd_rn(sd, __dmul_rn(vd[2], vd[2]));
-            ok = sd > 0.0 && sd <= 1.0;
-            if (ok && !(s > 0.f)) s = (float)sd;
-        }
-        if (ok) {
-            const float inv = rsqrtf(s);
-#pragma unroll
-            for (int a = 0; a < DIM; a++) u[a] = v[a] * inv;
-            if (DIM == 2) u[2] = 0.f;
-            return;
-        }
-    }
-    u[0] = 1.f;
-    u[1] = 0.f;
-    u[2] = 0.f;
-}
-
-// One candidate m of trial l: the binary64 lattice point and the acceptance
-// test of unit_dir.
-template <int DIM>
+template <int DIM, bool COMPACT = false>
 __device__ __forceinline__ bool cand_f64(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint64_t m,
                                          double v[3], double &s)
 {
     uint64_t c[4] = {pid, sweep, l, m};
-    philox4x64(c, seed, TAG_MOVE);
+    philox4x64<COMPACT>(c, seed, TAG_MOVE);
     v[2] = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; a++) v[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
@@ -263,19 +220,17 @@ __device__ __forceinline__ bool cand_f64(uint64_t seed, uint64_t sweep, uint64_t
     return s > 0.0 && s <= 1.0;
 }
 
-// The same candidate for the FP32 form (see unit_dir_f32): binary32 lattice
-// point, acceptance decided as in binary64.
-template <int DIM>
+template <int DIM, bool COMPACT = false>
 __device__ __forceinline__ bool cand_f32(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint64_t m,
                                          float v[3], float &s)
 {
     uint64_t c[4] = {pid, sweep, l, m};
-    philox4x64(c, seed, TAG_MOVE);
+    philox4x64<COMPACT>(c, seed, TAG_MOVE);
     v[2] = 0.f;
 #pragma unroll
     for (int a = 0; a < DIM; a++) v[a] = (float)((int32_t)(c[a] >> 40) - (1 << 23)) * 0x1p-23f;
-    s = v[0] * v[0] + v[1] * v[1];
-    if (DIM == 3) s += v[2] * v[2];
+    s = __fmaf_rn(v[1], v[1], __fmul_rn(v[0], v[0]));
+    if (DIM == 3) s = __fmaf_rn(v[2], v[2], s);
     if (s > 1.0f + 2e-6f) return false;
     if (s < 1.0f - 2e-6f && s > 2e-6f) return true;
     double vd[3];
@@ -290,7 +245,7 @@ __device__ __forceinline__ bool cand_f32(uint64_t seed, uint64_t sweep, uint64_t
 
 // Directions of trials l0 .. l0+7 of one particle, drawn by a whole warp:
 // lane k evaluates candidate k % 4 of trial l0 + k / 4, a ballot picks for
-// every trial its first accepted candidate (the one unit_dir would take),
+// every trial its first accepted candidate (the draw's direction),
 // and a trial whose four candidates are all rejected continues with
 // candidates 4, 5, ... in its own lane.  Lane t (t < 8) returns the direction
 // of trial l0 + t.  All lanes of the warp must call it.
@@ -300,8 +255,8 @@ __device__ __noinline__ void draw8(uint64_t seed, uint64_t sweep, uint64_t pid, 
     const int lane = threadIdx.x & 31, t = lane >> 2, cidx = lane & 3;
     DT v[3], s;
     bool ok;
-    if constexpr (F32) ok = cand_f32<DIM>(seed, sweep, pid, (uint64_t)(l0 + t), (uint64_t)cidx, v, s);
-    else ok = cand_f64<DIM>(seed, sweep, pid, (uint64_t)(l0 + t), (uint64_t)cidx, v, s);
+    if constexpr (F32) ok = cand_f32<DIM, true>(seed, sweep, pid, (uint64_t)(l0 + t), (uint64_t)cidx, v, s);
+    else ok = cand_f64<DIM, true>(seed, sweep, pid, (uint64_t)(l0 + t), (uint64_t)cidx, v, s);
     const unsigned bal = __ballot_sync(0xffffffffu, ok);
     // normalise in the lane that holds the chosen candidate
     DT w[3] = {(DT)0, (DT)0, (DT)0};
@@ -331,8 +286,8 @@ __device__ __noinline__ void draw8(uint64_t seed, uint64_t sweep, uint64_t pid, 
         for (int m = 4; m < MAX_CAND; m++) {
             DT vv[3], ss;
             bool okk;
-            if constexpr (F32) okk = cand_f32<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), (uint64_t)m, vv, ss);
-            else okk = cand_f64<DIM>(seed, sweep, pid, (uint64_t)(l0 + lane), (uint64_t)m, vv, ss);
+            if constexpr (F32) okk = cand_f32<DIM, true>(seed, sweep, pid, (uint64_t)(l0 + lane), (uint64_t)m, vv, ss);
+            else okk = cand_f64<DIM, true>(seed, sweep, pid, (uint64_t)(l0 + lane), (uint64_t)m, vv, ss);
             if (okk) {
                 if constexpr (F32) {
                     const float inv = rsqrtf(ss);

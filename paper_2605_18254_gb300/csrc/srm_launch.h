@@ -22,7 +22,8 @@ struct BatchShape {
     int tiles_n;        // scan tiles over particles
     int64_t sub_total;  // sweep work items per colour (sum of colour-cell capacities)
     bool f32;           // arithmetic of the working copies
-    bool has3d;         // some RVE is 3D (27 colours), else 9
+    bool has3d;         // some RVE is (or a slot may hold) a 3D RVE
+    bool has2d;         // some RVE is (or a slot may hold) a 2D RVE
     int cap;            // candidates a sweep warp stages in shared memory
 };
 
@@ -33,7 +34,7 @@ void launch_scan(const BatchShape &b, int which, cudaStream_t s);
 int64_t scan_part_len(int64_t max_len);
 int scan_tile();
 void launch_sweep(const BatchShape &b, cudaStream_t s);
-void launch_sweep_colour(const BatchShape &b, int chi, cudaStream_t s);
+int sweep_launches(const BatchShape &b);
 void sweep_configure();
 int sweep_cap_max(bool f32);
 int check_cap_max(bool f32);

@@ -192,6 +192,15 @@ def test_fp32_sweep_within_tolerance(seed, dim):
     assert frac > 0.99
 
 
+@pytest.mark.parametrize("lam,sweeps", [(1.0, 1), (1.08, 2)])
+def test_fp32_sweep_polydisperse_clustered(lam, sweeps):
+    # log-normal radii and a clustered start: dense cluster cores give cells
+    # with many particles and staged candidate lists of several 32-wide chunks
+    w = srm_inputs.poly_1m(n=20000)
+    frac = fp32_sweep_check(w, lam, w.c_m, sweeps=sweeps)
+    assert frac > 0.99
+
+
 @pytest.mark.parametrize("maker", [lambda: srm_inputs.disks_1k(), lambda: small_3d(3000, 0.45)])
 def test_fp32_full_run_certifies(maker):
     w = maker()
