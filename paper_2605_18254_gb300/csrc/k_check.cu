@@ -90,20 +90,23 @@ __device__ __forceinline__ void check_one(RveDev *st, int i, int &hit, unsigned 
 template <bool F32>
 __global__ void __launch_bounds__(256) k_check(BatchDev *bd)
 {
-    const int r = block_rve(bd->blk_p, bd->B);
+    int r;
+    if (!plan_block(bd->actp, bd->B, r)) return;
     RveDev *st = bd->rv[r];
-    if (!st->active || !st->do_check) return;
-    const int i = (blockIdx.x - bd->blk_p[r]) * blockDim.x + threadIdx.x;
-    int hit = 0;
-    unsigned examined = 0;
-    if (i < st->n && !st->flags[i]) {
-        if (st->dim == 3) check_one<3, F32>(st, i, hit, examined);
-        else check_one<2, F32>(st, i, hit, examined);
+    if (!st->do_check) return;
+    {
+        const int i = (blockIdx.x - bd->actp[r]) * 256 + threadIdx.x;
+        int hit = 0;
+        unsigned examined = 0;
+        if (i < st->n && !st->flags[i]) {
+            if (st->dim == 3) check_one<3, F32>(st, i, hit, examined);
+            else check_one<2, F32>(st, i, hit, examined);
+        }
+        const int tot = __reduce_add_sync(0xffffffffu, hit);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&st->red[0], (unsigned long long)tot);
+        examined = __reduce_add_sync(0xffffffffu, examined);
+        if ((threadIdx.x & 31) == 0 && examined) atomicAdd(&st->pairs_check, (unsigned long long)examined);
     }
-    const int tot = __reduce_add_sync(0xffffffffu, hit);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&st->red[0], (unsigned long long)tot);
-    examined = __reduce_add_sync(0xffffffffu, examined);
-    if ((threadIdx.x & 31) == 0 && examined) atomicAdd(&st->pairs_check, (unsigned long long)examined);
 }
 
 // ---------------------------------------------------------------------------
@@ -274,6 +277,7 @@ void check_configure() {}
 void launch_inspect_bin(RveDev *d_st, const BatchShape &solo, cudaStream_t s)
 {
     k_inspect_begin<<<1, 1, 0, s>>>(d_st);
+    launch_plan(solo, s);
     launch_bin(solo, solo.f32, false, s);
 }
 

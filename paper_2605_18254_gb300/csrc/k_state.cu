@@ -103,74 +103,68 @@ __global__ void k_control(BatchDev *bd)
     }
 }
 
-// Work plan of the sweep for this super-step: offsets of the colour cells of
-// the 2D and of the 3D RVEs at work, so that finished RVEs of a batch cost
-// nothing in the sweep.  One block.
+// Work plans of this super-step, over the RVEs at work only (finished or
+// empty members of a batch cost nothing): the colour cells of the 2D and of
+// the 3D RVEs (sweep work items), and the 256-wide particle and cell chunks
+// (particle- and cell-indexed kernels).  One block: block-wide exclusive
+// scans of the four per-RVE counts.
 __global__ void __launch_bounds__(1024) k_plan(BatchDev *bd)
 {
+    constexpr int Q = 4;
     const int B = bd->B;
-    __shared__ int32_t carry[2];
-    if (threadIdx.x == 0) {
-        carry[0] = 0;
-        carry[1] = 0;
-    }
+    __shared__ int32_t carry[Q];
+    __shared__ int32_t ws[Q][32];
+    int32_t *const out[Q] = {bd->act2, bd->act3, bd->actp, bd->actc};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x < Q) carry[threadIdx.x] = 0;
     __syncthreads();
     for (int base = 0; base < B; base += blockDim.x) {
         const int r = base + threadIdx.x;
-        int32_t w = 0, w3 = 0;
+        int32_t v[Q] = {0, 0, 0, 0};
         if (r < B) {
             const RveDev *st = bd->rv[r];
             if (st->active) {
-                w = st->dim == 2 ? st->nsub : 0;
-                w3 = st->dim == 3 ? st->nsub : 0;
+                v[0] = st->dim == 2 ? st->nsub : 0;
+                v[1] = st->dim == 3 ? st->nsub : 0;
+                v[2] = (st->n + 255) / 256;
+                v[3] = (st->ncells + 255) / 256;
             }
         }
-        // block-wide inclusive scans of w and w3
-        __shared__ int32_t ws[32], ws3[32];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        int32_t x = w, x3 = w3;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, x, o), y3 = __shfl_up_sync(0xffffffffu, x3, o);
-            if (lane >= o) {
-                x += y;
-                x3 += y3;
+        int32_t x[Q];
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            x[q] = v[q];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, x[q], o);
+                if (lane >= o) x[q] += y;
             }
-        }
-        if (lane == 31) {
-            ws[wid] = x;
-            ws3[wid] = x3;
+            if (lane == 31) ws[q][wid] = x[q];
         }
         __syncthreads();
         if (wid == 0) {
-            const int nw = blockDim.x >> 5;
-            int32_t t = lane < nw ? ws[lane] : 0, t3 = lane < nw ? ws3[lane] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(0xffffffffu, t, o), y3 = __shfl_up_sync(0xffffffffu, t3, o);
-                if (lane >= o) {
-                    t += y;
-                    t3 += y3;
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                int32_t t = lane < nw ? ws[q][lane] : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
                 }
+                ws[q][lane] = t;
             }
-            ws[lane] = t;
-            ws3[lane] = t3;
         }
         __syncthreads();
-        const int32_t before = wid ? ws[wid - 1] : 0, before3 = wid ? ws3[wid - 1] : 0;
-        if (r < B) {
-            bd->act2[r] = carry[0] + before + x - w;
-            bd->act3[r] = carry[1] + before3 + x3 - w3;
+        int32_t before[Q];
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            before[q] = wid ? ws[q][wid - 1] : 0;
+            if (r < B) out[q][r] = carry[q] + before[q] + x[q] - v[q];
         }
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) {
-            carry[0] += before + x;
-            carry[1] += before3 + x3;
-        }
+        if (threadIdx.x == blockDim.x - 1)
+            for (int q = 0; q < Q; q++) carry[q] += before[q] + x[q];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        bd->act2[B] = carry[0];
-        bd->act3[B] = carry[1];
-    }
+    if (threadIdx.x < Q) out[threadIdx.x][B] = carry[threadIdx.x];
 }
 
 // ---------------------------------------------------------------------------
@@ -266,12 +260,12 @@ __device__ __forceinline__ void bin_count_one(RveDev *st, int i)
 }
 
 template <bool F32, bool FAST>
-__global__ void k_bin_count(BatchDev *bd)
+__global__ void __launch_bounds__(256) k_bin_count(BatchDev *bd)
 {
-    const int r = block_rve(bd->blk_p, bd->B);
+    int r;
+    if (!plan_block(bd->actp, bd->B, r)) return;
     RveDev *st = bd->rv[r];
-    if (!st->active) return;
-    const int i = (blockIdx.x - bd->blk_p[r]) * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x - bd->actp[r]) * 256 + threadIdx.x;
     if (i >= st->n) return;
     if (st->dim == 3) bin_count_one<3, F32, FAST>(st, i);
     else bin_count_one<2, F32, FAST>(st, i);
@@ -315,12 +309,12 @@ __device__ __forceinline__ void bin_scatter_one(RveDev *st, int i)
 }
 
 template <bool IN32, bool OUT32>
-__global__ void k_bin_scatter(BatchDev *bd)
+__global__ void __launch_bounds__(256) k_bin_scatter(BatchDev *bd)
 {
-    const int r = block_rve(bd->blk_p, bd->B);
+    int r;
+    if (!plan_block(bd->actp, bd->B, r)) return;
     RveDev *st = bd->rv[r];
-    if (!st->active) return;
-    const int i = (blockIdx.x - bd->blk_p[r]) * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x - bd->actp[r]) * 256 + threadIdx.x;
     if (i >= st->n) return;
     if (st->dim == 3) bin_scatter_one<3, IN32, OUT32>(st, i);
     else bin_scatter_one<2, IN32, OUT32>(st, i);
@@ -341,13 +335,8 @@ __global__ void k_bin_stamp(BatchDev *bd)
 }
 
 template <bool F32>
-__global__ void k_cell_sort(BatchDev *bd)
+__device__ __forceinline__ void cell_sort_one(RveDev *st, int c)
 {
-    const int r = block_rve(bd->blk_c, bd->B);
-    RveDev *st = bd->rv[r];
-    if (!st->active) return;
-    const int c = (blockIdx.x - bd->blk_c[r]) * blockDim.x + threadIdx.x;
-    if (c >= st->ncells) return;
     const uint32_t b = st->cell_start[c], e = st->cell_start[c + 1];
     if (e - b < 2) return;
     const Slot d = st->slot[st->dst_idx];
@@ -379,6 +368,16 @@ __global__ void k_cell_sort(BatchDev *bd)
         d.rb[j] = rb;
         d.pid[j] = key;
     }
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_cell_sort(BatchDev *bd)
+{
+    int r;
+    if (!plan_block(bd->actc, bd->B, r)) return;
+    RveDev *st = bd->rv[r];
+    const int c = (blockIdx.x - bd->actc[r]) * 256 + threadIdx.x;
+    if (c < st->ncells) cell_sort_one<F32>(st, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -524,7 +523,7 @@ static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); 
 void launch_begin(const BatchShape &b, cudaStream_t s)
 {
     k_begin<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d);
-    k_plan<<<1, 1024, 0, s>>>(b.d);
+    launch_plan(b, s);
 }
 void launch_control(const BatchShape &b, cudaStream_t s) { k_control<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d); }
 
@@ -539,20 +538,38 @@ void launch_scan(const BatchShape &b, int which, cudaStream_t s)
 int64_t scan_part_len(int64_t max_len) { return blocks_for(max_len, SCAN_TILE); }
 int scan_tile() { return SCAN_TILE; }
 
+// Blocks of a launch whose blocks walk a plan (k_draw): at most eight
+// 256-thread blocks per SM (full residency), at most the chunks of the
+// group's capacity.
+int plan_blocks(int64_t capacity_chunks)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int64_t cap = (int64_t)sms * 8;
+    return (int)(capacity_chunks < cap ? (capacity_chunks > 0 ? capacity_chunks : 1) : cap);
+}
+
+void launch_plan(const BatchShape &b, cudaStream_t s) { k_plan<<<1, 1024, 0, s>>>(b.d); }
+
 void launch_bin(const BatchShape &b, bool in32, bool out32, cudaStream_t s)
 {
-    const int T = 256;
+    const int T = 256, np = b.blocks_p, nc = b.blocks_c;
     // the binary32 shift path only where the scatter also writes binary32
-    if (in32 && out32) k_bin_count<true, true><<<b.blocks_p, T, 0, s>>>(b.d);
-    else if (in32) k_bin_count<true, false><<<b.blocks_p, T, 0, s>>>(b.d);
-    else k_bin_count<false, false><<<b.blocks_p, T, 0, s>>>(b.d);
+    if (in32 && out32) k_bin_count<true, true><<<np, T, 0, s>>>(b.d);
+    else if (in32) k_bin_count<true, false><<<np, T, 0, s>>>(b.d);
+    else k_bin_count<false, false><<<np, T, 0, s>>>(b.d);
     launch_scan(b, 0, s);
-    if (in32 && out32) k_bin_scatter<true, true><<<b.blocks_p, T, 0, s>>>(b.d);
-    else if (in32) k_bin_scatter<true, false><<<b.blocks_p, T, 0, s>>>(b.d);
-    else k_bin_scatter<false, false><<<b.blocks_p, T, 0, s>>>(b.d);
+    if (in32 && out32) k_bin_scatter<true, true><<<np, T, 0, s>>>(b.d);
+    else if (in32) k_bin_scatter<true, false><<<np, T, 0, s>>>(b.d);
+    else k_bin_scatter<false, false><<<np, T, 0, s>>>(b.d);
     k_bin_stamp<<<blocks_for(b.B, 128), 128, 0, s>>>(b.d);
-    if (out32) k_cell_sort<true><<<b.blocks_c, T, 0, s>>>(b.d);
-    else k_cell_sort<false><<<b.blocks_c, T, 0, s>>>(b.d);
+    if (out32) k_cell_sort<true><<<nc, T, 0, s>>>(b.d);
+    else k_cell_sort<false><<<nc, T, 0, s>>>(b.d);
 }
 
 // ---------------------------------------------------------------------------

@@ -209,21 +209,23 @@ __device__ __forceinline__ void draw_warp(const RveDev *st, const Slot &d, int64
     }
 }
 
-// One thread block per 256 particles of one RVE (the particle-indexed block
-// ranges of the group), eight warps of 32 particles.
+// Warps walk the 32-particle pieces of the RVEs at work (plan actp).
 template <bool F32>
 __global__ void __launch_bounds__(256) k_draw(BatchDev *bd)
 {
-    const int r = block_rve(bd->blk_p, bd->B);
-    const RveDev *st = bd->rv[r];
-    if (!st->active) return;
-    const int64_t g0 = (int64_t)(blockIdx.x - bd->blk_p[r]) * 256 + (threadIdx.x & ~31);
-    const int n = st->n;
-    if (g0 >= n) return;
-    const int np_w = n - g0 < 32 ? (int)(n - g0) : 32;
-    const Slot d = st->slot[st->dst_idx];
-    if (st->dim == 3) draw_warp<3, F32>(st, d, g0, np_w);
-    else draw_warp<2, F32>(st, d, g0, np_w);
+    const int B = bd->B, stride = gridDim.x * (blockDim.x >> 5);
+    int r, chunk, sub;
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); warp_piece(bd->actp, B, it, r, chunk, sub);
+         it += stride) {
+        const RveDev *st = bd->rv[r];
+        const int64_t g0 = (int64_t)(chunk - bd->actp[r]) * 256 + sub * 32;
+        const int n = st->n;
+        if (g0 >= n) continue;
+        const int np_w = n - g0 < 32 ? (int)(n - g0) : 32;
+        const Slot d = st->slot[st->dst_idx];
+        if (st->dim == 3) draw_warp<3, F32>(st, d, g0, np_w);
+        else draw_warp<2, F32>(st, d, g0, np_w);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -625,11 +627,14 @@ static void launch_sweep_dim(const BatchShape &b, cudaStream_t s)
     k_sweep_df<DIM, F32><<<want < res ? want : res, SW_WARPS * 32, smem, s>>>(b.d, b.cap);
 }
 
-// Trial directions (k_draw), then the sweep of the 3D and of the 2D RVEs.
+// Trial directions (k_draw), then the sweep of the 3D and of the 2D RVEs
+// (one launch per dimension present; measured faster than one launch over
+// both, whose register budget is that of the larger 3D path).
 void launch_sweep(const BatchShape &b, cudaStream_t s)
 {
-    if (b.f32) k_draw<true><<<b.blocks_p, 256, 0, s>>>(b.d);
-    else k_draw<false><<<b.blocks_p, 256, 0, s>>>(b.d);
+    const int nb = plan_blocks(b.blocks_p);
+    if (b.f32) k_draw<true><<<nb, 256, 0, s>>>(b.d);
+    else k_draw<false><<<nb, 256, 0, s>>>(b.d);
     if (b.has3d) {
         if (b.f32) launch_sweep_dim<3, true>(b, s);
         else launch_sweep_dim<3, false>(b, s);

@@ -273,6 +273,7 @@ void group_free(Group &g)
     cudaStreamSynchronize(g.stream);
     if (g.cap_stream) cudaStreamDestroy(g.cap_stream);
     g.cap_stream = nullptr;
+
     if (g.pin) cudaFreeHost(g.pin);
     if (g.pin_red) cudaFreeHost(g.pin_red);
     g.pin = nullptr;
@@ -418,7 +419,7 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
         has2d = has2d || mb.dim == 2 || mb.any_dim;
     }
     BatchDev *d = (BatchDev *)dev_alloc(g, sizeof(BatchDev));
-    int32_t *d_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * (off.size() + 2 * (size_t)(B + 1)));
+    int32_t *d_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * (off.size() + 4 * (size_t)(B + 1)));
     RveDev **d_rv = (RveDev **)dev_alloc(g, sizeof(RveDev *) * (size_t)B);
     if (!d || !d_off || !d_rv) return fail(SRM_E_NOMEM, "device allocation failed");
     std::vector<RveDev *> rv((size_t)B);
@@ -433,7 +434,9 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     hb.sub = d_off + 4 * (B + 1);
     hb.act2 = d_off + 5 * (B + 1);
     hb.act3 = d_off + 6 * (B + 1);
-    CK(cudaMemsetAsync(hb.act2, 0, sizeof(int32_t) * 2 * (size_t)(B + 1), g.stream));
+    hb.actp = d_off + 7 * (B + 1);
+    hb.actc = d_off + 8 * (B + 1);
+    CK(cudaMemsetAsync(hb.act2, 0, sizeof(int32_t) * 4 * (size_t)(B + 1), g.stream));
     CK(cudaMemcpyAsync(d_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(d_rv, rv.data(), sizeof(RveDev *) * (size_t)B, cudaMemcpyHostToDevice, g.stream));
     CK(cudaMemcpyAsync(d, &hb, sizeof(BatchDev), cudaMemcpyHostToDevice, g.stream));
@@ -454,8 +457,8 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
 }
 
 // kernels of one super-step: begin and plan, binning (count, 3 scan passes,
-// scatter, stamp, in-cell sort), the trial draws and the sweep (one launch
-// per dimension present), check, control
+// scatter, stamp, in-cell sort), the trial draws and the sweep, check,
+// control
 static int64_t kernels_per_superstep(const BatchShape &sh) { return 2 + 7 + srm::sweep_launches(sh) + 1 + 1; }
 
 static void enqueue_superstep(Group &g, cudaStream_t s, const std::vector<cudaEvent_t> *ev = nullptr)

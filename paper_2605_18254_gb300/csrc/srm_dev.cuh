@@ -106,6 +106,8 @@ struct BatchDev {
     int32_t *sub;     // [B+1] first sweep work item of each RVE (cells of one colour)
     int32_t *act2;    // [B+1] first work item of each 2D RVE at work in this super-step
     int32_t *act3;    // [B+1] the same over the 3D RVEs at work
+    int32_t *actp;    // [B+1] first 256-particle chunk of each RVE at work
+    int32_t *actc;    // [B+1] first 256-cell chunk of each RVE at work (current grid)
     uint32_t wq[2];   // sweep work counters: [0] 3D RVEs, [1] 2D RVEs
 };
 
@@ -142,6 +144,33 @@ __device__ __forceinline__ int block_rve(const int32_t *off, int B)
     if (threadIdx.x == 0) r_sh = find_seg(off, B, (int)blockIdx.x);
     __syncthreads();
     return r_sh;
+}
+
+// Warp-level walk of a plan of 256-wide chunks: warp w of the grid takes the
+// 32-wide pieces w, w + (warps in the grid), ...; returns false when done.
+// No block-wide synchronisation, so warps with uneven work do not wait for
+// each other.
+__device__ __forceinline__ bool warp_piece(const int32_t *off, int B, int it, int &r, int &chunk, int &sub)
+{
+    const int pieces = off[B] * 8;
+    if (it >= pieces) return false;
+    chunk = it >> 3;
+    sub = it & 7;
+    int rr = 0;
+    if ((threadIdx.x & 31) == 0) rr = find_seg(off, B, chunk);
+    r = __shfl_sync(0xffffffffu, rr, 0);
+    return true;
+}
+
+// One block per chunk of a plan (offsets off[0..B], the RVEs at work in
+// this super-step), in a grid sized for the group's capacity: block b serves
+// chunk b; blocks past the plan return at once.  All threads of the block
+// must call it; the result is the same for the whole block.
+__device__ __forceinline__ bool plan_block(const int32_t *off, int B, int &r)
+{
+    if ((int)blockIdx.x >= off[B]) return false;
+    r = block_rve(off, B);
+    return true;
 }
 
 // ---------------------------------------------------------------------------

@@ -28,6 +28,8 @@ struct BatchShape {
 };
 
 void launch_begin(const BatchShape &b, cudaStream_t s);
+void launch_plan(const BatchShape &b, cudaStream_t s);
+int plan_blocks(int64_t capacity_chunks);
 void launch_control(const BatchShape &b, cudaStream_t s);
 void launch_bin(const BatchShape &b, bool in32, bool out32, cudaStream_t s);
 void launch_scan(const BatchShape &b, int which, cudaStream_t s);
