@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "srm_oracle.c")
+_SRC_A = os.path.join(_HERE, "srm_analysis.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libsrm_oracle.so")
 _lock = threading.Lock()
@@ -30,10 +31,11 @@ _d, _i64, _u64, _int = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.
 def build(force: bool = False) -> str:
     """Compile the reference with plain gcc, no FMA contraction, no fast-math."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    srcs = [_SRC, _SRC_A]
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in srcs):
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-shared", "-o", tmp] + srcs + ["-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -67,6 +69,9 @@ def _load():
                 "orc_run": ([ctypes.c_void_p, _i64], _i64),
                 "orc_pairs_brute": ([_int, P(_d), _i64, P(_d), P(_d), P(_i64), _i64, P(_d)], _i64),
                 "orc_certify": ([_int, P(_d), _i64, P(_d), P(_d), P(_d)], _i64),
+                "orc_nn": ([_int, P(_d), _i64, P(_d), P(_d), P(_d), P(_i64), P(_d)], None),
+                "orc_rdf": ([_int, P(_d), _i64, P(_d), _d, _int, P(_i64), P(_d)], _i64),
+                "orc_voronoi_lvf": ([_int, P(_d), _i64, P(_d), P(_d), P(ctypes.c_int32), P(_i64), P(_d)], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -129,6 +134,43 @@ def certify(dim, box, X, R):
     mg = np.zeros(1)
     cnt = _load().orc_certify(dim, _dp(_box3(box, dim)), R.size, _dp(X), _dp(R), _dp(mg))
     return int(cnt), float(mg[0])
+
+
+def nn(dim, box, X, R):
+    """Nearest neighbours by brute force: (centre distance, partner id,
+    smallest surface gap) per particle (Section 3.2, Fig. 4d)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    n = R.size
+    d, g = np.zeros(n), np.zeros(n)
+    j = np.zeros(n, dtype=np.int64)
+    _load().orc_nn(dim, _dp(_box3(box, dim)), n, _dp(X), _dp(R), _dp(d), j.ctypes.data_as(P(_i64)), _dp(g))
+    return d, j, g
+
+
+def rdf(dim, box, X, r_max, bins):
+    """Radial distribution of the centres: (ordered-pair counts per bin, g)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = X.shape[0]
+    c = np.zeros(bins, dtype=np.int64)
+    g = np.zeros(bins)
+    _load().orc_rdf(dim, _dp(_box3(box, dim)), n, _dp(X), r_max, bins, c.ctypes.data_as(P(_i64)), _dp(g))
+    return c, g
+
+
+def voronoi_lvf(dim, box, X, R, voxels):
+    """Local volume fraction from a discrete periodic Voronoi tessellation on
+    the given voxel grid: (voxel counts, LVF) per particle (Section 3.2)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    n = R.size
+    M = np.ones(3, dtype=np.int32)
+    M[:dim] = np.asarray(voxels, dtype=np.int32)[:dim]
+    c = np.zeros(n, dtype=np.int64)
+    lvf = np.zeros(n)
+    _load().orc_voronoi_lvf(dim, _dp(_box3(box, dim)), n, _dp(X), _dp(R), M.ctypes.data_as(P(ctypes.c_int32)),
+                            c.ctypes.data_as(P(_i64)), _dp(lvf))
+    return c, lvf
 
 
 class System:
