@@ -6,6 +6,8 @@
 #include "srm_dev.cuh"
 #include "srm_launch.h"
 
+#include <type_traits>
+
 namespace srm {
 
 __global__ void k_begin(BatchDev *bd)
@@ -370,14 +372,51 @@ __device__ __forceinline__ void cell_sort_one(RveDev *st, int c)
     }
 }
 
+// In-cell sort by particle id.  Each warp of a block takes 32 consecutive
+// cells: a cell of 2..32 particles is sorted by the whole warp (lane i loads
+// element i, its rank is the number of smaller ids, every element is written
+// once to its rank); a larger cell is insertion-sorted by its own lane.
 template <bool F32>
 __global__ void __launch_bounds__(256) k_cell_sort(BatchDev *bd)
 {
+    using PT = typename std::conditional<F32, float4, double4_32a>::type;
     int r;
     if (!plan_block(bd->actc, bd->B, r)) return;
     RveDev *st = bd->rv[r];
-    const int c = (blockIdx.x - bd->actc[r]) * 256 + threadIdx.x;
-    if (c < st->ncells) cell_sort_one<F32>(st, c);
+    const int lane = threadIdx.x & 31;
+    const int cl = (blockIdx.x - bd->actc[r]) * 256 + threadIdx.x;
+    uint32_t cb = 0, ce = 0;
+    if (cl < st->ncells) {
+        cb = st->cell_start[cl];
+        ce = st->cell_start[cl + 1];
+    }
+    if (ce - cb > 32) cell_sort_one<F32>(st, cl);
+    const Slot d = st->slot[st->dst_idx];
+    PT *pos = reinterpret_cast<PT *>(d.pos);
+    unsigned todo = __ballot_sync(0xffffffffu, ce - cb >= 2 && ce - cb <= 32);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t b = __shfl_sync(0xffffffffu, cb, src);
+        const uint32_t n = __shfl_sync(0xffffffffu, ce, src) - b;
+        uint32_t key = 0xffffffffu;
+        PT v;
+        double rb = 0.0;
+        if (lane < (int)n) {
+            key = d.pid[b + lane];
+            v = pos[b + lane];
+            rb = d.rb[b + lane];
+        }
+        uint32_t rank = 0;
+        for (uint32_t j = 0; j < n; j++) rank += __shfl_sync(0xffffffffu, key, (int)j) < key ? 1u : 0u;
+        __syncwarp();
+        if (lane < (int)n) {
+            pos[b + rank] = v;
+            d.rb[b + rank] = rb;
+            d.pid[b + rank] = key;
+        }
+        __syncwarp();
+    }
 }
 
 // ---------------------------------------------------------------------------
