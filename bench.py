@@ -322,7 +322,11 @@ def run_ours(args, rank, world, local_rank):
                 "hbm_side": hbm_side(w, args.precision, per_launch[dom], pk) if dom == "sweep" else None,
                 "peak_basis": (f"FP32 lanes: {N_SM} SMs x {FP32_LANES_PER_SM} x 2 flops x "
                                f"{pk.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz" + (" / 64 (FP64 rate)" if args.precision == 64 else "")),
-                "stage_ms_total": totals, "supersteps": tm["supersteps"]}
+                "stage_ms_total": totals, "supersteps": tm["supersteps"],
+                "rates": {"trials_per_s": (st1["trials"] - st0["trials"]) / max(1e-9, tm["ms_sweep"] * 1e-3),
+                          "check_particles_per_s": w.n * tm["check_launches"] / max(1e-9, tm["ms_check"] * 1e-3),
+                          "note": "trial moves of Algorithm 3 per second of sweep stage; particles checked by "
+                                  "Algorithm 6 per second of check stage (every particle of a checked sweep)"}}
     else:
         bytes_per = w.n * (64 if args.precision == 32 else 96)
         achieved = bytes_per / (per_launch["bin"] * 1e-3) / 1e9
@@ -353,9 +357,11 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         ups, dt = cpu_sample(w, 1)
+        import platform
         cpu = {"value": ups, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"1 sweep of Algorithm 3 over all {w.n} particles at the first swollen scale "
-                         f"({dt:.1f} s, single-threaded FP64 reference)"}
+                         f"({dt:.1f} s, single-threaded FP64 reference; host {platform.machine()}, "
+                         f"{os.cpu_count()} cores)"}
 
     h2d = int(x_host.numel() * 8 + r_host.numel() * 8)
     d2h = int(w.n * w.dim * 8 + w.n * 8)
@@ -535,6 +541,78 @@ def run_serve(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def regime_run(srm, dim, n, phi_t, seed, c_w, c_m_rel, precision, wall_cap, voxels):
+    """One generation from an RSA start at 0.1 (monodisperse, unit box) with
+    the given swelling rate and migration length (relative to the target
+    radius); stops at the target or after wall_cap seconds.  Returns the
+    reached fraction, time, counters and the descriptors of Section 3.2."""
+    import numpy as np
+    import torch
+    r_t = math.sqrt(phi_t / (n * math.pi)) if dim == 2 else (phi_t * 3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
+    g = srm.Rve(dim, (1.0,) * dim, ("mono", r_t * (0.1 / phi_t) ** (1.0 / dim)), phi_t, seed, n=n,
+                c_m=c_m_rel * r_t, c_w=c_w, precision=precision, init="rsa", f0=0.1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = {}
+    while time.perf_counter() - t0 < wall_cap:
+        info = g.run_to_target(200)
+        if info["converged"]:
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = g.state()
+    pairs, gap_min, phi = g.certify()
+    d, _, gap = g.nearest()
+    cnt, lvf = g.voronoi_lvf((voxels,) * dim)
+    g.close()
+    R = r_t * (phi / phi_t) ** (1.0 / dim)
+    return {"dim": dim, "n": n, "target_phi": phi_t, "c_w": c_w, "c_m_over_r": c_m_rel,
+            "reached_phi": phi, "converged": bool(info.get("converged", False)), "seconds": wall,
+            "iterations": st["iterations"], "accepted": st["accepted"], "shaken": st["shaken"],
+            "sweeps": st["sweeps"], "certified_pairs": pairs,
+            "nn_dist_over_d": {"mean": float(np.mean(d) / (2 * R)), "std": float(np.std(d) / (2 * R))},
+            "nn_gap_over_d": {"mean": float(np.mean(gap) / (2 * R)), "std": float(np.std(gap) / (2 * R)),
+                              "p05": float(np.percentile(gap, 5) / (2 * R))},
+            "lvf": {"mean": float(np.mean(lvf)), "std": float(np.std(lvf)),
+                    "p05": float(np.percentile(lvf, 5)), "p95": float(np.percentile(lvf, 95))},
+            "voxels_per_axis": voxels}
+
+
+def run_regimes(args, rank, world, local_rank):
+    """Equilibrium-like and clustered configurations (Section 3.2: 2D disks
+    and 3D spheres at 0.5) and the dense limits (Section 2: random close
+    packing for disks, about 0.60 for spheres), with the nearest-neighbour
+    and local-volume-fraction statistics that tell them apart."""
+    import torch
+    import paper_2605_18254_gb300 as srm
+    torch.cuda.set_device(local_rank)
+    cap = args.regime_seconds
+    runs = {
+        "2d_equilibrium_0.5": (2, 5000, 0.5, 11, 0.002, 0.5),
+        "2d_clustered_0.5": (2, 5000, 0.5, 11, 0.05, 0.02),
+        "3d_equilibrium_0.5": (3, 5000, 0.5, 12, 0.002, 0.5),
+        "3d_clustered_0.5": (3, 5000, 0.5, 12, 0.05, 0.02),
+        "2d_dense_0.87": (2, 5000, 0.87, 13, 0.002, 0.3),
+        "3d_dense_0.60": (3, 10000, 0.60, 14, 0.002, 0.3),
+    }
+    out = {}
+    t0 = time.perf_counter()
+    for name, (dim, n, phi, seed, c_w, cm) in runs.items():
+        out[name] = regime_run(srm, dim, n, phi, seed, c_w, cm, args.precision, cap, 400 if dim == 2 else 64)
+    wall = time.perf_counter() - t0
+    line = {"metric": "reached volume fraction and structure descriptors per regime", "value": wall,
+            "unit": "s", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * wall,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+            "config": {"workload": "regimes: monodisperse RSA starts at 0.1 in a unit box; equilibrium-like "
+                                   "(slow swelling, long migration) vs clustered (fast swelling, short migration) at "
+                                   "0.5 (2D 5000 disks, 3D 5000 spheres), dense runs toward 0.87 (2D) and 0.60 (3D) "
+                                   f"capped at {cap:.0f} s each; descriptors in binary64 on the GPU"},
+            "regimes": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,6 +628,7 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-big", type=int, default=10_000_000)
+    ap.add_argument("--regime-seconds", type=float, default=60.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -567,6 +646,8 @@ def main():
             run_ensemble(args, rank, world, local_rank)
         elif args.workload == "serve":
             run_serve(args, rank, world, local_rank)
+        elif args.workload == "regimes":
+            run_regimes(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -167,6 +167,40 @@ srm_status srm_positions(srm_rve *h, double *xyz, double *radii);
  * writes min(cap, *n) pairs and sets *n to the total. */
 srm_status srm_overlap_pairs(srm_rve *h, int64_t *ij, int64_t cap, int64_t *n);
 
+/* ---- structure descriptors of P (Section 3.2) ---------------------------
+ * The statistics the paper uses to tell clustered from equilibrium-like
+ * configurations: nearest-neighbour distances (Fig. 4d), the local volume
+ * fraction of every particle -- its area (volume) over the area (volume) of
+ * its Voronoi cell (Figs. 5 and 7) -- and the radial distribution of the
+ * centres.  They read P at its current scale in binary64 (periodic minimum
+ * image; distance = correctly rounded root of the squared differences summed
+ * in axis order).  Outputs are caller-owned host arrays in particle-id order;
+ * each call synchronises the handle's stream.  SRM_E_STATE inside an
+ * iteration (as srm_certify). */
+
+/* Nearest neighbour of every particle: nn_dist[i] = min over j != i of the
+ * centre distance S_ij, nn_id[i] = that j (ties to the smaller id; may be
+ * NULL), gap[i] = min over j != i of S_ij - (R_i + R_j) (the smallest
+ * surface gap; negative for overlaps).  Arrays of n. */
+srm_status srm_nearest(srm_rve *h, double *nn_dist, int64_t *nn_id, double *gap);
+
+/* Radial distribution of the centres: counts[k] = ordered pairs (i, j),
+ * i != j, with S_ij in [k dr, (k+1) dr), dr = r_max / bins (bin floor(S /
+ * dr)); gr[k] (may be NULL) = counts[k] V / (N (N - 1) V_k), V_k the volume
+ * (area) of shell k.  0 < r_max <= half the smallest box length (else
+ * SRM_E_ARG), 1 <= bins <= 4096. */
+srm_status srm_rdf(srm_rve *h, double r_max, int32_t bins, int64_t *counts, double *gr);
+
+/* Local volume fraction from a discrete periodic Voronoi tessellation on
+ * voxels[0] x voxels[1] (x voxels[2]) voxels (voxels[2] ignored in 2D; each
+ * in [1, 65536], at most 2^34 in total): the voxel centre ((i_a + 0.5) h_a,
+ * h_a = L_a / voxels[a]) belongs to the nearest particle centre (ties to the
+ * smaller id); count[j] = voxels of particle j, lvf[j] (may be NULL) = v_j /
+ * (count[j] prod h_a) with v_j = pi R_j^2 (2D) or 4/3 pi R_j^3 (3D), +inf for
+ * an empty cell.  The discrete cell volumes converge to the Voronoi volumes
+ * as the voxels shrink; their sum is the box volume exactly. */
+srm_status srm_voronoi_lvf(srm_rve *h, const int32_t voxels[3], int64_t *count, double *lvf);
+
 /* Runs count sweeps of Algorithm 3 on P at its current scale (each preceded
  * by a fresh binning, grid of the current scale): the relaxation move with
  * no swelling (Section 3.3, zero swelling rate).  Advances the sweep counter.

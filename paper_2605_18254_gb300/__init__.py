@@ -23,6 +23,7 @@ from . import build as _build
 
 __all__ = ["SrmError", "Rve", "load", "srm_init", "srm_step", "srm_run_to_target", "srm_certify",
            "srm_positions", "srm_overlap_pairs", "srm_sweep", "srm_set_scale", "srm_get_state",
+           "srm_nearest", "srm_rdf", "srm_voronoi_lvf",
            "srm_destroy", "srm_last_error", "srm_set_timing", "srm_get_timings",
            "srm_certify_noalloc", "srm_save", "srm_load", "srm_job_footprint", "make_job", "Batch",
            "PREC_F64", "PREC_F32"]
@@ -120,6 +121,9 @@ def load() -> ctypes.CDLL:
                                 c_int32),
                 "srm_positions": ([H, c_void_p, c_void_p], c_int32),
                 "srm_overlap_pairs": ([H, c_void_p, c_int64, POINTER(c_int64)], c_int32),
+                "srm_nearest": ([H, c_void_p, c_void_p, c_void_p], c_int32),
+                "srm_rdf": ([H, c_double, c_int32, c_void_p, c_void_p], c_int32),
+                "srm_voronoi_lvf": ([H, c_void_p, c_void_p, c_void_p], c_int32),
                 "srm_sweep": ([H, c_int32, POINTER(c_int64)], c_int32),
                 "srm_set_scale": ([H, c_double], c_int32),
                 "srm_get_state": ([H, POINTER(srm_state_info)], c_int32),
@@ -233,6 +237,32 @@ def srm_overlap_pairs(h, cap: int | None = None) -> np.ndarray:
     ij = np.zeros((max(cap, 1), 2), dtype=np.int64)
     _check(lib.srm_overlap_pairs(h, ij.ctypes.data, int(cap), ctypes.byref(n)))
     return ij[:min(int(n.value), cap)].copy()
+
+
+def srm_nearest(h, n: int):
+    """(centre distance, partner id, smallest surface gap) of every particle."""
+    d, g = np.zeros(n), np.zeros(n)
+    j = np.zeros(n, dtype=np.int64)
+    _check(load().srm_nearest(h, d.ctypes.data, j.ctypes.data, g.ctypes.data))
+    return d, j, g
+
+
+def srm_rdf(h, r_max: float, bins: int):
+    """(ordered-pair counts per bin, g(r)) of the centres."""
+    c = np.zeros(bins, dtype=np.int64)
+    g = np.zeros(bins)
+    _check(load().srm_rdf(h, float(r_max), int(bins), c.ctypes.data, g.ctypes.data))
+    return c, g
+
+
+def srm_voronoi_lvf(h, n: int, voxels):
+    """(voxel counts, local volume fraction) of every particle."""
+    M = np.ones(3, dtype=np.int32)
+    M[:len(voxels)] = np.asarray(voxels, dtype=np.int32)
+    c = np.zeros(n, dtype=np.int64)
+    lvf = np.zeros(n)
+    _check(load().srm_voronoi_lvf(h, M.ctypes.data, c.ctypes.data, lvf.ctypes.data))
+    return c, lvf
 
 
 def srm_sweep(h, count: int = 1) -> int:
@@ -363,6 +393,15 @@ class Rve:
 
     def overlap_pairs(self) -> np.ndarray:
         return srm_overlap_pairs(self.h)
+
+    def nearest(self):
+        return srm_nearest(self.h, self.n)
+
+    def rdf(self, r_max: float, bins: int):
+        return srm_rdf(self.h, r_max, bins)
+
+    def voronoi_lvf(self, voxels):
+        return srm_voronoi_lvf(self.h, self.n, voxels)
 
     def sweep(self, count: int = 1) -> int:
         return srm_sweep(self.h, count)

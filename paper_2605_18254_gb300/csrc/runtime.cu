@@ -672,7 +672,7 @@ srm_status member_certify(Group &g, size_t r, int64_t *overlap_pairs, double *mi
     srm::launch_inspect_bin(mb.d, mb.solo, g.stream);
     srm::launch_pairs_count(mb.d, mb.dim, mb.n, 1, g.stream);
     srm::launch_inspect_end(mb.d, g.stream);
-    g.launches += 1 + 7 + 1 + 1;
+    g.launches += 1 + 1 + 7 + 1 + 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(g.pin_red, mb.h.red, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, g.stream));
     CK(cudaStreamSynchronize(g.stream));
@@ -862,6 +862,138 @@ srm_status srm_certify(srm_rve *h, int64_t *overlap_pairs, double *min_gap, doub
     return member_certify(h->g, 0, overlap_pairs, min_gap, phi);
 }
 
+// ---------------------------------------------------------------------------
+// Structure descriptors of P (Section 3.2), on its binary64 binning at its
+// own scale (as the certification).
+// ---------------------------------------------------------------------------
+static void *analysis_scratch(Group &g, Member &mb, size_t bytes)
+{
+    if (bytes > mb.an_bytes) {
+        void *q = dev_alloc(g, bytes);
+        if (!q) return nullptr;
+        mb.d_an = q;
+        mb.an_bytes = bytes;
+    }
+    return mb.d_an;
+}
+
+srm_status srm_nearest(srm_rve *h, double *nn_dist, int64_t *nn_id, double *gap)
+{
+    if (!h || !nn_dist || !gap) return fail(SRM_E_ARG, "null argument");
+    Group &g = h->g;
+    Member &mb = *g.m[0];
+    srm_status st = member_idle(g, 0);
+    if (st != SRM_OK) return st;
+    const size_t n = (size_t)mb.n;
+    unsigned char *buf = (unsigned char *)analysis_scratch(g, mb, 24 * n);
+    if (!buf) return fail(SRM_E_NOMEM, "analysis scratch");
+    double *d_dist = (double *)buf, *d_gap = (double *)(buf + 8 * n);
+    long long *d_id = (long long *)(buf + 16 * n);
+    srm::launch_inspect_bin(mb.d, mb.solo, g.stream);
+    srm::launch_nearest(mb.d, mb.dim, mb.n, d_dist, d_id, d_gap, g.stream);
+    srm::launch_inspect_end(mb.d, g.stream);
+    g.launches += 1 + 1 + 7 + 1 + 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(nn_dist, d_dist, 8 * n, cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaMemcpyAsync(gap, d_gap, 8 * n, cudaMemcpyDeviceToHost, g.stream));
+    if (nn_id) CK(cudaMemcpyAsync(nn_id, d_id, 8 * n, cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    return SRM_OK;
+}
+
+srm_status srm_rdf(srm_rve *h, double r_max, int32_t bins, int64_t *counts, double *gr)
+{
+    if (!h || !counts) return fail(SRM_E_ARG, "null argument");
+    if (!(r_max > 0.0) || bins < 1 || bins > 4096) return fail(SRM_E_ARG, "need r_max > 0 and 1 <= bins <= 4096");
+    Group &g = h->g;
+    Member &mb = *g.m[0];
+    srm_status st = member_idle(g, 0);
+    if (st != SRM_OK) return st;
+    const RveDev &s0 = mb.h;
+    for (int a = 0; a < mb.dim; a++)
+        if (r_max > 0.5 * s0.L[a]) return fail(SRM_E_ARG, "r_max exceeds half the box (minimum image)");
+    unsigned long long *d_c = (unsigned long long *)analysis_scratch(g, mb, sizeof(unsigned long long) * (size_t)bins);
+    if (!d_c) return fail(SRM_E_NOMEM, "analysis scratch");
+    CK(cudaMemsetAsync(d_c, 0, sizeof(unsigned long long) * (size_t)bins, g.stream));
+    srm::launch_inspect_bin(mb.d, mb.solo, g.stream);
+    if ((st = pull_state(g, 0)) != SRM_OK) return st;  // the grid of the inspection binning
+    const RveDev &sv = g.pin[0];
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < mb.dim; a++) {
+        const int H = (int)std::ceil(r_max / sv.gw[a]);
+        if (2 * H + 1 >= sv.gn[a]) {
+            lo[a] = 0;
+            hi[a] = sv.gn[a] - 1;
+        } else {
+            lo[a] = -H;
+            hi[a] = H;
+        }
+    }
+    srm::launch_rdf(mb.d, mb.dim, mb.n, r_max, bins, lo, hi, d_c, g.stream);
+    srm::launch_inspect_end(mb.d, g.stream);
+    g.launches += 1 + 1 + 7 + 1 + 1;
+    CK(cudaGetLastError());
+    std::vector<unsigned long long> hc((size_t)bins);
+    CK(cudaMemcpyAsync(hc.data(), d_c, sizeof(unsigned long long) * (size_t)bins, cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    double V = 1.0;
+    for (int a = 0; a < mb.dim; a++) V *= s0.L[a];
+    const double pi = 3.14159265358979323846, dr = r_max / (double)bins, N = (double)mb.n;
+    for (int b = 0; b < bins; b++) {
+        counts[b] = (int64_t)hc[(size_t)b];
+        if (gr) {
+            const double r0 = b * dr, r1 = (b + 1) * dr;
+            const double shell =
+                mb.dim == 2 ? pi * (r1 * r1 - r0 * r0) : 4.0 / 3.0 * pi * (r1 * r1 * r1 - r0 * r0 * r0);
+            gr[b] = (double)counts[b] * V / (N * (N - 1.0) * shell);
+        }
+    }
+    return SRM_OK;
+}
+
+srm_status srm_voronoi_lvf(srm_rve *h, const int32_t voxels[3], int64_t *count, double *lvf)
+{
+    if (!h || !voxels || !count) return fail(SRM_E_ARG, "null argument");
+    Group &g = h->g;
+    Member &mb = *g.m[0];
+    srm_status st = member_idle(g, 0);
+    if (st != SRM_OK) return st;
+    int32_t M[3] = {1, 1, 1};
+    double hv[3] = {1.0, 1.0, 1.0};
+    long long total = 1;
+    for (int a = 0; a < mb.dim; a++) {
+        if (voxels[a] < 1 || voxels[a] > 65536) return fail(SRM_E_ARG, "voxels per axis must be in [1, 65536]");
+        M[a] = voxels[a];
+        hv[a] = mb.h.L[a] / (double)M[a];
+        total *= M[a];
+    }
+    if (total > (1LL << 34)) return fail(SRM_E_ARG, "more than 2^34 voxels");
+    const size_t n = (size_t)mb.n;
+    unsigned long long *d_c = (unsigned long long *)analysis_scratch(g, mb, 8 * n);
+    if (!d_c) return fail(SRM_E_NOMEM, "analysis scratch");
+    CK(cudaMemsetAsync(d_c, 0, 8 * n, g.stream));
+    srm::launch_inspect_bin(mb.d, mb.solo, g.stream);
+    srm::launch_voronoi(mb.d, mb.dim, M, hv, d_c, g.stream);
+    srm::launch_inspect_end(mb.d, g.stream);
+    g.launches += 1 + 1 + 7 + 1 + 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(count, d_c, 8 * n, cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    if (lvf) {
+        std::vector<double> xyz(n * (size_t)mb.dim), rad(n);
+        if ((st = member_positions(g, 0, xyz.data(), rad.data())) != SRM_OK) return st;
+        double cell = 1.0;
+        for (int a = 0; a < mb.dim; a++) cell *= hv[a];
+        const double pi = 3.14159265358979323846;
+        for (size_t j = 0; j < n; j++) {
+            const double R = rad[j];
+            const double v = mb.dim == 2 ? pi * R * R : 4.0 / 3.0 * pi * R * R * R;
+            lvf[j] = count[j] ? v / ((double)count[j] * cell) : HUGE_VAL;
+        }
+    }
+    return SRM_OK;
+}
+
 srm_status srm_overlap_pairs(srm_rve *h, int64_t *ij, int64_t cap, int64_t *n)
 {
     if (!h || !n || (cap > 0 && !ij)) return fail(SRM_E_ARG, "null argument");
@@ -872,7 +1004,7 @@ srm_status srm_overlap_pairs(srm_rve *h, int64_t *ij, int64_t cap, int64_t *n)
     srm::launch_inspect_bin(mb.d, mb.solo, g.stream);
     srm::launch_pairs_count(mb.d, mb.dim, mb.n, 0, g.stream);
     srm::launch_scan(mb.solo, 1, g.stream);
-    g.launches += 1 + 7 + 1 + 3;
+    g.launches += 1 + 1 + 7 + 1 + 3;
     CK(cudaGetLastError());
     uint32_t total = 0;
     CK(cudaMemcpyAsync(g.pin_red, mb.h.pcount + mb.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, g.stream));

@@ -53,6 +53,8 @@ struct Member {
     double *d_xyz = nullptr, *d_rad = nullptr;
     long long *d_ij = nullptr;
     int64_t d_ij_cap = 0;
+    void *d_an = nullptr;  // scratch of the structure descriptors (grows)
+    size_t an_bytes = 0;
 };
 
 // RVEs advanced by the same launches.

@@ -49,6 +49,13 @@ void launch_inspect_end(RveDev *d_st, cudaStream_t s);
 void launch_pairs_count(RveDev *d_st, int dim, int64_t n, int want_gap, cudaStream_t s);
 void launch_pairs_fill(RveDev *d_st, int dim, int64_t n, long long *ij, cudaStream_t s);
 void launch_gather(RveDev *d_st, int dim, bool f32, int64_t n, double *xyz, double *rad, cudaStream_t s);
+
+// structure descriptors (k_analysis.cu), on the binning of launch_inspect_bin
+void launch_nearest(RveDev *d_st, int dim, int64_t n, double *nn_dist, long long *nn_id, double *gap, cudaStream_t s);
+void launch_rdf(RveDev *d_st, int dim, int64_t n, double r_max, int bins, const int lo[3], const int hi[3],
+                unsigned long long *counts, cudaStream_t s);
+void launch_voronoi(RveDev *d_st, int dim, const int32_t M[3], const double h[3], unsigned long long *count,
+                    cudaStream_t s);
 void launch_import(RveDev *d_st, int dim, bool f32, int64_t n, const double *xyz, const double *rb,
                    cudaStream_t s);
 
