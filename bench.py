@@ -587,13 +587,16 @@ def run_regimes(args, rank, world, local_rank):
     import paper_2605_18254_gb300 as srm
     torch.cuda.set_device(local_rank)
     cap = args.regime_seconds
+    # (dim, N, target, seed, c_w, c_m / target radius): slow swelling with
+    # long migration relaxes toward equilibrium; fast swelling with migration
+    # just long enough to clear the overlaps of one swell step leaves clusters
     runs = {
         "2d_equilibrium_0.5": (2, 5000, 0.5, 11, 0.002, 0.5),
-        "2d_clustered_0.5": (2, 5000, 0.5, 11, 0.05, 0.02),
-        "3d_equilibrium_0.5": (3, 5000, 0.5, 12, 0.002, 0.5),
-        "3d_clustered_0.5": (3, 5000, 0.5, 12, 0.05, 0.02),
-        "2d_dense_0.87": (2, 5000, 0.87, 13, 0.002, 0.3),
-        "3d_dense_0.60": (3, 10000, 0.60, 14, 0.002, 0.3),
+        "2d_clustered_0.5": (2, 5000, 0.5, 11, 0.01, 0.03),
+        "3d_equilibrium_0.5": (3, 5000, 0.5, 12, 0.002, 0.1),
+        "3d_clustered_0.5": (3, 5000, 0.5, 12, 0.01, 0.03),
+        "2d_dense_0.87": (2, 5000, 0.87, 13, 0.0005, 0.05),
+        "3d_dense_0.60": (3, 10000, 0.60, 14, 0.0005, 0.05),
     }
     out = {}
     t0 = time.perf_counter()

@@ -97,3 +97,24 @@ def test_fp32_form_close():
     assert np.abs(c - oc).sum() <= 0.001 * c.sum()
     occ, _ = oracle.rdf(3, box, x, 0.1, 50)
     assert np.abs(cnt - occ).sum() <= 0.001 * occ.sum()
+
+
+def regime_lvf_std(c_w, c_m_rel, seed):
+    n, phi = 2000, 0.5
+    r_t = math.sqrt(phi / (n * math.pi))
+    g = srm.Rve(2, (1.0, 1.0), ("mono", r_t * (0.1 / phi) ** 0.5), phi, seed, n=n, c_m=c_m_rel * r_t, c_w=c_w,
+                precision=32, init="rsa", f0=0.1)
+    assert g.run_to_target(20000)["converged"]
+    assert g.certify()[0] == 0
+    c, lvf = g.voronoi_lvf((200, 200))
+    g.close()
+    return float(np.std(lvf))
+
+
+def test_clustered_regime_broadens_lvf():
+    """Fast swelling with short migration leaves clusters (Section 3.2, Fig.
+    5): at the same volume fraction the spread of the local volume fraction
+    is clearly larger than after slow swelling with long migration."""
+    eq = np.mean([regime_lvf_std(0.002, 0.5, s) for s in (1, 2)])
+    cl = np.mean([regime_lvf_std(0.01, 0.03, s) for s in (1, 2)])
+    assert cl > 1.4 * eq, (cl, eq)
