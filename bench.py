@@ -199,6 +199,66 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_member(args):
+    """One RVE of the ensemble run to target by the reference (worker
+    process); returns (particle updates, seconds)."""
+    import oracle
+    import srm_inputs
+    i, seed0 = args
+    w = srm_inputs.ensemble_member(i, 256, seed0)
+    s = oracle.System(w.dim, w.box, w.x, w.radii, lam=1.0, target_phi=w.target_phi, c_w=w.c_w, c_m=w.c_m,
+                      N_k=w.N_k, N_l=w.N_l, N_shake=w.N_shake, seed=w.seed)
+    t0 = time.perf_counter()
+    s.run()
+    dt = time.perf_counter() - t0
+    return w.n * s.counters()["sweeps"], dt
+
+
+def run_oracle_timing(args, rank, world):
+    """The reference on the host cores: C1 run in full; C2 and C3 one sweep,
+    extrapolated to the sweeps of a full run (labelled); ensemble throughput
+    of one reference process per core on the first members of C4."""
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    import platform
+    import oracle
+    import srm_inputs
+    out = {"host": {"machine": platform.machine(), "cores": os.cpu_count()}}
+    w = srm_inputs.disks_1k()
+    s = oracle.System(w.dim, w.box, w.x, w.radii, lam=1.0, target_phi=w.target_phi, c_w=w.c_w, c_m=w.c_m,
+                      N_k=w.N_k, N_l=w.N_l, N_shake=w.N_shake, seed=w.seed)
+    t0 = time.perf_counter()
+    s.run()
+    dt = time.perf_counter() - t0
+    sw = s.counters()["sweeps"]
+    out["disks_1k_full_run"] = {"seconds": dt, "sweeps": sw, "particle_updates_per_s": w.n * sw / dt,
+                                "cores": 1}
+    for name, sweeps_full in (("spheres_100k", args.c2_sweeps), ("poly_1m", args.c3_sweeps)):
+        wl = srm_inputs.RECIPES[name]()
+        ups, dts = cpu_sample(wl, 1)
+        out[name] = {"one_sweep_s": dts, "particle_updates_per_s": ups, "cores": 1,
+                     "extrapolated_time_to_target_s": dts * sweeps_full,
+                     "note": f"one sweep timed, times {sweeps_full} sweeps of the GPU run to target (extrapolated)"}
+    nproc = os.cpu_count() or 1
+    members = [(i, 0) for i in range(min(args.oracle_members, 256))]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(nproc) as pool:
+        res = pool.map(_oracle_member, members)
+    wall = time.perf_counter() - t0
+    out["ensemble_members"] = {"members": len(members), "processes": nproc, "wall_s": wall,
+                               "particle_updates_per_s": sum(u for u, _ in res) / wall,
+                               "note": "first members of the 256-RVE ensemble (2D disks), each run to target"}
+    line = {"impl": "reference", "metric": "reference throughput on the host cores", "value":
+            out["ensemble_members"]["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 0,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oracle timing: C1 in full, C2/C3 one sweep extrapolated, C4 members on "
+                                   f"{nproc} processes"}, "oracle": out}
+    print(json.dumps(line), flush=True)
+
+
 def combine_ranks(dev_s, e2e_s, updates, dist=None, device="cpu"):
     """Whole-job numbers of replicas: the slowest rank's times, the sum of
     the particle updates of all ranks (host-side reduction only; the ranks
@@ -632,12 +692,18 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-big", type=int, default=10_000_000)
     ap.add_argument("--regime-seconds", type=float, default=60.0)
+    ap.add_argument("--c2-sweeps", type=int, default=168, help="sweeps of the GPU run of spheres_100k to target")
+    ap.add_argument("--c3-sweeps", type=int, default=16711, help="sweeps of the GPU run of poly_1m to target")
+    ap.add_argument("--oracle-members", type=int, default=32)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "oracle_timing":
+        run_oracle_timing(args, rank, world)
         return
     if world > 1:
         import torch

@@ -169,15 +169,17 @@ def ensemble(count: int = 256, seed0: int = 0, n_lo: float = 1e3, n_hi: float = 
     """Independent RVEs: the first half disks, the second half spheres; RVE i
     draws its size log-uniform in [n_lo, n_hi] and its target uniform in
     [phi_lo, phi_hi] from the input stream of seed i, and runs with seed i."""
-    out = []
-    for i in range(count):
-        u = uniforms(seed0 + i, 0x4D455441, 2)  # "META"
-        n = int(math.floor(n_lo * (n_hi / n_lo) ** u[0]))
-        phi_t = phi_lo + (phi_hi - phi_lo) * u[1]
-        dim = 2 if i < count // 2 else 3
-        w = _mono(f"ensemble[{i}]", dim, n, phi_t, f0, seed0 + i)
-        out.append(w)
-    return out
+    return [ensemble_member(i, count, seed0, n_lo, n_hi, phi_lo, phi_hi, f0) for i in range(count)]
+
+
+def ensemble_member(i: int, count: int = 256, seed0: int = 0, n_lo: float = 1e3, n_hi: float = 1e5,
+                    phi_lo: float = 0.30, phi_hi: float = 0.55, f0: float = 0.1) -> Workload:
+    """RVE i of ensemble(count, seed0, ...)."""
+    u = uniforms(seed0 + i, 0x4D455441, 2)  # "META"
+    n = int(math.floor(n_lo * (n_hi / n_lo) ** u[0]))
+    phi_t = phi_lo + (phi_hi - phi_lo) * u[1]
+    dim = 2 if i < count // 2 else 3
+    return _mono(f"ensemble[{i}]", dim, n, phi_t, f0, seed0 + i)
 
 
 RECIPES = {
