@@ -234,6 +234,31 @@ typedef struct srm_state_info {
 
 srm_status srm_get_state(srm_rve *h, srm_state_info *out);
 
+/* Launch shape of the sweep (not in the paper: a property of this GPU
+ * implementation).  Results do not depend on it -- the sweep's order is
+ * fixed by the cells' colours, and cells whose stencil exceeds the staging
+ * capacity read the rest from global memory -- only the speed does. */
+typedef struct srm_tuning {
+    int32_t sweep_blocks_per_sm;   /* blocks per SM of the persistent sweep grid; 0 = all that fit */
+    int32_t stage_capacity;        /* candidates a sweep warp stages in shared memory (rounded up to a
+                                      multiple of 32, clamped to [64, 512] FP32 / [64, 256] FP64;
+                                      <= 0 keeps the current one) */
+    int32_t candidates;            /* autotune output: shapes tried */
+    int32_t reserved;
+    double ns_per_particle_sweep;  /* autotune output: best device time per particle sweep */
+} srm_tuning;
+
+/* Autotuner: runs the RVE (or batch) for `supersteps` super-steps (>= 1,
+ * rounded up to whole recorded graphs of 8) with each candidate shape --
+ * blocks per SM from 2 to the resident maximum, staging capacity at the
+ * current value, half and twice -- in two interleaved rounds, scores each
+ * by device time per particle sweep (CUDA events) and keeps the fastest.
+ * The super-steps are real work: the RVEs advance (and may finish).  *best
+ * (may be NULL) receives the chosen shape.  Synchronises the stream. */
+srm_status srm_autotune(srm_rve *h, int32_t supersteps, srm_tuning *best);
+srm_status srm_set_tuning(srm_rve *h, const srm_tuning *t);   /* re-records the graphs */
+srm_status srm_get_tuning(srm_rve *h, srm_tuning *t);
+
 /* Per-stage device time of the super-steps run while timing is on, from CUDA
  * events recorded between the launches of each super-step (one host
  * synchronisation per super-step while on, so use it for measurement only).
@@ -307,6 +332,11 @@ srm_status srm_batch_advance(srm_batch *b, int32_t supersteps);
 /* Runs every RVE of the batch to its target (at most max_iters iterations
  * each; SRM_E_NOT_CONVERGED otherwise). */
 srm_status srm_batch_run(srm_batch *b, int64_t max_iters);
+
+/* The autotuner and launch shape of a batch (as srm_autotune). */
+srm_status srm_batch_autotune(srm_batch *b, int32_t supersteps, srm_tuning *best);
+srm_status srm_batch_set_tuning(srm_batch *b, const srm_tuning *t);
+srm_status srm_batch_get_tuning(srm_batch *b, srm_tuning *t);
 
 /* Slots that reached their target since the last poll, each reported once. */
 srm_status srm_batch_poll(srm_batch *b, int32_t *done_slots, int32_t cap, int32_t *n_done);

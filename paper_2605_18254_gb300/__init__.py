@@ -23,7 +23,7 @@ from . import build as _build
 
 __all__ = ["SrmError", "Rve", "load", "srm_init", "srm_step", "srm_run_to_target", "srm_certify",
            "srm_positions", "srm_overlap_pairs", "srm_sweep", "srm_set_scale", "srm_get_state",
-           "srm_nearest", "srm_rdf", "srm_voronoi_lvf",
+           "srm_nearest", "srm_rdf", "srm_voronoi_lvf", "srm_tuning",
            "srm_destroy", "srm_last_error", "srm_set_timing", "srm_get_timings",
            "srm_certify_noalloc", "srm_save", "srm_load", "srm_job_footprint", "make_job", "Batch",
            "PREC_F64", "PREC_F32"]
@@ -92,6 +92,11 @@ class srm_job(Structure):
                 ("seed", c_uint64), ("params", srm_params)]
 
 
+class srm_tuning(Structure):
+    _fields_ = [("sweep_blocks_per_sm", c_int32), ("stage_capacity", c_int32), ("candidates", c_int32),
+                ("reserved", c_int32), ("ns_per_particle_sweep", c_double)]
+
+
 class srm_timings(Structure):
     _fields_ = [("ms_bin", c_double), ("ms_sweep", c_double), ("ms_check", c_double),
                 ("ms_control", c_double), ("supersteps", c_int64), ("sweep_launches", c_int64),
@@ -127,6 +132,12 @@ def load() -> ctypes.CDLL:
                 "srm_sweep": ([H, c_int32, POINTER(c_int64)], c_int32),
                 "srm_set_scale": ([H, c_double], c_int32),
                 "srm_get_state": ([H, POINTER(srm_state_info)], c_int32),
+                "srm_autotune": ([H, c_int32, POINTER(srm_tuning)], c_int32),
+                "srm_set_tuning": ([H, POINTER(srm_tuning)], c_int32),
+                "srm_get_tuning": ([H, POINTER(srm_tuning)], c_int32),
+                "srm_batch_autotune": ([H, c_int32, POINTER(srm_tuning)], c_int32),
+                "srm_batch_set_tuning": ([H, POINTER(srm_tuning)], c_int32),
+                "srm_batch_get_tuning": ([H, POINTER(srm_tuning)], c_int32),
                 "srm_destroy": ([H], None),
                 "srm_set_timing": ([H, c_int32], c_int32),
                 "srm_save": ([H, c_void_p, POINTER(c_size_t)], c_int32),
@@ -394,6 +405,20 @@ class Rve:
     def overlap_pairs(self) -> np.ndarray:
         return srm_overlap_pairs(self.h)
 
+    def autotune(self, supersteps: int = 8) -> dict:
+        t = srm_tuning()
+        _check(load().srm_autotune(self.h, int(supersteps), ctypes.byref(t)))
+        return _as_dict(t)
+
+    def set_tuning(self, sweep_blocks_per_sm: int, stage_capacity: int = 0):
+        t = srm_tuning(sweep_blocks_per_sm=int(sweep_blocks_per_sm), stage_capacity=int(stage_capacity))
+        _check(load().srm_set_tuning(self.h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = srm_tuning()
+        _check(load().srm_get_tuning(self.h, ctypes.byref(t)))
+        return _as_dict(t)
+
     def nearest(self):
         return srm_nearest(self.h, self.n)
 
@@ -527,6 +552,20 @@ class Batch:
 
     def advance(self, supersteps: int):
         _check(load().srm_batch_advance(self.h, int(supersteps)))
+
+    def autotune(self, supersteps: int = 8) -> dict:
+        t = srm_tuning()
+        _check(load().srm_batch_autotune(self.h, int(supersteps), ctypes.byref(t)))
+        return _as_dict(t)
+
+    def set_tuning(self, sweep_blocks_per_sm: int, stage_capacity: int = 0):
+        t = srm_tuning(sweep_blocks_per_sm=int(sweep_blocks_per_sm), stage_capacity=int(stage_capacity))
+        _check(load().srm_batch_set_tuning(self.h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = srm_tuning()
+        _check(load().srm_batch_get_tuning(self.h, ctypes.byref(t)))
+        return _as_dict(t)
 
     def run(self, max_iters: int = 1 << 40) -> bool:
         st = load().srm_batch_run(self.h, int(max_iters))

@@ -137,6 +137,27 @@ srm_status srm_batch_advance(srm_batch *b, int32_t supersteps)
     return SRM_OK;
 }
 
+srm_status srm_batch_autotune(srm_batch *b, int32_t supersteps, srm_tuning *best)
+{
+    if (!b) return fail(SRM_E_ARG, "null handle");
+    return group_autotune(b->g, supersteps, best);
+}
+
+srm_status srm_batch_set_tuning(srm_batch *b, const srm_tuning *t)
+{
+    if (!b || !t) return fail(SRM_E_ARG, "null argument");
+    return group_set_tuning(b->g, t->sweep_blocks_per_sm, t->stage_capacity);
+}
+
+srm_status srm_batch_get_tuning(srm_batch *b, srm_tuning *t)
+{
+    if (!b || !t) return fail(SRM_E_ARG, "null argument");
+    *t = srm_tuning{};
+    t->sweep_blocks_per_sm = b->g.sweep_bps;
+    t->stage_capacity = b->g.cap;
+    return SRM_OK;
+}
+
 srm_status srm_batch_run(srm_batch *b, int64_t max_iters)
 {
     if (!b || max_iters < 0) return fail(SRM_E_ARG, "bad argument");

@@ -623,8 +623,16 @@ static void launch_sweep_dim(const BatchShape &b, cudaStream_t s)
     const size_t smem = sweep_smem(F32, b.cap);
     const int64_t want64 = (b.sub_total * (DIM == 3 ? 27 : 9) + SW_WARPS - 1) / SW_WARPS;
     const int want = (int)(want64 > 0x7fffffff ? 0x7fffffff : want64);
-    const int res = resident_blocks(k_sweep_df<DIM, F32>, smem) * (g_sms > 0 ? g_sms : 1);
+    int per_sm = resident_blocks(k_sweep_df<DIM, F32>, smem);
+    if (b.sweep_bps > 0 && b.sweep_bps < per_sm) per_sm = b.sweep_bps;
+    const int res = per_sm * (g_sms > 0 ? g_sms : 1);
     k_sweep_df<DIM, F32><<<want < res ? want : res, SW_WARPS * 32, smem, s>>>(b.d, b.cap);
+}
+
+int sweep_blocks_per_sm(bool f32, int cap)
+{
+    const size_t smem = sweep_smem(f32, cap);
+    return f32 ? resident_blocks(k_sweep_df<3, true>, smem) : resident_blocks(k_sweep_df<3, false>, smem);
 }
 
 // Trial directions (k_draw), then the sweep of the 3D and of the 2D RVEs

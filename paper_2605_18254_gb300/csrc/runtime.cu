@@ -453,6 +453,7 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     sh.has3d = has3d;
     sh.has2d = has2d;
     sh.cap = g.cap;
+    sh.sweep_bps = g.sweep_bps;
     return SRM_OK;
 }
 
@@ -513,6 +514,118 @@ srm_status group_finalize(Group &g)
         return fail(SRM_E_NOMEM, "pinned host allocation failed");
     if ((st = capture(g, 1, &g.g1)) != SRM_OK) return st;
     return capture(g, g.gN_steps, &g.gN);
+}
+
+bool idle_mode(int32_t m);
+
+// Launch shape of the sweep: blocks per SM of its persistent grid and the
+// staging capacity.  The graphs are recorded again; results do not depend
+// on either (the dataflow order is that of the cells' colours, and cells
+// that do not fit the staging read the rest from global memory).
+srm_status group_set_tuning(Group &g, int sweep_bps, int cap)
+{
+    const int cmax = srm::sweep_cap_max(g.f32);
+    cap = cap <= 0 ? g.cap : (cap + 31) / 32 * 32;
+    if (cap < 64) cap = 64;
+    if (cap > cmax) cap = cmax;
+    if (sweep_bps < 0) return fail(SRM_E_ARG, "blocks per SM must be >= 0");
+    CK(cudaStreamSynchronize(g.stream));
+    if (g.g1) cudaGraphExecDestroy(g.g1);
+    if (g.gN) cudaGraphExecDestroy(g.gN);
+    if (g.gT) cudaGraphExecDestroy(g.gT);
+    g.g1 = g.gN = g.gT = nullptr;
+    g.cap = cap;
+    g.sweep_bps = sweep_bps;
+    g.sh.cap = cap;
+    g.sh.sweep_bps = sweep_bps;
+    srm_status st = capture(g, 1, &g.g1);
+    if (st != SRM_OK) return st;
+    return capture(g, g.gN_steps, &g.gN);
+}
+
+// Particle sweeps done so far, summed over the group's RVEs (N x sweeps).
+static double group_work(const Group &g)
+{
+    double w = 0.0;
+    for (size_t r = 0; r < g.m.size(); r++) w += (double)g.pin[r].n * (double)g.pin[r].sweeps;
+    return w;
+}
+
+// Tries each candidate launch shape on the running group, in interleaved
+// rounds of `supersteps` super-steps (real work: the RVEs advance), scores
+// it by device time per particle sweep, and keeps the best.
+srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best)
+{
+    if (supersteps < 1) return fail(SRM_E_ARG, "supersteps must be >= 1");
+    const int cap0 = g.cap, cmax = srm::sweep_cap_max(g.f32);
+    std::vector<int> caps{cap0};
+    for (int c : {cap0 / 2, 2 * cap0}) {
+        c = std::max(64, std::min(cmax, (c + 31) / 32 * 32));
+        if (std::find(caps.begin(), caps.end(), c) == caps.end()) caps.push_back(c);
+    }
+    std::vector<std::pair<int, int>> cand;
+    for (int c : caps) {
+        const int mx = srm::sweep_blocks_per_sm(g.f32, c);
+        for (int b = 2; b < mx; b++) cand.push_back({b, c});
+        cand.push_back({0, c});
+    }
+    std::vector<double> score(cand.size(), 0.0);
+    std::vector<int> seen(cand.size(), 0);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int graphs = (supersteps + g.gN_steps - 1) / g.gN_steps;
+    srm_status st = SRM_OK;
+    for (int round = 0; round < 2 && st == SRM_OK; round++) {
+        for (size_t k = 0; k < cand.size() && st == SRM_OK; k++) {
+            if ((st = group_set_tuning(g, cand[k].first, cand[k].second)) != SRM_OK) break;
+            if ((st = pull_states(g)) != SRM_OK) break;
+            const double w0 = group_work(g);
+            CK(cudaEventRecord(e0, g.stream));
+            for (int i = 0; i < graphs; i++) CK(cudaGraphLaunch(g.gN, g.stream));
+            CK(cudaEventRecord(e1, g.stream));
+            g.launches += g.launches_per_step * g.gN_steps * graphs;
+            if ((st = pull_states(g)) != SRM_OK) break;
+            const double dw = group_work(g) - w0;
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (dw > 0.0) {
+                score[k] += ms / dw;
+                seen[k]++;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SRM_OK) return st;
+    size_t bi = 0;
+    double bs = 1e300;
+    for (size_t k = 0; k < cand.size(); k++)
+        if (seen[k] && score[k] / seen[k] < bs) {
+            bs = score[k] / seen[k];
+            bi = k;
+        }
+    const bool any = bs < 1e300;
+    const int bps = any ? cand[bi].first : 0, cap = any ? cand[bi].second : cap0;
+    if ((st = group_set_tuning(g, bps, cap)) != SRM_OK) return st;
+    // leave every RVE between iterations, as the other calls expect (an
+    // iteration takes at most N_k + N_shake + 1 super-steps)
+    for (int k = 0; k < 4096; k++) {
+        if ((st = pull_states(g)) != SRM_OK) return st;
+        bool idle = true;
+        for (size_t r = 0; r < g.m.size(); r++) idle = idle && idle_mode(g.pin[r].mode);
+        if (idle) break;
+        CK(cudaGraphLaunch(g.g1, g.stream));
+        g.launches += g.launches_per_step;
+    }
+    if (best) {
+        best->sweep_blocks_per_sm = bps;
+        best->stage_capacity = cap;
+        best->candidates = (int32_t)cand.size();
+        best->reserved = 0;
+        best->ns_per_particle_sweep = any ? 1e6 * bs : 0.0;
+    }
+    return SRM_OK;
 }
 
 static srm_status device_status(int32_t code)
@@ -991,6 +1104,27 @@ srm_status srm_voronoi_lvf(srm_rve *h, const int32_t voxels[3], int64_t *count, 
             lvf[j] = count[j] ? v / ((double)count[j] * cell) : HUGE_VAL;
         }
     }
+    return SRM_OK;
+}
+
+srm_status srm_autotune(srm_rve *h, int32_t supersteps, srm_tuning *best)
+{
+    if (!h) return fail(SRM_E_ARG, "null handle");
+    return group_autotune(h->g, supersteps, best);
+}
+
+srm_status srm_set_tuning(srm_rve *h, const srm_tuning *t)
+{
+    if (!h || !t) return fail(SRM_E_ARG, "null argument");
+    return group_set_tuning(h->g, t->sweep_blocks_per_sm, t->stage_capacity);
+}
+
+srm_status srm_get_tuning(srm_rve *h, srm_tuning *t)
+{
+    if (!h || !t) return fail(SRM_E_ARG, "null argument");
+    *t = srm_tuning{};
+    t->sweep_blocks_per_sm = h->g.sweep_bps;
+    t->stage_capacity = h->g.cap;
     return SRM_OK;
 }
 

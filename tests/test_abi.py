@@ -41,6 +41,7 @@ STRUCTS = {
     "srm_state_info": srm.srm_state_info,
     "srm_timings": srm.srm_timings,
     "srm_job": srm.srm_job,
+    "srm_tuning": srm.srm_tuning,
 }
 
 

@@ -123,3 +123,28 @@ def test_checkpoint_resume_bit_exact(precision):
     assert sa["sweep"] == sb["sweep"] and sa["lambda"] == sb["lambda"]
     g.close()
     h.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_launch_shape_does_not_change_results(precision):
+    """The autotuner and explicit launch shapes (one sweep block per SM, the
+    smallest staging capacity, which sends dense cells down the overflow
+    path) change the speed only: every member ends bit for bit as alone."""
+    ws = mixed_workloads()
+    b = srm.Batch([job_of(w, precision) for w in ws])
+    t = b.autotune(8)
+    assert t["candidates"] >= 2 and t["ns_per_particle_sweep"] > 0
+    assert b.tuning()["stage_capacity"] == t["stage_capacity"]
+    assert b.run(3) in (True, False)  # every RVE is between iterations after tuning
+    b.set_tuning(1, 64)
+    tn = b.tuning()
+    assert tn["sweep_blocks_per_sm"] == 1 and tn["stage_capacity"] == 64
+    b.advance(24)
+    b.set_tuning(0, 0)
+    assert b.run()
+    for i, w in enumerate(ws):
+        x, r, st = alone(w, precision)
+        xb, _ = b.positions(i)
+        np.testing.assert_array_equal(xb, x)
+        assert b.state(i)["sweeps"] == st["sweeps"]
+    b.close()
