@@ -581,10 +581,14 @@ def run_serve(args, rank, world, local_rank):
     for i in range(n_jobs):
         j = job(i)  # keep the arrays the job points to alive while it is used
         small_cells = max(small_cells, srm.srm_job_footprint(j[0])[1])
-    pools = [serve.PoolSpec(slots=args.serve_slots, max_particles=1_000_000, max_cells=small_cells),
-             serve.PoolSpec(slots=1, max_particles=big_n, max_cells=big_cells)]
+    # small jobs in a 2D and a 3D pool (one sweep launch per super-step each,
+    # the pools overlap on their streams), the big job in a pool of its own
+    half = max(1, args.serve_slots // 2)
+    pools = [serve.PoolSpec(slots=half, max_particles=1_000_000, max_cells=small_cells, dim=2),
+             serve.PoolSpec(slots=half, max_particles=1_000_000, max_cells=small_cells, dim=3),
+             serve.PoolSpec(slots=1, max_particles=big_n, max_cells=big_cells, dim=3)]
     server = serve.Server(pools, precision=args.precision, advance=16)
-    # capacity of the small-job pool: a burst of jobs all arriving at t = 0
+    # capacity of the small-job pools: a burst of jobs all arriving at t = 0
     calib = [serve.Request(rid=i, arrival=0.0, job=job(i)) for i in range(min(16, n_jobs))]
     done, wall = server.run(calib)
     rate = 0.7 * len(done) / wall
@@ -603,9 +607,9 @@ def run_serve(args, rank, world, local_rank):
         "config": {"workload": f"serving: 1 RVE of {big_n} 3D spheres (unit cube, target 0.30) submitted at t=0 "
                                f"beside {n_jobs} jobs (2D/3D, N log-uniform 1e4..1e6, targets 0.30..0.50) "
                                f"arriving as a Poisson stream at {rate:.2f} jobs/s (70% of the measured "
-                               "capacity of the small-job pool); pools: "
-                               f"{args.serve_slots} slots of 1e6 particles + 1 slot of {big_n}, each pool one batch "
-                               "on its own stream"},
+                               "capacity of the small-job pools); pools: "
+                               f"{half} 2D slots and {half} 3D slots of 1e6 particles + 1 slot of {big_n}, each pool "
+                               "one batch on its own stream"},
         "serving": summ, "big_job_time_to_target_s": big.finished - big.arrival,
         "big_job_sweeps": big.sweeps, "arrival_rate_jobs_per_s": rate,
         "clocks": clk.summary(),

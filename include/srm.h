@@ -312,10 +312,12 @@ srm_status srm_batch_create(srm_batch **out, const srm_job *jobs, int32_t n_jobs
 
 /* A batch of n_slots empty slots for continuous serving: each slot takes a
  * job of at most max_particles particles and max_cells cells on the finest
- * grid of its run (srm_job_footprint), 2D or 3D.  stage_capacity: candidates
- * a sweep warp stages in shared memory (0: 256). */
+ * grid of its run (srm_job_footprint), of dimension dim (2 or 3; 0: either
+ * -- every super-step then runs the sweeps of both dimensions, one after
+ * the other).  stage_capacity: candidates a sweep warp stages in shared
+ * memory (0: 256). */
 srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_particles,
-                                  int64_t max_cells, int32_t precision, int32_t stage_capacity,
+                                  int64_t max_cells, int32_t dim, int32_t precision, int32_t stage_capacity,
                                   void *cuda_stream, const srm_allocator *alloc);
 
 /* Particles and finest-grid cells a job needs (for admission decisions). */

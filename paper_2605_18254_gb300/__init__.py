@@ -144,7 +144,7 @@ def load() -> ctypes.CDLL:
                 "srm_load": ([POINTER(H), c_void_p, c_size_t, c_void_p, POINTER(srm_allocator)], c_int32),
                 "srm_batch_create": ([POINTER(H), POINTER(srm_job), c_int32, c_void_p,
                                       POINTER(srm_allocator)], c_int32),
-                "srm_batch_create_slots": ([POINTER(H), c_int32, c_int64, c_int64, c_int32, c_int32,
+                "srm_batch_create_slots": ([POINTER(H), c_int32, c_int64, c_int64, c_int32, c_int32, c_int32,
                                             c_void_p, POINTER(srm_allocator)], c_int32),
                 "srm_job_footprint": ([POINTER(srm_job), POINTER(c_int64), POINTER(c_int64)], c_int32),
                 "srm_batch_admit": ([H, c_int32, POINTER(srm_job)], c_int32),
@@ -516,7 +516,7 @@ class Batch:
     creates empty slots for continuous serving (admit / advance / poll / release).
     """
 
-    def __init__(self, jobs=None, *, slots=0, max_particles=0, max_cells=0, precision=PREC_F32,
+    def __init__(self, jobs=None, *, slots=0, max_particles=0, max_cells=0, dim=0, precision=PREC_F32,
                  stage_capacity=0, stream=None, torch_memory=True):
         import torch
         lib = load()
@@ -538,7 +538,7 @@ class Batch:
                 self._meta[i] = (int(j.dim), int(j.radii.n))
         else:
             _check(lib.srm_batch_create_slots(ctypes.byref(self.h), int(slots), int(max_particles),
-                                              int(max_cells), int(precision), int(stage_capacity),
+                                              int(max_cells), int(dim), int(precision), int(stage_capacity),
                                               c_void_p(self.stream),
                                               ctypes.byref(alloc) if alloc is not None else None))
 

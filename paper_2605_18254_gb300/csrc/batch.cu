@@ -65,10 +65,11 @@ srm_status srm_batch_create(srm_batch **out, const srm_job *jobs, int32_t n_jobs
 }
 
 srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_particles, int64_t max_cells,
-                                  int32_t precision, int32_t stage_capacity, void *cuda_stream,
+                                  int32_t dim, int32_t precision, int32_t stage_capacity, void *cuda_stream,
                                   const srm_allocator *alloc)
 {
     if (!out || n_slots < 1 || max_particles < 1 || max_cells < 27) return fail(SRM_E_ARG, "bad argument");
+    if (dim != 0 && dim != 2 && dim != 3) return fail(SRM_E_ARG, "dim must be 0, 2 or 3");
     if (precision != SRM_PREC_F32 && precision != SRM_PREC_F64) return fail(SRM_E_ARG, "precision must be 32 or 64");
     if (max_particles > 0x7fffffffLL || max_cells > 0x7ffffff0LL) return fail(SRM_E_ARG, "capacity too large");
     *out = nullptr;
@@ -81,7 +82,9 @@ srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_
     srm_status st = SRM_OK;
     for (int32_t i = 0; i < n_slots && st == SRM_OK; i++) {
         Member *mb = new Member();
-        mb->any_dim = true;  // a slot may take 2D or 3D jobs: launch both sweeps
+        mb->any_dim = dim == 0;  // a slot for either dimension: both sweeps are launched
+        mb->dim = dim == 0 ? 3 : dim;
+        mb->slot_dim = dim;
         g.m.push_back(mb);
         st = member_alloc(g, *mb, max_particles, max_cells, max_cells / 9);
     }
@@ -117,6 +120,7 @@ srm_status srm_batch_admit(srm_batch *b, int32_t slot, const srm_job *job)
     Prep q;
     if ((st = job_prepare(job, q)) != SRM_OK) return st;
     if (!member_fits(mb, q)) return fail(SRM_E_ARG, "job exceeds the capacity of the slot");
+    if (mb.slot_dim != 0 && q.dim != mb.slot_dim) return fail(SRM_E_ARG, "job dimension differs from the slot's");
     return member_load(g, mb, q);
 }
 

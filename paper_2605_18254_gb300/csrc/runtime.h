@@ -44,6 +44,7 @@ struct Member {
     RveDev *d = nullptr;  // device state
     int64_t n_cap = 0, ncells_cap = 0, nsub_cap = 0;
     bool loaded = false, harvested = false, any_dim = false;  // any_dim: a slot for 2D or 3D jobs
+    int slot_dim = 0;  // dimension a serving slot accepts (0: either)
     int dim = 3;
     int64_t n = 0;
     double S0 = 0.0, V = 1.0, phi_t = 0.0, lam_min = 0.0;

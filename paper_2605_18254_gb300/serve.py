@@ -1,7 +1,8 @@
 """Continuous-batching request loop for RVE generation.
 
 Jobs (one RVE each) arrive over time.  The server keeps a few pools of
-slots; a pool is one batch (srm_batch_create_slots) on its own CUDA stream,
+slots (for one dimension, or either); a pool is one batch
+(srm_batch_create_slots) on its own CUDA stream,
 all of whose slots are advanced by the same kernel launches.  A job is
 admitted into a free slot of the first pool whose slot capacity (particles,
 finest-grid cells) fits it, as soon as such a slot is free -- while the jobs
@@ -46,6 +47,7 @@ class PoolSpec:
     max_particles: int
     max_cells: int
     stage_capacity: int = 0
+    dim: int = 0  # dimension the pool's slots accept (0: either; one sweep launch per super-step if 2 or 3)
 
 
 def slot_bytes(max_particles: int, max_cells: int) -> int:
@@ -62,7 +64,7 @@ class Server:
         if memory_budget is not None and need > memory_budget:
             raise ValueError(f"pools need {need} bytes of device memory, budget {memory_budget}")
         self.streams = [torch.cuda.Stream() for _ in self.specs]
-        self.pools = [Batch(slots=p.slots, max_particles=p.max_particles, max_cells=p.max_cells,
+        self.pools = [Batch(slots=p.slots, max_particles=p.max_particles, max_cells=p.max_cells, dim=p.dim,
                             precision=precision, stage_capacity=p.stage_capacity,
                             stream=s.cuda_stream) for p, s in zip(self.specs, self.streams)]
         self.free = [list(range(p.slots)) for p in self.specs]
@@ -72,7 +74,8 @@ class Server:
 
     def _fits(self, k, req):
         p = self.specs[k]
-        return req.particles <= p.max_particles and req.cells <= p.max_cells
+        return (req.particles <= p.max_particles and req.cells <= p.max_cells
+                and (p.dim == 0 or p.dim == int(req.job[0].dim)))
 
     def run(self, requests, time_limit=3600.0):
         """Serves requests (sorted by arrival time) to completion."""

@@ -148,3 +148,25 @@ def test_launch_shape_does_not_change_results(precision):
         np.testing.assert_array_equal(xb, x)
         assert b.state(i)["sweeps"] == st["sweeps"]
     b.close()
+
+
+def test_slots_of_one_dimension():
+    """A pool of 2D slots (one sweep launch per super-step) runs 2D jobs as
+    alone and rejects a 3D job."""
+    ws = [w for w in mixed_workloads() if w.dim == 2]
+    b = srm.Batch(slots=2, max_particles=4000, max_cells=400000, dim=2, precision=32)
+    w3 = [w for w in mixed_workloads() if w.dim == 3][0]
+    with pytest.raises(srm.SrmError) as e:
+        b.admit(0, job_of(w3, 32))
+    assert e.value.status == 1
+    for s, w in enumerate(ws):
+        b.admit(s, job_of(w, 32))
+    steps, finished = 0, set()
+    while len(finished) < len(ws) and steps < 20000:
+        b.advance(8)
+        finished.update(b.poll())
+        steps += 1
+    for s, w in enumerate(ws):
+        x, r, _ = alone(w, 32)
+        np.testing.assert_array_equal(b.positions(s)[0], x)
+    b.close()
