@@ -109,10 +109,17 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Position of the k-th (from 0) set bit of m; m has more than k set bits.
+// It is the largest p with popc(m & (2^p - 1)) <= k: a binary search over p,
+// five steps, the same for every lane.
 __device__ __forceinline__ int nth_set(unsigned m, int k)
 {
-    for (int i = 0; i < k; i++) m &= m - 1u;
-    return __ffs(m) - 1;
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int p = pos + step;
+        if (p <= 31 && __popc(m & ((1u << p) - 1u)) <= k) pos = p;
+    }
+    return pos;
 }
 
 // ---------------------------------------------------------------------------
@@ -121,8 +128,7 @@ __device__ __forceinline__ int nth_set(unsigned m, int k)
 // g0 + (t >> 1); lane l owns trials l and 32 + l.  Each round every lane
 // evaluates one candidate of a pending trial -- when fewer than 32 trials are
 // pending, several lanes take consecutive candidates of one trial -- and a
-// trial takes its first accepted candidate, which is the candidate unit_dir
-// (unit_dir_f32 in the FP32 form) accepts, normalised the same way.
+// trial takes its first accepted candidate (the direction of the draw).
 // ---------------------------------------------------------------------------
 template <int DIM, bool F32>
 __device__ __forceinline__ void draw_warp(const RveDev *st, const Slot &d, int64_t g0, int np_w)
@@ -142,7 +148,14 @@ __device__ __forceinline__ void draw_warp(const RveDev *st, const Slot &d, int64
         if (np == 0) break;
         // the trial this lane evaluates (rank k among the pending ones) and
         // its candidate index
-        const int k = lane % np, rep = lane / np;
+        // lane = rep np + k; with np <= 31 the quotient of (lane + 1/2) / np
+        // is never within 1/64 of an integer, so the binary32 value truncates
+        // to it exactly
+        int k = lane, rep = 0;
+        if (np < 32) {
+            rep = (int)(((float)lane + 0.5f) / (float)np);
+            k = lane - rep * np;
+        }
         const int tr = k < c0 ? nth_set(m0, k) : 32 + nth_set(m1, k - c0);
         const int nmA = __shfl_sync(0xffffffffu, nm[0], tr & 31), nmB = __shfl_sync(0xffffffffu, nm[1], tr & 31);
         const int mc = (tr < 32 ? nmA : nmB) + rep;
