@@ -46,7 +46,7 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             sig = {
-                "orc_philox4x64_10": ([P(_u64), P(_u64), P(_u64)], None),
+                "orc_philox4x32_10": ([P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)], None),
                 "orc_unit_dir": ([_u64, _u64, _u64, _u64, _int, P(_d)], _int),
                 "orc_wrap": ([_d, _d], _d),
                 "orc_grid": ([_int, P(_d), _d, _d, _d, P(_i64), P(_d)], None),
@@ -91,12 +91,12 @@ def _box3(box, dim):
     return L
 
 
-def philox4x64_10(ctr, key) -> np.ndarray:
-    c = np.ascontiguousarray(ctr, dtype=np.uint64)
-    k = np.ascontiguousarray(key, dtype=np.uint64)
-    out = np.zeros(4, dtype=np.uint64)
-    _load().orc_philox4x64_10(c.ctypes.data_as(P(_u64)), k.ctypes.data_as(P(_u64)),
-                              out.ctypes.data_as(P(_u64)))
+def philox4x32_10(ctr, key) -> np.ndarray:
+    u32 = ctypes.c_uint32
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox4x32_10(c.ctypes.data_as(P(u32)), k.ctypes.data_as(P(u32)), out.ctypes.data_as(P(u32)))
     return out
 
 
@@ -179,6 +179,8 @@ class System:
 
     def __init__(self, dim, box, x, r, lam=1.0, lam_t=None, target_phi=None, c_w=0.01,
                  c_m=0.01, N_k=10, N_l=10, N_shake=10, seed=1, sweep=0, literal=False):
+        if not 1 <= N_l < (1 << 16):
+            raise ValueError("N_l must be in [1, 65535] (the try index takes 16 counter bits)")
         lib = _load()
         self.dim = int(dim)
         self.box = _box3(box, dim)

@@ -24,12 +24,12 @@
  *   - touching counts as a collision: sqrt(dx^2+dy^2[+dz^2]) <= R_q + R_t
  *     (Alg 5);
  *   - "unit random vector" is a uniform direction: rejection sampling from
- *     the cube [-1,1)^d on a 2^-53 lattice, then division by the norm, with
- *     the draws taken from Philox4x64-10 keyed by (seed, move tag) at counter
- *     (particle id, sweep index, try, candidate) (Alg 3);
+ *     the cube [-1,1)^d on a 2^-31 lattice, then division by the norm, with
+ *     the draws taken from Philox4x32-10 keyed by the seed at counter
+ *     (particle id, sweep index, try and candidate) (Alg 3);
  *   - the shake step runs N_shake sweeps of Alg 3 on the unswollen P, each
- *     preceded by a fresh binning, on the grid of the iteration (Alg 1 lines
- *     19-22, Section 2 step d);
+ *     preceded by a fresh binning, on the grid of the iteration (Alg 1,
+ *     Section 2 step d);
  *   - the order of Alg 3's "for each particle" is the canonical coloured
  *     order: for colour chi = sum_a (c_a mod 3) 3^a ascending, for cells of
  *     that colour in lexicographic order, particles of the cell by ascending
@@ -40,61 +40,57 @@
 #include <stdlib.h>
 #include <string.h>
 
-typedef unsigned __int128 u128;
-
 /* ---------------------------------------------------------------------------
- * Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
- * easy as 1, 2, 3", SC'11, Section 4.2): ten rounds of two 64x64->128 bit
- * multiplies, with the key advanced by the two Weyl constants between rounds.
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11, Section 4.2): ten rounds of two 32x32->64 bit
+ * multiplies (high halves xored with the other counter words and the key,
+ * low halves kept), the key advanced by the two Weyl constants between
+ * rounds.
  * ------------------------------------------------------------------------- */
-#define PHILOX_M0 0xD2E7470EE14C6C93ULL
-#define PHILOX_M1 0xCA5A826395121157ULL
-#define PHILOX_W0 0x9E3779B97F4A7C15ULL
-#define PHILOX_W1 0xBB67AE8584CAA73BULL
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
 
-void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
 {
-    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
-    uint64_t k0 = key[0], k1 = key[1];
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
     for (int round = 0; round < 10; round++) {
         if (round > 0) {
             k0 += PHILOX_W0;
             k1 += PHILOX_W1;
         }
-        u128 p0 = (u128)PHILOX_M0 * (u128)c0;
-        u128 p1 = (u128)PHILOX_M1 * (u128)c2;
-        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
-        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
-        uint64_t n0 = hi1 ^ c1 ^ k0;
-        uint64_t n1 = lo1;
-        uint64_t n2 = hi0 ^ c3 ^ k1;
-        uint64_t n3 = lo0;
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        const uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
         c0 = n0; c1 = n1; c2 = n2; c3 = n3;
     }
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Stream tag of the migration draws ("SRM-MOVE" in ASCII). */
-#define ORC_TAG_MOVE 0x53524D2D4D4F5645ULL
 #define ORC_MAX_CAND 32
 
-/* Uniform direction on the unit circle / sphere (Alg 3).  Candidate m
- * takes one Philox block at counter (pid, sweep, try, m); coordinate a is
- * ((word_a >> 10) - 2^53) * 2^-53, a point of the cube [-1,1) on a 2^-53
- * lattice, exact in binary64.  The first candidate with 0 < |v|^2 <= 1 is
- * normalised by dividing each coordinate by sqrt(|v|^2).  After 32 rejected
- * candidates (probability < 1e-10) the direction is the first axis.
+/* Uniform direction on the unit circle / sphere (Alg 3).  Candidate m of
+ * try l takes one Philox block at counter (pid, sweep mod 2^32, l + 2^16 m,
+ * sweep div 2^32) with key (seed mod 2^32, seed div 2^32); coordinate a is
+ * (word_a - 2^31) * 2^-31, a point of the cube [-1,1) on a 2^-31 lattice,
+ * exact in binary64.  The first candidate with 0 < |v|^2 <= 1 is normalised
+ * by dividing each coordinate by sqrt(|v|^2).  After 32 rejected candidates
+ * (probability < 1e-10) the direction is the first axis.  l < 2^16.
  * Returns the index of the accepted candidate. */
 int orc_unit_dir(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, int dim, double u[3])
 {
-    uint64_t key[2] = {seed, ORC_TAG_MOVE};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int m = 0; m < ORC_MAX_CAND; m++) {
-        uint64_t ctr[4] = {pid, sweep, l, (uint64_t)m};
-        uint64_t w[4];
-        orc_philox4x64_10(ctr, key, w);
+        const uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)sweep, (uint32_t)(l + ((uint64_t)m << 16)),
+                                 (uint32_t)(sweep >> 32)};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
         double v[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < dim; a++)
-            v[a] = (double)((int64_t)(w[a] >> 10) - (int64_t)(1ULL << 53)) * 0x1p-53;
+        for (int a = 0; a < dim; a++) v[a] = (double)((int64_t)w[a] - (int64_t)2147483648LL) * 0x1p-31;
         double s = v[0] * v[0] + v[1] * v[1];
         if (dim == 3) s = s + v[2] * v[2];
         if (s > 0.0 && s <= 1.0) {

@@ -1,69 +1,77 @@
 """Pins of the reference's random-number layer against things other than itself.
 
-* Philox4x64-10 against numpy's independent implementation of the same
-  generator (numpy.random.Philox, which advances the counter by one before
-  each block).
+* Philox4x32-10 against the known-answer vectors published with the
+  generator (tests/golden/philox4x32_10_kat.txt).
 * The unit-vector sampler (Algorithm 3, read as a uniform direction)
   against its definition: unit norm, the first accepted lattice point of the
-  cube drawn from numpy's Philox stream, and uniformity of the angle (2D) and
-  of cos(theta) and the azimuth (3D).
+  cube drawn from the (pinned) Philox blocks at the documented counters, and
+  uniformity of the angle (2D) and of cos(theta) and the azimuth (3D).
 """
+import os
+
 import numpy as np
 import pytest
 from scipy import stats
 
 import oracle
 
-MASK = (1 << 64) - 1
-TAG_MOVE = 0x53524D2D4D4F5645
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
 
 
-def numpy_philox(ctr, key):
-    c = 0
-    for i, w in enumerate(ctr):
-        c |= int(w) << (64 * i)
-    c = (c - 1) & ((1 << 256) - 1)
-    bg = np.random.Philox(counter=np.array([(c >> (64 * i)) & MASK for i in range(4)],
-                                           dtype=np.uint64),
-                          key=np.array(key, dtype=np.uint64))
-    return bg.random_raw(4)
+def kat_vectors():
+    out = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out.append((w[0:4], w[4:6], w[6:10]))
+    return out
 
 
-def test_philox_matches_numpy():
-    rng = np.random.default_rng(12345)
-    for _ in range(300):
-        ctr = [int(x) for x in rng.integers(0, 2**64, size=4, dtype=np.uint64)]
-        key = [int(x) for x in rng.integers(0, 2**64, size=2, dtype=np.uint64)]
-        np.testing.assert_array_equal(oracle.philox4x64_10(ctr, key), numpy_philox(ctr, key))
-    # the counter layouts the method uses: small ids, sweep, try, candidate
-    for pid in (0, 1, 999, 2**32 + 5):
-        for sweep in (0, 7):
-            ctr = [pid, sweep, 3, 1]
-            key = [42, TAG_MOVE]
-            np.testing.assert_array_equal(oracle.philox4x64_10(ctr, key), numpy_philox(ctr, key))
+def test_philox_known_answers():
+    vs = kat_vectors()
+    assert len(vs) == 3
+    for ctr, key, want in vs:
+        np.testing.assert_array_equal(oracle.philox4x32_10(ctr, key), np.array(want, dtype=np.uint32))
+
+
+def test_philox_counter_words_matter():
+    base = oracle.philox4x32_10([1, 2, 3, 4], [5, 6])
+    for i in range(4):
+        c = [1, 2, 3, 4]
+        c[i] ^= 1
+        assert not np.array_equal(oracle.philox4x32_10(c, [5, 6]), base)
+    for i in range(2):
+        k = [5, 6]
+        k[i] ^= 1
+        assert not np.array_equal(oracle.philox4x32_10([1, 2, 3, 4], k), base)
+
+
+def _block(seed, sweep, pid, l, m):
+    ctr = [pid & 0xFFFFFFFF, sweep & 0xFFFFFFFF, (l + (m << 16)) & 0xFFFFFFFF, (sweep >> 32) & 0xFFFFFFFF]
+    return oracle.philox4x32_10(ctr, [seed & 0xFFFFFFFF, seed >> 32])
 
 
 def _lattice(words, dim):
-    return np.array([float((int(w) >> 10) - (1 << 53)) * 2.0**-53 for w in words[:dim]])
+    return np.array([float(int(w) - (1 << 31)) * 2.0**-31 for w in words[:dim]])
 
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_unit_dir_is_first_accepted_lattice_point(dim):
-    seed = 7
-    for pid in range(60):
-        for l in range(3):
-            u, m = oracle.unit_dir(seed, 5, pid, l, dim)
-            # candidates before m fall outside the unit ball, candidate m inside
-            for mm in range(m + 1):
-                v = _lattice(numpy_philox([pid, 5, l, mm], [seed, TAG_MOVE]), dim)
-                s = float(np.sum(v * v))
-                if mm < m:
-                    assert not (0.0 < s <= 1.0)
-                else:
-                    assert 0.0 < s <= 1.0
-                    # direction of v, unit length
-                    np.testing.assert_allclose(u, v / np.sqrt(s), rtol=0, atol=4e-16)
-            assert abs(np.linalg.norm(u) - 1.0) < 4e-16
+    for seed, sweep in ((7, 5), (2**40 + 3, 2**33 + 9)):
+        for pid in range(60):
+            for l in range(3):
+                u, m = oracle.unit_dir(seed, sweep, pid, l, dim)
+                # candidates before m fall outside the unit ball, candidate m inside
+                for mm in range(m + 1):
+                    v = _lattice(_block(seed, sweep, pid, l, mm), dim)
+                    s = float(np.sum(v * v))
+                    if mm < m:
+                        assert not (0.0 < s <= 1.0)
+                    else:
+                        assert 0.0 < s <= 1.0
+                        np.testing.assert_allclose(u, v / np.sqrt(s), rtol=0, atol=4e-16)
+                assert abs(np.linalg.norm(u) - 1.0) < 4e-16
 
 
 def _sample(dim, n, seed=11):
@@ -89,6 +97,6 @@ def test_unit_dir_uniform_3d():
 
 def test_streams_distinct():
     a = oracle.unit_dir(1, 0, 0, 0, 3)[0]
-    for args in [(2, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0), (1, 0, 0, 1)]:
+    for args in [(2, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0), (1, 0, 0, 1), (2**32 + 1, 0, 0, 0), (1, 2**32, 0, 0)]:
         b = oracle.unit_dir(*args, 3)[0]
         assert not np.array_equal(a, b)
