@@ -75,7 +75,7 @@ typedef struct srm_params {
     double c_w;              /* swelling rate: lambda <- lambda (1 + c_w)        */
     double c_m;              /* migration step length (absolute)                 */
     int32_t N_k;             /* sweeps tried per iteration before the shake      */
-    int32_t N_l;             /* trial moves per particle and sweep               */
+    int32_t N_l;             /* trial moves per particle and sweep, 1..65535     */
     int32_t N_shake;         /* sweeps of the shake step                          */
     int32_t precision;       /* srm_precision                                    */
     int32_t init;            /* srm_init_kind                                    */
@@ -117,7 +117,7 @@ typedef struct srm_rve srm_rve;
  * The target scale is lambda_t = (phi_t prod L / S0)^(1/d), S0 = sum of the
  * base disk areas or sphere volumes (Algorithm 1).
  * Rejects (SRM_E_ARG): dim not 2 or 3, n < 1, L <= 0, phi_t outside (0, 1),
- * c_m <= 0, N_k, N_l < 1, N_shake < 0, and boxes narrower than three cells of
+ * c_m <= 0, N_k, N_l outside 1..65535, N_shake < 0, and boxes narrower than three cells of
  * the final cell size 2.5 lambda_t max r + c_m on some axis (the minimum-image
  * search of Algorithm 5 needs them).  The starting positions are uploaded;
  * device state is created.  Returns SRM_E_INIT if RSA fails. */

@@ -138,7 +138,7 @@ __device__ __forceinline__ void draw_warp(const RveDev *st, const Slot &d, int64
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     const uint64_t seed = st->seed, sweep = st->sweep;
-    const uint64_t pidv = lane < np_w ? (uint64_t)d.pid[g0 + lane] : 0ull;
+    const uint32_t pidv = lane < np_w ? d.pid[g0 + lane] : 0u;
     int nm[2] = {0, 0};
     bool pend[2] = {(lane >> 1) < np_w, ((32 + lane) >> 1) < np_w};
     DT res[2][3] = {{(DT)1, (DT)0, (DT)0}, {(DT)1, (DT)0, (DT)0}};
@@ -159,7 +159,7 @@ __device__ __forceinline__ void draw_warp(const RveDev *st, const Slot &d, int64
         const int tr = k < c0 ? nth_set(m0, k) : 32 + nth_set(m1, k - c0);
         const int nmA = __shfl_sync(0xffffffffu, nm[0], tr & 31), nmB = __shfl_sync(0xffffffffu, nm[1], tr & 31);
         const int mc = (tr < 32 ? nmA : nmB) + rep;
-        const uint64_t pidt = __shfl_sync(0xffffffffu, pidv, tr >> 1);
+        const uint64_t pidt = __shfl_sync(0xffffffffu, pidv, tr >> 1);  // 32-bit id
         DT v[3] = {(DT)0, (DT)0, (DT)0}, s = (DT)0;
         bool ok = false;
         if (mc < MAX_CAND) {

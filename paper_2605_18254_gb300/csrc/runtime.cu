@@ -160,6 +160,7 @@ srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, dou
     if (!(p.c_m > 0.0)) return fail(SRM_E_ARG, "c_m must be > 0");
     if (!(p.c_w >= 0.0)) return fail(SRM_E_ARG, "c_w must be >= 0");
     if (p.N_k < 1 || p.N_l < 1 || p.N_shake < 0) return fail(SRM_E_ARG, "N_k, N_l >= 1, N_shake >= 0");
+    if (p.N_l > 65535) return fail(SRM_E_ARG, "N_l must be <= 65535 (the try index takes 16 counter bits)");
     if (p.precision != SRM_PREC_F64 && p.precision != SRM_PREC_F32)
         return fail(SRM_E_ARG, "precision must be 32 or 64");
     if (p.precision == SRM_PREC_F32 && !(p.guard > 0.0 && p.guard < 1e-2))

@@ -174,17 +174,17 @@ __device__ __forceinline__ bool plan_block(const int32_t *off, int B, int &r)
 }
 
 // ---------------------------------------------------------------------------
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
-// 64x64 -> 128-bit products; the key is advanced by the Weyl constants
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products (high halves xored with the other counter words
+// and the key, low halves kept); the key is advanced by the Weyl constants
 // between rounds.
 // ---------------------------------------------------------------------------
-// One round: two 64x64 -> 128-bit products, words permuted and keyed.
-__device__ __forceinline__ void philox_round(uint64_t c[4], uint64_t k0, uint64_t k1)
+__device__ __forceinline__ void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1)
 {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-    const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
-    const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
-    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
     c[0] = n0;
     c[1] = lo1;
     c[2] = n2;
@@ -194,9 +194,9 @@ __device__ __forceinline__ void philox_round(uint64_t c[4], uint64_t k0, uint64_
 // COMPACT keeps the ten rounds as a loop: fewer registers, for the rare
 // draws inside the sweep (whose register budget sets its occupancy).
 template <bool COMPACT = false>
-__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1)
+__device__ __forceinline__ void philox4x32(uint32_t c[4], uint32_t k0, uint32_t k1)
 {
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
     if constexpr (COMPACT) {
 #pragma unroll 1
         for (int r = 0; r < 10; r++) {
@@ -214,36 +214,48 @@ __device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t 
     }
 }
 
-constexpr uint64_t TAG_MOVE = 0x53524D2D4D4F5645ULL;  // "SRM-MOVE"
+// Counter of candidate m of try l of particle pid in sweep `sweep`, key = the
+// 64-bit seed (l < 2^16, m < 2^16).
+__device__ __forceinline__ void draw_block(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint64_t m,
+                                           uint32_t c[4], uint32_t &k0, uint32_t &k1)
+{
+    c[0] = (uint32_t)pid;
+    c[1] = (uint32_t)sweep;
+    c[2] = (uint32_t)(l + (m << 16));
+    c[3] = (uint32_t)(sweep >> 32);
+    k0 = (uint32_t)seed;
+    k1 = (uint32_t)(seed >> 32);
+}
+
 constexpr int MAX_CAND = 32;
 
 // Uniform direction in DIM dimensions for (seed, sweep, particle, try l):
-// candidate m is the Philox block at counter (pid, sweep, l, m), mapped to
-// the lattice point ((w_a >> 10) - 2^53) 2^-53 of [-1, 1)^DIM; the first
-// candidate with 0 < |v|^2 <= 1 is divided by its norm, and after MAX_CAND
-// rejected candidates the direction is e_0.  cand_f64 evaluates one
-// candidate in binary64 (exact or correctly rounded operations only; the
-// direction is v / sqrt(|v|^2), correctly rounded).  cand_f32 is the same
-// draw for the FP32 form, without binary64 arithmetic in the common case
-// (binary64 runs at 1/64 of the binary32 rate on this GPU): coordinate a is
-// the top 24 bits of the Philox word, v_a = ((w_a >> 40) - 2^23) 2^-23, the
-// binary64 lattice point truncated by less than 2^-23, so |v|^2 in binary32
-// is within 1e-6 of the binary64 value and the acceptance test is decided in
-// binary32 outside a band of +-2e-6 around 1 (and 0) and by the binary64
-// computation inside it -- the accepted candidate is always the one the
-// binary64 draw accepts.  Its direction is v rsqrt(|v|^2) in binary32, with
-// |v|^2 summed by explicit fused multiply-adds (the same rounding wherever
-// the compiler inlines it).
+// candidate m is the Philox block of draw_block, mapped to the lattice point
+// (w_a - 2^31) 2^-31 of [-1, 1)^DIM; the first candidate with 0 < |v|^2 <= 1
+// is divided by its norm, and after MAX_CAND rejected candidates the
+// direction is e_0.  cand_f64 evaluates one candidate in binary64 (exact or
+// correctly rounded operations only; the direction is v / sqrt(|v|^2),
+// correctly rounded).  cand_f32 is the same draw for the FP32 form, without
+// binary64 arithmetic in the common case (binary64 runs at 1/64 of the
+// binary32 rate on this GPU): coordinate a is the top 24 bits of the Philox
+// word, v_a = ((w_a >> 8) - 2^23) 2^-23, the binary64 lattice point truncated
+// by less than 2^-23, so |v|^2 in binary32 is within 1e-6 of the binary64
+// value and the acceptance test is decided in binary32 outside a band of
+// +-2e-6 around 1 (and 0) and by the binary64 computation inside it -- the
+// accepted candidate is always the one the binary64 draw accepts.  Its
+// direction is v rsqrt(|v|^2) in binary32, with |v|^2 summed by explicit
+// fused multiply-adds (the same rounding wherever the compiler inlines it).
 
 template <int DIM, bool COMPACT = false>
 __device__ __forceinline__ bool cand_f64(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint64_t m,
                                          double v[3], double &s)
 {
-    uint64_t c[4] = {pid, sweep, l, m};
-    philox4x64<COMPACT>(c, seed, TAG_MOVE);
+    uint32_t c[4], k0, k1;
+    draw_block(seed, sweep, pid, l, m, c, k0, k1);
+    philox4x32<COMPACT>(c, k0, k1);
     v[2] = 0.0;
 #pragma unroll
-    for (int a = 0; a < DIM; a++) v[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
+    for (int a = 0; a < DIM; a++) v[a] = __dmul_rn(__ll2double_rn((long long)c[a] - 2147483648LL), 0x1p-31);
     s = __dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1]));
     if (DIM == 3) s = __dadd_rn(s, __dmul_rn(v[2], v[2]));
     return s > 0.0 && s <= 1.0;
@@ -253,18 +265,19 @@ template <int DIM, bool COMPACT = false>
 __device__ __forceinline__ bool cand_f32(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint64_t m,
                                          float v[3], float &s)
 {
-    uint64_t c[4] = {pid, sweep, l, m};
-    philox4x64<COMPACT>(c, seed, TAG_MOVE);
+    uint32_t c[4], k0, k1;
+    draw_block(seed, sweep, pid, l, m, c, k0, k1);
+    philox4x32<COMPACT>(c, k0, k1);
     v[2] = 0.f;
 #pragma unroll
-    for (int a = 0; a < DIM; a++) v[a] = (float)((int32_t)(c[a] >> 40) - (1 << 23)) * 0x1p-23f;
+    for (int a = 0; a < DIM; a++) v[a] = (float)((int32_t)(c[a] >> 8) - (1 << 23)) * 0x1p-23f;
     s = __fmaf_rn(v[1], v[1], __fmul_rn(v[0], v[0]));
     if (DIM == 3) s = __fmaf_rn(v[2], v[2], s);
     if (s > 1.0f + 2e-6f) return false;
     if (s < 1.0f - 2e-6f && s > 2e-6f) return true;
     double vd[3];
 #pragma unroll
-    for (int a = 0; a < DIM; a++) vd[a] = __dmul_rn(__ll2double_rn((long long)(c[a] >> 10) - (1LL << 53)), 0x1p-53);
+    for (int a = 0; a < DIM; a++) vd[a] = __dmul_rn(__ll2double_rn((long long)c[a] - 2147483648LL), 0x1p-31);
     double sd = __dadd_rn(__dmul_rn(vd[0], vd[0]), __dmul_rn(vd[1], vd[1]));
     if (DIM == 3) sd = __dadd_rn(sd, __dmul_rn(vd[2], vd[2]));
     const bool ok = sd > 0.0 && sd <= 1.0;

@@ -37,3 +37,17 @@ def test_iteration_cap_reports_not_converged():
     info = g.run_to_target()
     assert info["converged"]
     g.close()
+
+
+def test_try_count_beyond_counter_field_rejected():
+    """The try index l takes 16 bits of the generator's counter word, so
+    N_l above 65535 is refused at initialisation with SRM_E_ARG; 65535 is
+    accepted."""
+    w = srm_inputs._mono("t", 2, 500, 0.3, 0.1, 5)
+    with pytest.raises(srm.SrmError) as e:
+        srm.Rve(w.dim, w.box, w.radii, w.target_phi, w.seed, init="explicit", positions=w.x, c_m=w.c_m,
+                N_l=65536)
+    assert e.value.status == 1
+    g = srm.Rve(w.dim, w.box, w.radii, w.target_phi, w.seed, init="explicit", positions=w.x, c_m=w.c_m,
+                N_l=65535)
+    g.close()
