@@ -19,6 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "srm_oracle.c")
 _SRC_A = os.path.join(_HERE, "srm_analysis.c")
+_SRC_P = os.path.join(_HERE, "srm_platelet.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libsrm_oracle.so")
 _lock = threading.Lock()
@@ -31,7 +32,7 @@ _d, _i64, _u64, _int = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.
 def build(force: bool = False) -> str:
     """Compile the reference with plain gcc, no FMA contraction, no fast-math."""
     os.makedirs(_BUILD, exist_ok=True)
-    srcs = [_SRC, _SRC_A]
+    srcs = [_SRC, _SRC_A, _SRC_P]
     if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in srcs):
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
@@ -72,6 +73,24 @@ def _load():
                 "orc_nn": ([_int, P(_d), _i64, P(_d), P(_d), P(_d), P(_i64), P(_d)], None),
                 "orc_rdf": ([_int, P(_d), _i64, P(_d), _d, _int, P(_i64), P(_d)], _i64),
                 "orc_voronoi_lvf": ([_int, P(_d), _i64, P(_d), P(_d), P(ctypes.c_int32), P(_i64), P(_d)], None),
+                "orc_unit_dir_stream": ([_u64, _u64, _u64, _u64, _int, _int, P(_d)], _int),
+                "orc_plt_basis": ([P(_d), P(_d), P(_d)], None),
+                "orc_plt_point_disk": ([P(_d), P(_d), P(_d), _d], _d),
+                "orc_plt_rim_near_disk": ([P(_d), P(_d), P(_d), _d, P(_d), P(_d), _d, _d, _d, P(_int)], _int),
+                "orc_plt_collide": ([P(_d), P(_d), P(_d), _d, _d], _int),
+                "orc_plt_trial": ([_u64, _u64, _u64, _u64, P(_d), _d, _d, P(_d), P(_d), P(_d), P(_d)], None),
+                "orc_plt_create": ([P(_d), _i64, P(_d), P(_d), _d, _d, _d, _d, _d, _d, _d, _int, _int, _int,
+                                    _u64, _u64], ctypes.c_void_p),
+                "orc_plt_destroy": ([ctypes.c_void_p], None),
+                "orc_plt_get": ([ctypes.c_void_p, P(_d), P(_d)], None),
+                "orc_plt_lambda": ([ctypes.c_void_p], _d),
+                "orc_plt_sweep_counter": ([ctypes.c_void_p], _u64),
+                "orc_plt_counters": ([ctypes.c_void_p, P(_i64)], None),
+                "orc_plt_sweep": ([ctypes.c_void_p], _i64),
+                "orc_plt_check": ([ctypes.c_void_p, P(ctypes.c_uint8)], _i64),
+                "orc_plt_iterate": ([ctypes.c_void_p, P(_i64)], _int),
+                "orc_plt_run": ([ctypes.c_void_p, _i64], _i64),
+                "orc_plt_pairs_brute": ([P(_d), _i64, P(_d), P(_d), _d, _d, P(_i64), _i64], _i64),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -103,6 +122,12 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 def unit_dir(seed: int, sweep: int, pid: int, l: int, dim: int):
     u = np.zeros(3)
     m = _load().orc_unit_dir(seed, sweep, pid, l, dim, _dp(u))
+    return u[:dim], m
+
+
+def unit_dir_stream(seed: int, sweep: int, pid: int, l: int, dim: int, stream: int):
+    u = np.zeros(3)
+    m = _load().orc_unit_dir_stream(seed, sweep, pid, l, dim, stream, _dp(u))
     return u[:dim], m
 
 
@@ -276,3 +301,124 @@ class System:
 
     def certify(self):
         return certify(self.dim, self.box[:self.dim], self.x, self.radii())
+
+
+# ---------------------------------------------------------------------------
+# Platelets (spherodisks, Section 3.3): see the header of srm_platelet.c.
+# ---------------------------------------------------------------------------
+def _v3(v):
+    return np.ascontiguousarray(v, dtype=np.float64).reshape(3)
+
+
+def plt_basis(n):
+    e1, e2 = np.zeros(3), np.zeros(3)
+    _load().orc_plt_basis(_dp(_v3(n)), _dp(e1), _dp(e2))
+    return e1, e2
+
+
+def plt_point_disk(p, cd, nd, b) -> float:
+    return _load().orc_plt_point_disk(_dp(_v3(p)), _dp(_v3(cd)), _dp(_v3(nd)), b)
+
+
+def plt_rim_near_disk(cc, n_c, a, cd, nd, b, thr):
+    """(decision, evaluations) for the rim of the disk (cc, n_c, a) against
+    the disk (cd, nd, b) at distance thr."""
+    e1, e2 = plt_basis(n_c)
+    c = float(np.dot(_v3(n_c), _v3(nd)))
+    sn = float(np.sqrt(max(0.0, 1.0 - c * c)))
+    ev = _int(0)
+    r = _load().orc_plt_rim_near_disk(_dp(_v3(cc)), _dp(e1), _dp(e2), a, _dp(_v3(cd)), _dp(_v3(nd)), b, sn, thr,
+                                      ctypes.byref(ev))
+    return int(r), int(ev.value)
+
+
+def plt_collide(dj, ni, nj, a, t) -> int:
+    return int(_load().orc_plt_collide(_dp(_v3(dj)), _dp(_v3(ni)), _dp(_v3(nj)), a, t))
+
+
+def plt_trial(seed, sweep, pid, l, box, c_m, c_r, x0, u0):
+    q, u = np.zeros(3), np.zeros(3)
+    _load().orc_plt_trial(seed, sweep, pid, l, _dp(_v3(box)), c_m, c_r, _dp(_v3(x0)), _dp(_v3(u0)), _dp(q), _dp(u))
+    return q, u
+
+
+def plt_pairs_brute(box, X, U, a, t, cap: int = 1 << 16):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    ij = np.zeros((cap, 2), dtype=np.int64)
+    cnt = _load().orc_plt_pairs_brute(_dp(_v3(box)), X.shape[0], _dp(X), _dp(U), a, t, ij.ctypes.data_as(P(_i64)),
+                                      cap)
+    return ij[:min(cnt, cap)].copy(), int(cnt)
+
+
+def plt_lambda_for_density(box, n, a0, t0, rho) -> float:
+    """Scale at which n platelets of base diameter 2 (a0 + t0) reach the
+    number density rho = n D^3 / V of Eq. 1 (V the box volume)."""
+    V = float(box[0]) * float(box[1]) * float(box[2])
+    return (rho * V / n) ** (1.0 / 3.0) / (2.0 * (a0 + t0))
+
+
+class PlateletSystem:
+    """Platelets in the reference: centres X and unit normals U in id order,
+    base sizes (a0, t0), scale lambda, target scale, SRM parameters and the
+    rotation rate c_r."""
+
+    def __init__(self, box, x, u, a0, t0, lam=1.0, lam_t=None, c_w=0.01, c_m=0.01, c_r=0.0, N_k=10, N_l=10,
+                 N_shake=10, seed=1, sweep=0):
+        if not 1 <= N_l < (1 << 16):
+            raise ValueError("N_l must be in [1, 65535] (the try index takes 16 counter bits)")
+        if not 0.0 <= c_r < 1.0:
+            raise ValueError("c_r must be in [0, 1)")
+        lib = _load()
+        self.box = _v3(box)
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        self.n = x.size // 3
+        self.a0, self.t0 = float(a0), float(t0)
+        self._h = lib.orc_plt_create(_dp(self.box), self.n, _dp(x), _dp(u), a0, t0, lam,
+                                     lam if lam_t is None else lam_t, c_w, c_m, c_r, N_k, N_l, N_shake, seed, sweep)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_plt_destroy(h)
+            self._h = None
+
+    def state(self):
+        X, U = np.zeros(3 * self.n), np.zeros(3 * self.n)
+        _lib.orc_plt_get(self._h, _dp(X), _dp(U))
+        return X.reshape(-1, 3), U.reshape(-1, 3)
+
+    @property
+    def lam(self) -> float:
+        return _lib.orc_plt_lambda(self._h)
+
+    @property
+    def sweep_counter(self) -> int:
+        return int(_lib.orc_plt_sweep_counter(self._h))
+
+    def counters(self) -> dict:
+        c = np.zeros(5, dtype=np.int64)
+        _lib.orc_plt_counters(self._h, c.ctypes.data_as(P(_i64)))
+        return dict(iters=int(c[0]), accepted=int(c[1]), shaken=int(c[2]), moves_accepted=int(c[3]),
+                    sweeps=int(c[4]))
+
+    def sweep(self) -> int:
+        return int(_lib.orc_plt_sweep(self._h))
+
+    def check(self):
+        flags = np.zeros(self.n, dtype=np.uint8)
+        cnt = _lib.orc_plt_check(self._h, flags.ctypes.data_as(P(ctypes.c_uint8)))
+        return int(cnt), flags
+
+    def iterate(self):
+        info = np.zeros(3, dtype=np.int64)
+        acc = _lib.orc_plt_iterate(self._h, info.ctypes.data_as(P(_i64)))
+        return int(acc), dict(k_sweeps=int(info[0]), overlapping=int(info[1]), shake_sweeps=int(info[2]))
+
+    def run(self, max_iters: int = 1 << 40) -> int:
+        return int(_lib.orc_plt_run(self._h, max_iters))
+
+    def pairs_brute(self):
+        X, U = self.state()
+        return plt_pairs_brute(self.box, X, U, self.lam * self.a0, self.lam * self.t0)

@@ -73,6 +73,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 
 #define ORC_MAX_CAND 32
 
+int orc_unit_dir_stream(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, int dim, int stream, double u[3]);
+
 /* Uniform direction on the unit circle / sphere (Alg 3).  Candidate m of
  * try l takes one Philox block at counter (pid, sweep mod 2^32, l + 2^16 m,
  * sweep div 2^32) with key (seed mod 2^32, seed div 2^32); coordinate a is
@@ -83,10 +85,18 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * Returns the index of the accepted candidate. */
 int orc_unit_dir(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, int dim, double u[3])
 {
+    return orc_unit_dir_stream(seed, sweep, pid, l, dim, 0, u);
+}
+
+/* The same draw from stream 0 or 1: stream 1 sets the top bit of the fourth
+ * counter word (sweep < 2^63), giving a second independent direction per
+ * try (the rotation of a platelet, Section 3.3). */
+int orc_unit_dir_stream(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, int dim, int stream, double u[3])
+{
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint32_t hi = (uint32_t)(sweep >> 32) | (stream ? 0x80000000u : 0u);
     for (int m = 0; m < ORC_MAX_CAND; m++) {
-        const uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)sweep, (uint32_t)(l + ((uint64_t)m << 16)),
-                                 (uint32_t)(sweep >> 32)};
+        const uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)sweep, (uint32_t)(l + ((uint64_t)m << 16)), hi};
         uint32_t w[4];
         orc_philox4x32_10(ctr, key, w);
         double v[3] = {0.0, 0.0, 0.0};
