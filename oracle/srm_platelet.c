@@ -32,8 +32,9 @@
  * an end of one disk's chord on the line where the planes meet lies inside
  * the other disk).  So the platelets collide exactly when some rim point of
  * one disk lies within t_i + t_j of the other disk.  The rim is walked by
- * bisection.  The rim point moves at most V = 2 a / (1 + s^2) per unit of
- * the rational parameter s, and its distance to the other disk is
+ * bisection.  The rim point moves at most 2 a / (1 + s^2) <= a (2 - s^2)
+ * =: V per unit of the rational parameter s (1 / (1 + x) <= 1 - x / 2 on
+ * [0, 1]), and its distance to the other disk is
  * sqrt(h^2 + e^2) with h its height above that disk's plane and e the
  * excess of its projected distance from that disk's centre over the radius
  * (0 inside).  Along the rim h changes at most at V sin(theta) (the rim lies
@@ -41,7 +42,8 @@
  * at V, so over an interval of half-width r around its midpoint,
  * sqrt(max(0, |h| - V r sin)^2 + max(0, e - V r)^2) bounds the distance
  * from below.  Intervals whose bound is above the threshold are dropped, a
- * midpoint at or below it is a collision.  An interval still undecided at
+ * midpoint at or below it is a collision (both compared as squares: h^2 +
+ * e^2 <= thr^2).  An interval still undecided at
  * 2^-30 of the circle, or after 4096 evaluations of one rim, counts as a
  * collision (a near-contact the bisection cannot resolve is reported as
  * contact).  Cheap exact separations come first: the
@@ -120,8 +122,9 @@ static void rim_point(const double cc[3], const double e1[3], const double e2[3]
 {
     int first = tau < 2.0;
     double s = first ? tau - 1.0 : tau - 3.0;
-    double den = 1.0 + s * s;
-    double C = (1.0 - s * s) / den, S = (2.0 * s) / den;
+    double s2 = s * s;
+    double inv = 1.0 / (1.0 + s2);
+    double C = (1.0 - s2) * inv, S = (2.0 * s) * inv;
     double sa = first ? a : -a;
     for (int k = 0; k < 3; k++) p[k] = cc[k] + sa * (C * e1[k] + S * e2[k]);
 }
@@ -137,6 +140,7 @@ int orc_plt_rim_near_disk(const double cc[3], const double e1[3], const double e
 {
     int d = PLT_TOP, ne = 0;
     int64_t k = 0;
+    double thr2 = thr * thr;
     for (;;) {
         double w = ldexp(4.0, -d);
         double lo = (double)k * w;
@@ -144,21 +148,19 @@ int orc_plt_rim_near_disk(const double cc[3], const double e1[3], const double e
         rim_point(cc, e1, e2, a, lo + 0.5 * w, p);
         double h, e;
         point_disk_he(p, cd, nd, b, &h, &e);
-        double dist = sqrt(h * h + e * e);
         ne++;
-        if (dist <= thr) {
+        if (h * h + e * e <= thr2) {
             if (evals) *evals = ne;
             return 1;
         }
         double off = lo < 2.0 ? 1.0 : 3.0;
         double sl = lo - off, sr = (lo + w) - off;
         double m2 = (sl <= 0.0 && sr >= 0.0) ? 0.0 : (sl * sl < sr * sr ? sl * sl : sr * sr);
-        double r = ((2.0 * a) / (1.0 + m2)) * (0.5 * w);
+        double r = (a * (2.0 - m2)) * (0.5 * w);
         double hl = fabs(h) - r * sn, el = e - r;
         if (hl < 0.0) hl = 0.0;
         if (el < 0.0) el = 0.0;
-        double lb = sqrt(hl * hl + el * el);
-        if (!(lb > thr)) {
+        if (!(hl * hl + el * el > thr2)) {
             if (d == PLT_DEPTH || ne >= PLT_EVALS) {
                 if (evals) *evals = ne;
                 return 1;
