@@ -26,7 +26,7 @@ __all__ = ["SrmError", "Rve", "load", "srm_init", "srm_step", "srm_run_to_target
            "srm_nearest", "srm_rdf", "srm_voronoi_lvf", "srm_tuning",
            "srm_destroy", "srm_last_error", "srm_set_timing", "srm_get_timings",
            "srm_certify_noalloc", "srm_save", "srm_load", "srm_job_footprint", "make_job", "Batch",
-           "PREC_F64", "PREC_F32"]
+           "PREC_F64", "PREC_F32", "Platelets", "srm_plt_lambda_for_density", "srm_plt_collide_pairs"]
 
 PREC_F64, PREC_F32 = 64, 32
 RADII_EXPLICIT, RADII_MONO, RADII_LOGNORMAL = 0, 1, 2
@@ -97,6 +97,23 @@ class srm_tuning(Structure):
                 ("reserved", c_int32), ("ns_per_particle_sweep", c_double)]
 
 
+class srm_plt_params(Structure):
+    _fields_ = [("c_w", c_double), ("c_m", c_double), ("c_r", c_double), ("N_k", c_int32), ("N_l", c_int32),
+                ("N_shake", c_int32), ("wait_limit", c_int32), ("sweep0", c_uint64)]
+
+
+class srm_plt_step_info(Structure):
+    _fields_ = [("result", c_int32), ("k_sweeps", c_int32), ("shake_sweeps", c_int32), ("reserved", c_int32),
+                ("colliding", c_int64), ("moves", c_int64), ("lambda_", c_double), ("rho", c_double),
+                ("sweep", c_uint64)]
+
+
+class srm_plt_run_info(Structure):
+    _fields_ = [("iterations", c_int64), ("accepted", c_int64), ("shaken", c_int64), ("sweeps", c_int64),
+                ("moves", c_int64), ("lambda_", c_double), ("rho", c_double), ("converged", c_int32),
+                ("reserved", c_int32)]
+
+
 class srm_timings(Structure):
     _fields_ = [("ms_bin", c_double), ("ms_sweep", c_double), ("ms_check", c_double),
                 ("ms_control", c_double), ("supersteps", c_int64), ("sweep_launches", c_int64),
@@ -164,6 +181,21 @@ def load() -> ctypes.CDLL:
                                          POINTER(c_int64), POINTER(c_double), c_void_p], c_int32),
                 "srm_get_timings": ([H, POINTER(srm_timings)], c_int32),
                 "srm_last_error": ([], c_char_p),
+                "srm_plt_params_default": ([POINTER(srm_plt_params)], None),
+                "srm_plt_lambda_for_density": ([POINTER(c_double), c_int64, c_double, c_double, c_double,
+                                                POINTER(c_double)], c_int32),
+                "srm_plt_init": ([POINTER(H), POINTER(c_double), c_int64, c_double, c_double, c_void_p, c_void_p,
+                                  c_double, c_double, c_uint64, POINTER(srm_plt_params), c_void_p], c_int32),
+                "srm_plt_set_params": ([H, POINTER(srm_plt_params)], c_int32),
+                "srm_plt_step": ([H, POINTER(srm_plt_step_info)], c_int32),
+                "srm_plt_run_to_target": ([H, c_int64, POINTER(srm_plt_run_info)], c_int32),
+                "srm_plt_sweeps": ([H, c_int32, POINTER(c_int64)], c_int32),
+                "srm_plt_check": ([H, POINTER(c_int64), c_void_p], c_int32),
+                "srm_plt_state": ([H, c_void_p, c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_uint64)],
+                                  c_int32),
+                "srm_plt_collide_pairs": ([c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double, c_void_p,
+                                           c_void_p], c_int32),
+                "srm_plt_destroy": ([H], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -654,3 +686,102 @@ def srm_load(data: bytes, stream=None, torch_memory=True) -> "Rve":
     st = srm_get_state(h)
     r.dim, r.n = int(st["dim"]), int(st["n"])
     return r
+
+
+# ---------------------------------------------------------------------------
+# Platelets (include/srm_platelet.h): spherodisks with a rotational move
+# ---------------------------------------------------------------------------
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+def srm_plt_lambda_for_density(box, n, a0, t0, rho) -> float:
+    """Scale at which n platelets reach the number density rho of Eq. 1."""
+    L = (c_double * 3)(*[float(v) for v in box])
+    out = c_double()
+    _check(load().srm_plt_lambda_for_density(L, int(n), float(a0), float(t0), float(rho), ctypes.byref(out)))
+    return out.value
+
+
+def srm_plt_collide_pairs(dj, ni, nj, a, t, stream=None) -> np.ndarray:
+    """Contact decisions of m platelet pairs (rows of dj, ni, nj) on the GPU."""
+    import torch
+    dj, ni, nj = _f64(dj, (-1, 3)), _f64(ni, (-1, 3)), _f64(nj, (-1, 3))
+    m = dj.shape[0]
+    out = np.zeros(m, dtype=np.uint8)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().srm_plt_collide_pairs(dj.ctypes.data, ni.ctypes.data, nj.ctypes.data, m, float(a), float(t),
+                                        out.ctypes.data, stream))
+    return out
+
+
+class Platelets:
+    """One platelet RVE on the GPU (srm_plt_* of include/srm_platelet.h):
+    centres x and unit normals u (n x 3), base sizes a0, t0, scales lambda0
+    (start) and lambda_t (target), seed and the SRM parameters with the
+    rotation rate c_r."""
+
+    def __init__(self, box, x, u, a0, t0, lambda0, lambda_t, seed, *, c_m, c_w=0.01, c_r=0.0, N_k=10, N_l=10,
+                 N_shake=10, wait_limit=0, sweep0=0, stream=None):
+        import torch
+        lib = load()
+        self.box = tuple(float(v) for v in box)
+        x, u = _f64(x, (-1, 3)), _f64(u, (-1, 3))
+        self.n = x.shape[0]
+        p = srm_plt_params()
+        lib.srm_plt_params_default(ctypes.byref(p))
+        p.c_w, p.c_m, p.c_r, p.N_k, p.N_l, p.N_shake = c_w, c_m, c_r, N_k, N_l, N_shake
+        p.wait_limit, p.sweep0 = wait_limit, sweep0
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        L = (c_double * 3)(*self.box)
+        h = H()
+        _check(lib.srm_plt_init(ctypes.byref(h), L, self.n, float(a0), float(t0), x.ctypes.data, u.ctypes.data,
+                                float(lambda0), float(lambda_t), int(seed), ctypes.byref(p), stream))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().srm_plt_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_params(self, *, c_m, c_w=0.01, c_r=0.0, N_k=10, N_l=10, N_shake=10, wait_limit=0):
+        p = srm_plt_params()
+        load().srm_plt_params_default(ctypes.byref(p))
+        p.c_w, p.c_m, p.c_r, p.N_k, p.N_l, p.N_shake, p.wait_limit = c_w, c_m, c_r, N_k, N_l, N_shake, wait_limit
+        _check(load().srm_plt_set_params(self._h, ctypes.byref(p)))
+
+    def step(self) -> dict:
+        info = srm_plt_step_info()
+        _check(load().srm_plt_step(self._h, ctypes.byref(info)))
+        return _as_dict(info)
+
+    def run_to_target(self, max_iters: int = 0) -> dict:
+        info = srm_plt_run_info()
+        st = load().srm_plt_run_to_target(self._h, int(max_iters), ctypes.byref(info))
+        if st not in (0, 4):
+            _check(st)
+        return _as_dict(info)
+
+    def sweeps(self, count: int) -> int:
+        acc = c_int64()
+        _check(load().srm_plt_sweeps(self._h, int(count), ctypes.byref(acc)))
+        return acc.value
+
+    def check(self):
+        cnt = c_int64()
+        flags = np.zeros(self.n, dtype=np.uint8)
+        _check(load().srm_plt_check(self._h, ctypes.byref(cnt), flags.ctypes.data))
+        return cnt.value, flags
+
+    def state(self):
+        x = np.zeros((self.n, 3))
+        u = np.zeros((self.n, 3))
+        lam, rho, sw = c_double(), c_double(), c_uint64()
+        _check(load().srm_plt_state(self._h, x.ctypes.data, u.ctypes.data, ctypes.byref(lam), ctypes.byref(rho),
+                                    ctypes.byref(sw)))
+        return x, u, dict(lambda_=lam.value, rho=rho.value, sweep=sw.value)

@@ -1,0 +1,1014 @@
+// platelet.cu -- SRM for thin circular platelets (Section 3.3): spherodisk
+// contact, the rotational migration move, and the binning, sweep and check
+// kernels with the host control of Algorithm 1 for them.
+//
+// Binary64 throughout.  This translation unit is compiled with
+// --fmad=false: every multiply and add below is one IEEE operation in the
+// order written (division and square root are correctly rounded), so the
+// results equal the binary64 reference bit for bit.
+//
+// Layout in HBM: centres and normals as double4 (x, y, z, unused) in
+// particle-id order, two copies each (P and the swollen copy Q of Algorithm
+// 1); per sweep a cell list (cell of each platelet, cell starts, ids sorted
+// by cell and by id inside a cell) and one completion stamp per cell.
+//
+// Sweep: one launch per sweep.  Each warp takes the next cell from a work
+// counter in canonical colour order, waits until the cells of lower colour
+// within reach are stamped for this sweep (bounded polls), then moves the
+// cell's platelets one after the other in id order: all lanes form the same
+// trial, lanes 0..26 each scan one of the 27 cells around the trial's cell
+// for platelets within bounding-sphere reach, all 32 lanes then decide the
+// staged pairs (binary64, the cost of the method), and a warp vote accepts
+// the first trial without a collision.  Lane 0 writes the new state; the
+// cell's stamp is released at the end.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+#include "srm_platelet.h"
+
+namespace srm {
+namespace plt {
+
+constexpr int TOP = 3;       // first level evaluated: 8 intervals of the circle
+constexpr int DEPTH = 30;    // finest level
+constexpr int EVALS = 4096;  // evaluations per rim
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ double dot3(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Orthonormal basis of the plane of the unit normal n: e1 = n x axis_k /
+// |n x axis_k| with k the axis of smallest |n_k| (first on ties), e2 = n x e1.
+__device__ __forceinline__ void basis(const double n[3], double e1[3], double e2[3])
+{
+    const double ax = fabs(n[0]), ay = fabs(n[1]), az = fabs(n[2]);
+    int k = 0;
+    double m = ax;
+    if (ay < m) {
+        k = 1;
+        m = ay;
+    }
+    if (az < m) k = 2;
+    double c[3];
+    if (k == 0) {
+        c[0] = 0.0;
+        c[1] = n[2];
+        c[2] = -n[1];
+    } else if (k == 1) {
+        c[0] = -n[2];
+        c[1] = 0.0;
+        c[2] = n[0];
+    } else {
+        c[0] = n[1];
+        c[1] = -n[0];
+        c[2] = 0.0;
+    }
+    const double r = sqrt(dot3(c, c));
+    for (int a = 0; a < 3; a++) e1[a] = c[a] / r;
+    e2[0] = n[1] * e1[2] - n[2] * e1[1];
+    e2[1] = n[2] * e1[0] - n[0] * e1[2];
+    e2[2] = n[0] * e1[1] - n[1] * e1[0];
+}
+
+// Height h of p above the disk's plane and excess e of its projected
+// distance from the centre over the radius b (0 inside).
+__device__ __forceinline__ void point_disk_he(const double p[3], const double cd[3], const double nd[3], double b,
+                                              double &h, double &e)
+{
+    const double q[3] = {p[0] - cd[0], p[1] - cd[1], p[2] - cd[2]};
+    const double hh = dot3(q, nd);
+    const double r[3] = {q[0] - hh * nd[0], q[1] - hh * nd[1], q[2] - hh * nd[2]};
+    const double rr = dot3(r, r);
+    h = hh;
+    e = rr <= b * b ? 0.0 : sqrt(rr) - b;
+}
+
+// Is a point of the circle (centre cc, basis e1 e2, radius a) within thr of
+// the disk (cd, nd, b)?  sn: sine of the angle between the normals.  The
+// circle is parametrised by tau in [0, 4): s = tau - 1 on the first half,
+// ((1 - s^2) e1 + 2 s e2) / (1 + s^2), s = tau - 3 and the negated point on
+// the second.  Depth-first bisection from the 8 intervals of width 1/2, left
+// half first: a midpoint with h^2 + e^2 <= thr^2 is a collision; an interval
+// whose lower bound max(0, |h| - V r sn)^2 + max(0, e - V r)^2 (V = a (2 -
+// min s^2) >= 2 a / (1 + min s^2), the rim speed; r the half-width) exceeds
+// thr^2 is dropped; an interval still open at level 30 or after 4096
+// evaluations counts as a collision.
+__device__ __noinline__ bool rim_near_disk(const double cc[3], const double e1[3], const double e2[3], double a,
+                                           const double cd[3], const double nd[3], double b, double sn, double thr)
+{
+    int d = TOP, ne = 0;
+    long long k = 0;
+    const double thr2 = thr * thr;
+    for (;;) {
+        const double w = __longlong_as_double((long long)(1023 + 2 - d) << 52);  // 4 / 2^d
+        const double lo = (double)k * w;
+        const double tau = lo + 0.5 * w;
+        const bool first = tau < 2.0;
+        const double s = first ? tau - 1.0 : tau - 3.0;
+        const double s2 = s * s;
+        const double inv = 1.0 / (1.0 + s2);
+        const double C = (1.0 - s2) * inv, S = (2.0 * s) * inv;
+        const double sa = first ? a : -a;
+        double p[3];
+        for (int j = 0; j < 3; j++) p[j] = cc[j] + sa * (C * e1[j] + S * e2[j]);
+        double h, e;
+        point_disk_he(p, cd, nd, b, h, e);
+        ne++;
+        if (h * h + e * e <= thr2) return true;
+        const double off = lo < 2.0 ? 1.0 : 3.0;
+        const double sl = lo - off, sr = (lo + w) - off;
+        const double m2 = (sl <= 0.0 && sr >= 0.0) ? 0.0 : (sl * sl < sr * sr ? sl * sl : sr * sr);
+        const double r = (a * (2.0 - m2)) * (0.5 * w);
+        double hl = fabs(h) - r * sn, el = e - r;
+        if (hl < 0.0) hl = 0.0;
+        if (el < 0.0) el = 0.0;
+        if (!(hl * hl + el * el > thr2)) {
+            if (d == DEPTH || ne >= EVALS) return true;
+            d++;
+            k = 2 * k;
+            continue;
+        }
+        while (d > TOP && (k & 1)) {
+            k >>= 1;
+            d--;
+        }
+        k++;
+        if (d == TOP && k == 8) return false;
+    }
+}
+
+// Contact of two platelets with disk radius a and half-thickness t: dj =
+// centre of j minus centre of i (minimum image).  Bounding spheres, the two
+// slabs along the normals, then the rim of i against the disk of j and the
+// rim of j against the disk of i.
+__device__ __forceinline__ bool collide(const double dj[3], const double ni[3], const double nj[3], double a, double t)
+{
+    const double thr = t + t;
+    const double reach = (a + a) + thr;
+    if (dot3(dj, dj) > reach * reach) return false;
+    const double c = dot3(ni, nj);
+    double s2 = 1.0 - c * c;
+    if (s2 < 0.0) s2 = 0.0;
+    const double sn = sqrt(s2);
+    const double ext = a * sn;
+    if (fabs(dot3(dj, ni)) - ext > thr) return false;
+    if (fabs(dot3(dj, nj)) - ext > thr) return false;
+    double ei1[3], ei2[3], ej1[3], ej2[3];
+    const double zero[3] = {0.0, 0.0, 0.0};
+    basis(ni, ei1, ei2);
+    basis(nj, ej1, ej2);
+    if (rim_near_disk(zero, ei1, ei2, a, dj, nj, a, sn, thr)) return true;
+    return rim_near_disk(dj, ej1, ej2, a, zero, ni, a, sn, thr);
+}
+
+// Uniform direction of try l from stream tag (0: translation, the draw of
+// the spheres; 0x80000000: rotation): candidate m is the Philox4x32-10 block
+// at counter (pid, sweep lo, l + 2^16 m, sweep hi | tag), key = the seed,
+// coordinates (w - 2^31) 2^-31; first candidate with 0 < |v|^2 <= 1,
+// divided by sqrt(|v|^2); after 32 rejections the first axis.
+__device__ __noinline__ void unit_dir(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, uint32_t tag,
+                                      double u[3])
+{
+    for (int m = 0; m < MAX_CAND; m++) {
+        uint32_t c[4], k0, k1;
+        draw_block(seed, sweep, pid, l, (uint64_t)m, c, k0, k1);
+        c[3] |= tag;
+        philox4x32<true>(c, k0, k1);
+        double v[3];
+        for (int j = 0; j < 3; j++) v[j] = (double)((long long)c[j] - 2147483648LL) * 0x1p-31;
+        double s = v[0] * v[0] + v[1] * v[1];
+        s = s + v[2] * v[2];
+        if (s > 0.0 && s <= 1.0) {
+            const double nrm = sqrt(s);
+            for (int j = 0; j < 3; j++) u[j] = v[j] / nrm;
+            return;
+        }
+    }
+    u[0] = 1.0;
+    u[1] = 0.0;
+    u[2] = 0.0;
+}
+
+struct PltDev {
+    double L[3], halfL[3], w[3];
+    int32_t n[3], H[3];
+    int32_t N, ncells, N_l, wait_limit;
+    double a, t, c_m, c_r;
+    uint64_t seed, sweep;
+    uint32_t epoch;
+    double4_32a *X, *U;
+    int32_t *cell_of, *count, *start, *members;
+    uint32_t *stamp;
+    uint32_t *ctr;  // [0] work counter, [1] status
+    unsigned long long *acc;  // [0] accepted moves, [1] colliding platelets
+};
+
+__device__ __forceinline__ int32_t wrapc(int32_t c, int32_t n)
+{
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+
+__device__ __forceinline__ int32_t cell_of_point(const PltDev &d, const double q[3], int32_t c[3])
+{
+    for (int j = 0; j < 3; j++) c[j] = cell_coord_d(q[j], d.w[j], d.n[j]);
+    return c[0] + d.n[0] * (c[1] + d.n[1] * c[2]);
+}
+
+__device__ __forceinline__ void min_image(const PltDev &d, const double4_32a &xt, const double q[3], double dj[3])
+{
+    const double v[3] = {xt.x, xt.y, xt.z};
+    for (int j = 0; j < 3; j++) {
+        double x = v[j] - q[j];
+        if (x > d.halfL[j]) x -= d.L[j];
+        if (x < -d.halfL[j]) x += d.L[j];
+        dj[j] = x;
+    }
+}
+
+// Algorithm 2 on centres: cell of each platelet and the cell counts.
+__global__ void k_pbin_count(PltDev d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const double4_32a p = d.X[i];
+    const double q[3] = {p.x, p.y, p.z};
+    int32_t c[3];
+    const int32_t cell = cell_of_point(d, q, c);
+    d.cell_of[i] = cell;
+    atomicAdd(&d.count[cell], 1);
+}
+
+// Exclusive scan of the counts into the cell starts (one block of 1024
+// threads walking the cells), counts reset for the scatter.
+__global__ void __launch_bounds__(1024) k_pscan(PltDev d)
+{
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < d.ncells; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int32_t v = i < d.ncells ? d.count[i] : 0;
+        int32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(FULL, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        const int32_t excl = carry + (warp ? wsum[warp - 1] : 0) + x - v;
+        if (i < d.ncells) {
+            d.start[i] = excl;
+            d.count[i] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) d.start[d.ncells] = carry;
+}
+
+__global__ void k_pscatter(PltDev d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const int32_t c = d.cell_of[i];
+    d.members[d.start[c] + atomicAdd(&d.count[c], 1)] = i;
+}
+
+// Ids of each cell in ascending order (insertion sort; cells hold a few
+// tens of platelets).
+__global__ void k_psort(PltDev d)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.ncells) return;
+    const int32_t b = d.start[c], e = d.start[c + 1];
+    for (int32_t i = b + 1; i < e; i++) {
+        const int32_t v = d.members[i];
+        int32_t j = i - 1;
+        while (j >= b && d.members[j] > v) {
+            d.members[j + 1] = d.members[j];
+            j--;
+        }
+        d.members[j + 1] = v;
+    }
+}
+
+// Trial l of platelet pid from (x0, u0): centre x0 + c_m u wrapped (Alg 4),
+// normal (u0 + c_r v) / |u0 + c_r v| (unchanged when c_r = 0).
+__device__ __forceinline__ void trial(const PltDev &d, uint64_t pid, uint64_t l, const double x0[3],
+                                      const double u0[3], double q[3], double u[3])
+{
+    double dir[3];
+    unit_dir(d.seed, d.sweep, pid, l, 0u, dir);
+    for (int j = 0; j < 3; j++) q[j] = wrap_d(x0[j] + d.c_m * dir[j], d.L[j]);
+    if (d.c_r > 0.0) {
+        double v[3], m[3];
+        unit_dir(d.seed, d.sweep, pid, l, 0x80000000u, v);
+        for (int j = 0; j < 3; j++) m[j] = u0[j] + d.c_r * v[j];
+        const double r = sqrt(dot3(m, m));
+        for (int j = 0; j < 3; j++) u[j] = m[j] / r;
+    } else {
+        for (int j = 0; j < 3; j++) u[j] = u0[j];
+    }
+}
+
+// Waits (lanes in parallel) until every cell of lower colour within H of
+// (cx, cy, cz) carries this sweep's stamp.  False if a wait gave up (the
+// status word is then set) or another warp already failed.
+__device__ bool wait_lower(const PltDev &d, int cx, int cy, int cz, int chi, int lane)
+{
+    const int sx = 2 * d.H[0] + 1, sy = 2 * d.H[1] + 1, sz = 2 * d.H[2] + 1;
+    const int total = sx * sy * sz;
+    bool ok = true;
+    for (int o = lane; o < total && ok; o += 32) {
+        const int ox = o % sx - d.H[0], oy = (o / sx) % sy - d.H[1], oz = o / (sx * sy) - d.H[2];
+        if (ox == 0 && oy == 0 && oz == 0) continue;
+        const int nx = wrapc(cx + ox, d.n[0]), ny = wrapc(cy + oy, d.n[1]), nz = wrapc(cz + oz, d.n[2]);
+        const int nchi = nx % 3 + 3 * (ny % 3) + 9 * (nz % 3);
+        if (nchi >= chi) continue;
+        const uint32_t *st = &d.stamp[nx + d.n[0] * (ny + d.n[1] * nz)];
+        int polls = 0;
+        while (ld_acquire(st) != d.epoch) {
+            if (d.wait_limit < 0 || ++polls > d.wait_limit) {
+                atomicExch(&d.ctr[1], (uint32_t)STATUS_WAIT_TIMEOUT);
+                ok = false;
+                break;
+            }
+            if ((polls & 255) == 0 && ld_acquire(&d.ctr[1]) != 0u) {
+                ok = false;
+                break;
+            }
+            __nanosleep(polls < 1024 ? 64 : 1000);
+        }
+    }
+    return __all_sync(FULL, ok);
+}
+
+constexpr int SLOT = 16;  // candidates a lane stages per trial (more are tested in place)
+
+// Is the trial (q, u) of platelet pid clear of every platelet listed in the
+// 27 cells around q's cell?  Lanes 0..26 scan one cell each and stage the
+// platelets inside bounding-sphere reach; the staged pairs are then decided
+// by all 32 lanes, 32 at a time, stopping at the first collision.  A lane
+// with more than SLOT candidates decides the rest itself.  Returns the same
+// answer on every lane.
+__device__ bool trial_collides(const PltDev &d, int32_t pid, const double q[3], const double u[3], int lane,
+                               int32_t *slot, int32_t *flat)
+{
+    int cnt = 0;
+    bool hit = false;
+    const double reach = (d.a + d.a) + (d.t + d.t);
+    const double reach2 = reach * reach;
+    int32_t b0 = 0, e0 = 0;
+    if (lane < 27) {
+        int32_t qc[3];
+        cell_of_point(d, q, qc);
+        const int nx = wrapc(qc[0] + lane % 3 - 1, d.n[0]);
+        const int ny = wrapc(qc[1] + (lane / 3) % 3 - 1, d.n[1]);
+        const int nz = wrapc(qc[2] + lane / 9 - 1, d.n[2]);
+        const int nc = nx + d.n[0] * (ny + d.n[1] * nz);
+        b0 = d.start[nc];
+        e0 = d.start[nc + 1];
+        for (int32_t j = b0; j < e0; j++) {
+            const int32_t tj = d.members[j];
+            if (tj == pid) continue;
+            const double4_32a xt = d.X[tj];
+            double dj[3];
+            min_image(d, xt, q, dj);
+            if (dot3(dj, dj) > reach2) continue;
+            if (cnt < SLOT) {
+                slot[lane * SLOT + cnt] = tj;
+                cnt++;
+            } else if (!hit) {
+                const double4_32a ut = d.U[tj];
+                const double nt[3] = {ut.x, ut.y, ut.z};
+                hit = collide(dj, u, nt, d.a, d.t);
+            }
+        }
+    }
+    // flatten the staged candidates
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    for (int i = 0; i < cnt; i++) flat[incl - cnt + i] = slot[lane * SLOT + i];
+    __syncwarp();
+    bool found = __any_sync(FULL, hit);
+    for (int r0 = 0; r0 < total && !found; r0 += 32) {
+        const int i = r0 + lane;
+        bool h = false;
+        if (i < total) {
+            const int32_t tj = flat[i];
+            const double4_32a xt = d.X[tj], ut = d.U[tj];
+            double dj[3];
+            min_image(d, xt, q, dj);
+            const double nt[3] = {ut.x, ut.y, ut.z};
+            h = collide(dj, u, nt, d.a, d.t);
+        }
+        found = __any_sync(FULL, h);
+    }
+    __syncwarp();
+    return found;
+}
+
+// One sweep of Algorithm 3 over the cells in canonical colour order.
+__global__ void __launch_bounds__(128) k_psweep(PltDev d)
+{
+    __shared__ int32_t s_slot[4][27 * SLOT];
+    __shared__ int32_t s_flat[4][27 * SLOT];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int S0 = d.n[0] / 3, S1 = d.n[1] / 3, S2 = d.n[2] / 3;
+    const int per = S0 * S1 * S2;
+    const int total = 27 * per;
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = (int)atomicAdd(&d.ctr[0], 1u);
+        w = __shfl_sync(FULL, w, 0);
+        if (w >= total) return;
+        const int chi = w / per, r = w - chi * per;
+        const int cx = 3 * (r % S0) + chi % 3, cy = 3 * ((r / S0) % S1) + (chi / 3) % 3;
+        const int cz = 3 * (r / (S0 * S1)) + chi / 9;
+        const int cell = cx + d.n[0] * (cy + d.n[1] * cz);
+        if (!wait_lower(d, cx, cy, cz, chi, lane)) return;
+        unsigned long long acc = 0;
+        const int32_t k1 = d.start[cell + 1];
+        for (int32_t k = d.start[cell]; k < k1; k++) {
+            const int32_t pid = d.members[k];
+            const double4_32a xp = d.X[pid], up = d.U[pid];
+            const double x0[3] = {xp.x, xp.y, xp.z}, u0[3] = {up.x, up.y, up.z};
+            for (int l = 0; l < d.N_l; l++) {
+                double q[3], u[3];
+                trial(d, (uint64_t)pid, (uint64_t)l, x0, u0, q, u);
+                if (!trial_collides(d, pid, q, u, lane, s_slot[wib], s_flat[wib])) {
+                    if (lane == 0) {
+                        double4_32a nx4, nu4;
+                        nx4.x = q[0];
+                        nx4.y = q[1];
+                        nx4.z = q[2];
+                        nx4.w = 0.0;
+                        nu4.x = u[0];
+                        nu4.y = u[1];
+                        nu4.z = u[2];
+                        nu4.w = 0.0;
+                        d.X[pid] = nx4;
+                        d.U[pid] = nu4;
+                    }
+                    acc++;
+                    break;
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (acc) atomicAdd(&d.acc[0], acc);
+            st_release(&d.stamp[cell], d.epoch);
+        }
+    }
+}
+
+// Algorithm 6: does platelet i collide with any other platelet listed in
+// the 27 cells around its cell?
+__global__ void __launch_bounds__(128) k_pcheck(PltDev d, uint8_t *flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const double4_32a xp = d.X[i], up = d.U[i];
+    const double q[3] = {xp.x, xp.y, xp.z}, u[3] = {up.x, up.y, up.z};
+    int32_t c[3];
+    cell_of_point(d, q, c);
+    bool hit = false;
+    for (int o = 0; o < 27 && !hit; o++) {
+        const int nx = wrapc(c[0] + o % 3 - 1, d.n[0]), ny = wrapc(c[1] + (o / 3) % 3 - 1, d.n[1]);
+        const int nz = wrapc(c[2] + o / 9 - 1, d.n[2]);
+        const int nc = nx + d.n[0] * (ny + d.n[1] * nz);
+        const int32_t je = d.start[nc + 1];
+        for (int32_t j = d.start[nc]; j < je && !hit; j++) {
+            const int32_t tj = d.members[j];
+            if (tj == i) continue;
+            const double4_32a xt = d.X[tj], ut = d.U[tj];
+            double dj[3];
+            min_image(d, xt, q, dj);
+            const double nt[3] = {ut.x, ut.y, ut.z};
+            hit = collide(dj, u, nt, d.a, d.t);
+        }
+    }
+    if (flags) flags[i] = hit ? 1 : 0;
+    if (hit) atomicAdd(&d.acc[1], 1ull);
+}
+
+__global__ void k_ppairs(const double *dj, const double *ni, const double *nj, long long m, double a, double t,
+                         uint8_t *out)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const double d3[3] = {dj[3 * k], dj[3 * k + 1], dj[3 * k + 2]};
+    const double a3[3] = {ni[3 * k], ni[3 * k + 1], ni[3 * k + 2]};
+    const double b3[3] = {nj[3 * k], nj[3 * k + 1], nj[3 * k + 2]};
+    out[k] = collide(d3, a3, b3, a, t) ? 1 : 0;
+}
+
+}  // namespace plt
+}  // namespace srm
+
+using srm::plt::PltDev;
+
+struct srm_plt {
+    cudaStream_t s = nullptr;
+    int64_t n = 0;
+    double L[3] = {1.0, 1.0, 1.0};
+    double a0 = 0.0, t0 = 0.0, lam = 1.0, lam_t = 1.0;
+    uint64_t seed = 0, sweep = 0;
+    srm_plt_params p{};
+    int cur = 0;                        // P = copy cur, Q = copy 1 - cur
+    double4_32a *X[2] = {nullptr, nullptr}, *U[2] = {nullptr, nullptr};
+    int32_t *cell_of = nullptr, *count = nullptr, *start = nullptr, *members = nullptr;
+    uint32_t *stamp = nullptr, *ctr = nullptr;
+    unsigned long long *acc = nullptr;
+    uint8_t *flags = nullptr;
+    unsigned long long *pin = nullptr;  // pinned: [0] moves, [1] colliding, [2] status
+    int64_t ncells_cap = 0;
+    uint32_t epoch = 0;
+    int64_t iters = 0, accepted = 0, shaken = 0, sweeps = 0, moves = 0;
+};
+
+namespace {
+
+constexpr int WAIT_DEFAULT = 1 << 23;  // polls; after the first 1024 each sleeps about 1 us
+
+void grid_of(const srm_plt *h, double lam, int32_t n[3], double w[3], int32_t H[3])
+{
+    const double cs = 2.5 * (lam * (h->a0 + h->t0)) + h->p.c_m;
+    const double reach = 2.0 * (lam * (h->a0 + h->t0)) + 2.0 * h->p.c_m;
+    for (int a = 0; a < 3; a++) {
+        int64_t k = (int64_t)(h->L[a] / (3.0 * cs));
+        if (k < 1) k = 1;
+        n[a] = (int32_t)(3 * k);
+        w[a] = h->L[a] / (double)n[a];
+        int32_t Ha = reach < w[a] * (1.0 - 1e-9) ? 1 : 2;
+        if (Ha > (n[a] - 1) / 2) Ha = (n[a] - 1) / 2;
+        H[a] = Ha;
+    }
+}
+
+srm_status check_params(const srm_plt_params &p)
+{
+    if (!(p.c_m > 0.0)) return fail(SRM_E_ARG, "c_m must be > 0");
+    if (!(p.c_w >= 0.0)) return fail(SRM_E_ARG, "c_w must be >= 0");
+    if (!(p.c_r >= 0.0 && p.c_r < 1.0)) return fail(SRM_E_ARG, "c_r must be in [0, 1)");
+    if (p.N_k < 1 || p.N_l < 1 || p.N_l > 65535 || p.N_shake < 0)
+        return fail(SRM_E_ARG, "N_k >= 1, N_l in 1..65535, N_shake >= 0");
+    return SRM_OK;
+}
+
+srm_status check_box(const srm_plt *h, const srm_plt_params &p, double lam_t)
+{
+    const double cs = 2.5 * (lam_t * (h->a0 + h->t0)) + p.c_m;
+    for (int a = 0; a < 3; a++)
+        if (h->L[a] < 3.0 * cs) return fail(SRM_E_ARG, "box narrower than three cells of the final cell size");
+    return SRM_OK;
+}
+
+template <typename T>
+srm_status dalloc(srm_plt *h, T **p, size_t count)
+{
+    if (cudaMallocAsync((void **)p, sizeof(T) * (count ? count : 1), h->s) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(SRM_E_NOMEM, "device allocation failed");
+    }
+    return SRM_OK;
+}
+
+void dfree(srm_plt *h, void *p)
+{
+    if (p) cudaFreeAsync(p, h->s);
+}
+
+srm_status ensure_cells(srm_plt *h, int64_t ncells)
+{
+    if (ncells <= h->ncells_cap) return SRM_OK;
+    if (ncells > 0x7fffffffLL - 1) return fail(SRM_E_ARG, "cell grid too fine");
+    dfree(h, h->count);
+    dfree(h, h->start);
+    dfree(h, h->stamp);
+    h->count = nullptr;
+    h->start = nullptr;
+    h->stamp = nullptr;
+    srm_status st;
+    if ((st = dalloc(h, &h->count, (size_t)ncells)) != SRM_OK) return st;
+    if ((st = dalloc(h, &h->start, (size_t)ncells + 1)) != SRM_OK) return st;
+    if ((st = dalloc(h, &h->stamp, (size_t)ncells)) != SRM_OK) return st;
+    CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * (size_t)ncells, h->s));
+    h->ncells_cap = ncells;
+    return SRM_OK;
+}
+
+// Binning of copy c on the grid of scale lam_grid (Algorithm 2), radii at
+// scale lam; fills d for the following sweep or check.
+srm_status bin(srm_plt *h, int c, double lam, double lam_grid, PltDev &d)
+{
+    std::memset(&d, 0, sizeof(d));
+    grid_of(h, lam_grid, d.n, d.w, d.H);
+    const int64_t ncells = (int64_t)d.n[0] * d.n[1] * d.n[2];
+    srm_status st = ensure_cells(h, ncells);
+    if (st != SRM_OK) return st;
+    for (int a = 0; a < 3; a++) {
+        d.L[a] = h->L[a];
+        d.halfL[a] = 0.5 * h->L[a];
+    }
+    d.N = (int32_t)h->n;
+    d.ncells = (int32_t)ncells;
+    d.N_l = h->p.N_l;
+    d.wait_limit = h->p.wait_limit == 0 ? WAIT_DEFAULT : h->p.wait_limit;
+    d.a = lam * h->a0;
+    d.t = lam * h->t0;
+    d.c_m = h->p.c_m;
+    d.c_r = h->p.c_r;
+    d.seed = h->seed;
+    d.sweep = h->sweep;
+    d.X = h->X[c];
+    d.U = h->U[c];
+    d.cell_of = h->cell_of;
+    d.count = h->count;
+    d.start = h->start;
+    d.members = h->members;
+    d.stamp = h->stamp;
+    d.ctr = h->ctr;
+    d.acc = h->acc;
+    const int nb = (int)((h->n + 255) / 256);
+    CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * (size_t)ncells, h->s));
+    srm::plt::k_pbin_count<<<nb, 256, 0, h->s>>>(d);
+    srm::plt::k_pscan<<<1, 1024, 0, h->s>>>(d);
+    srm::plt::k_pscatter<<<nb, 256, 0, h->s>>>(d);
+    srm::plt::k_psort<<<(int)((ncells + 255) / 256), 256, 0, h->s>>>(d);
+    CK(cudaGetLastError());
+    return SRM_OK;
+}
+
+// One sweep of Algorithm 3 on copy c at scale lam, binned on the grid of
+// lam_grid; advances the sweep counter.
+srm_status sweep_once(srm_plt *h, int c, double lam, double lam_grid)
+{
+    PltDev d;
+    srm_status st = bin(h, c, lam, lam_grid, d);
+    if (st != SRM_OK) return st;
+    d.epoch = ++h->epoch;
+    CK(cudaMemsetAsync(h->ctr, 0, sizeof(uint32_t), h->s));  // work counter (the status word stays)
+    int64_t blocks = ((int64_t)d.ncells + 3) / 4;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    srm::plt::k_psweep<<<(int)blocks, 128, 0, h->s>>>(d);
+    CK(cudaGetLastError());
+    h->sweep++;
+    h->sweeps++;
+    return SRM_OK;
+}
+
+// Reads the counters (synchronises the stream); SRM_E_DEVICE_TIMEOUT if a
+// sweep gave up waiting.
+srm_status read_counters(srm_plt *h, unsigned long long &moves, unsigned long long &colliding)
+{
+    CK(cudaMemcpyAsync(h->pin, h->acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h->pin + 2, h->ctr + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    moves = h->pin[0];
+    colliding = h->pin[1];
+    const uint32_t status = (uint32_t)(h->pin[2] & 0xffffffffull);
+    if (status != 0u) return fail(SRM_E_DEVICE_TIMEOUT, "a platelet sweep gave up waiting for a neighbouring cell");
+    return SRM_OK;
+}
+
+srm_status zero_counters(srm_plt *h)
+{
+    CK(cudaMemsetAsync(h->acc, 0, 2 * sizeof(unsigned long long), h->s));
+    return SRM_OK;
+}
+
+// Algorithm 6 on copy c at scale lam (grid of lam_grid): colliding count.
+srm_status check_copy(srm_plt *h, int c, double lam, double lam_grid, uint8_t *flags_dev, int64_t &count,
+                      unsigned long long &moves)
+{
+    PltDev d;
+    srm_status st = bin(h, c, lam, lam_grid, d);
+    if (st != SRM_OK) return st;
+    CK(cudaMemsetAsync(h->acc + 1, 0, sizeof(unsigned long long), h->s));
+    srm::plt::k_pcheck<<<(int)((h->n + 127) / 128), 128, 0, h->s>>>(d, flags_dev);
+    CK(cudaGetLastError());
+    unsigned long long col = 0;
+    if ((st = read_counters(h, moves, col)) != SRM_OK) return st;
+    count = (int64_t)col;
+    return SRM_OK;
+}
+
+double density(const srm_plt *h)
+{
+    const double D = 2.0 * (h->lam * (h->a0 + h->t0));
+    return (double)h->n * (D * D * D) / (h->L[0] * h->L[1] * h->L[2]);
+}
+
+}  // namespace
+
+extern "C" {
+
+void srm_plt_params_default(srm_plt_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->c_w = 0.01;
+    p->N_k = 10;
+    p->N_l = 10;
+    p->N_shake = 10;
+}
+
+srm_status srm_plt_lambda_for_density(const double box[3], int64_t n, double a0, double t0, double rho,
+                                      double *lambda)
+{
+    if (!box || !lambda) return fail(SRM_E_ARG, "null argument");
+    if (n < 1 || !(a0 > 0.0) || !(t0 > 0.0) || !(rho > 0.0)) return fail(SRM_E_ARG, "n, sizes and rho must be > 0");
+    for (int a = 0; a < 3; a++)
+        if (!(box[a] > 0.0)) return fail(SRM_E_ARG, "box lengths must be > 0");
+    const double V = box[0] * box[1] * box[2];
+    *lambda = std::cbrt(rho * V / (double)n) / (2.0 * (a0 + t0));
+    return SRM_OK;
+}
+
+srm_status srm_plt_init(srm_plt **out, const double box[3], int64_t n, double a0, double t0, const double *x,
+                        const double *u, double lambda0, double lambda_t, uint64_t seed, const srm_plt_params *pin,
+                        void *cuda_stream)
+{
+    if (!out || !box || !x || !u) return fail(SRM_E_ARG, "null argument");
+    *out = nullptr;
+    if (n < 1 || n > 0x7fffffffLL - 1) return fail(SRM_E_ARG, "n must be in [1, 2^31 - 1)");
+    if (!(a0 > 0.0) || !(t0 > 0.0)) return fail(SRM_E_ARG, "base sizes must be > 0");
+    if (!(lambda0 > 0.0) || !(lambda_t >= lambda0)) return fail(SRM_E_ARG, "need 0 < lambda0 <= lambda_t");
+    for (int a = 0; a < 3; a++)
+        if (!(box[a] > 0.0)) return fail(SRM_E_ARG, "box lengths must be > 0");
+    srm_plt_params p;
+    if (pin) p = *pin;
+    else srm_plt_params_default(&p);
+    srm_status st = check_params(p);
+    if (st != SRM_OK) return st;
+    srm_plt *h = new (std::nothrow) srm_plt();
+    if (!h) return fail(SRM_E_NOMEM, "host allocation failed");
+    h->s = (cudaStream_t)cuda_stream;
+    h->n = n;
+    for (int a = 0; a < 3; a++) h->L[a] = box[a];
+    h->a0 = a0;
+    h->t0 = t0;
+    h->lam = lambda0;
+    h->lam_t = lambda_t;
+    h->seed = seed;
+    h->sweep = p.sweep0;
+    h->p = p;
+    if ((st = check_box(h, p, lambda_t)) != SRM_OK) {
+        delete h;
+        return st;
+    }
+    for (int64_t i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++)
+            if (!(x[3 * i + a] >= 0.0 && x[3 * i + a] < box[a])) {
+                delete h;
+                return fail(SRM_E_ARG, "centres must lie in [0, L)");
+            }
+    const size_t nn = (size_t)n;
+    if ((st = dalloc(h, &h->X[0], nn)) != SRM_OK || (st = dalloc(h, &h->X[1], nn)) != SRM_OK ||
+        (st = dalloc(h, &h->U[0], nn)) != SRM_OK || (st = dalloc(h, &h->U[1], nn)) != SRM_OK ||
+        (st = dalloc(h, &h->cell_of, nn)) != SRM_OK || (st = dalloc(h, &h->members, nn)) != SRM_OK ||
+        (st = dalloc(h, &h->flags, nn)) != SRM_OK || (st = dalloc(h, &h->ctr, 2)) != SRM_OK ||
+        (st = dalloc(h, &h->acc, 2)) != SRM_OK) {
+        srm_plt_destroy(h);
+        return st;
+    }
+    if (cudaMallocHost((void **)&h->pin, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        h->pin = nullptr;
+        srm_plt_destroy(h);
+        return fail(SRM_E_NOMEM, "pinned allocation failed");
+    }
+    std::memset(h->pin, 0, 4 * sizeof(unsigned long long));
+    std::vector<double> hx(4 * nn), hu(4 * nn);
+    for (size_t i = 0; i < nn; i++)
+        for (int a = 0; a < 3; a++) {
+            hx[4 * i + a] = x[3 * i + a];
+            hu[4 * i + a] = u[3 * i + a];
+        }
+    cudaError_t e = cudaMemcpyAsync(h->X[0], hx.data(), sizeof(double) * 4 * nn, cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->U[0], hu.data(), sizeof(double) * 4 * nn, cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ctr, 0, 2 * sizeof(uint32_t), h->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, 2 * sizeof(unsigned long long), h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);  // host staging buffers go out of scope
+    if (e != cudaSuccess) {
+        srm_plt_destroy(h);
+        return fail(SRM_E_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return SRM_OK;
+}
+
+srm_status srm_plt_set_params(srm_plt *h, const srm_plt_params *p)
+{
+    if (!h || !p) return fail(SRM_E_ARG, "null argument");
+    srm_status st = check_params(*p);
+    if (st != SRM_OK) return st;
+    if ((st = check_box(h, *p, h->lam_t)) != SRM_OK) return st;
+    const uint64_t keep = h->sweep;
+    h->p = *p;
+    h->p.sweep0 = keep;
+    return SRM_OK;
+}
+
+srm_status srm_plt_step(srm_plt *h, srm_plt_step_info *out)
+{
+    if (!h) return fail(SRM_E_ARG, "null handle");
+    srm_plt_step_info info;
+    std::memset(&info, 0, sizeof(info));
+    srm_status st;
+    if (h->lam >= h->lam_t) {
+        info.result = 2;
+    } else {
+        h->iters++;
+        double lam_q = h->lam * (1.0 + h->p.c_w);
+        if (lam_q > h->lam_t) lam_q = h->lam_t;
+        const int P = h->cur, Q = 1 - h->cur;
+        const size_t bytes = sizeof(double4_32a) * (size_t)h->n;
+        CK(cudaMemcpyAsync(h->X[Q], h->X[P], bytes, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaMemcpyAsync(h->U[Q], h->U[P], bytes, cudaMemcpyDeviceToDevice, h->s));
+        if ((st = zero_counters(h)) != SRM_OK) return st;
+        int64_t cnt = -1;
+        unsigned long long mv = 0;
+        int k;
+        for (k = 1; k <= h->p.N_k; k++) {
+            if ((st = sweep_once(h, Q, lam_q, lam_q)) != SRM_OK) return st;
+            if ((st = check_copy(h, Q, lam_q, lam_q, nullptr, cnt, mv)) != SRM_OK) return st;
+            if (cnt == 0) break;
+        }
+        const bool acc = cnt == 0;
+        info.k_sweeps = acc ? k : h->p.N_k;
+        info.colliding = cnt;
+        if (acc) {
+            h->cur = Q;
+            h->lam = lam_q;
+            h->accepted++;
+            info.result = 1;
+        } else {
+            for (int j = 0; j < h->p.N_shake; j++)
+                if ((st = sweep_once(h, P, h->lam, lam_q)) != SRM_OK) return st;
+            unsigned long long col = 0;
+            if ((st = read_counters(h, mv, col)) != SRM_OK) return st;
+            h->shaken++;
+            info.result = 0;
+            info.shake_sweeps = h->p.N_shake;
+        }
+        info.moves = (int64_t)mv;
+        h->moves += (int64_t)mv;
+    }
+    info.lambda = h->lam;
+    info.rho = density(h);
+    info.sweep = h->sweep;
+    if (out) *out = info;
+    return SRM_OK;
+}
+
+srm_status srm_plt_run_to_target(srm_plt *h, int64_t max_iters, srm_plt_run_info *out)
+{
+    if (!h) return fail(SRM_E_ARG, "null handle");
+    srm_plt_run_info r;
+    std::memset(&r, 0, sizeof(r));
+    const int64_t it0 = h->iters, acc0 = h->accepted, sh0 = h->shaken, sw0 = h->sweeps, mv0 = h->moves;
+    int64_t it = 0;
+    srm_status st = SRM_OK;
+    while (h->lam < h->lam_t && (max_iters <= 0 || it < max_iters)) {
+        if ((st = srm_plt_step(h, nullptr)) != SRM_OK) break;
+        it++;
+    }
+    r.iterations = h->iters - it0;
+    r.accepted = h->accepted - acc0;
+    r.shaken = h->shaken - sh0;
+    r.sweeps = h->sweeps - sw0;
+    r.moves = h->moves - mv0;
+    r.lambda = h->lam;
+    r.rho = density(h);
+    r.converged = h->lam >= h->lam_t ? 1 : 0;
+    if (out) *out = r;
+    if (st != SRM_OK) return st;
+    return r.converged ? SRM_OK : fail(SRM_E_NOT_CONVERGED, "iteration cap reached before the target scale");
+}
+
+srm_status srm_plt_sweeps(srm_plt *h, int32_t count, int64_t *accepted)
+{
+    if (!h) return fail(SRM_E_ARG, "null handle");
+    if (count < 0) return fail(SRM_E_ARG, "count must be >= 0");
+    srm_status st = zero_counters(h);
+    if (st != SRM_OK) return st;
+    for (int32_t i = 0; i < count; i++)
+        if ((st = sweep_once(h, h->cur, h->lam, h->lam)) != SRM_OK) return st;
+    unsigned long long mv = 0, col = 0;
+    if ((st = read_counters(h, mv, col)) != SRM_OK) return st;
+    h->moves += (int64_t)mv;
+    if (accepted) *accepted = (int64_t)mv;
+    return SRM_OK;
+}
+
+srm_status srm_plt_check(srm_plt *h, int64_t *colliding, uint8_t *flags)
+{
+    if (!h) return fail(SRM_E_ARG, "null handle");
+    int64_t cnt = 0;
+    unsigned long long mv = 0;
+    srm_status st = check_copy(h, h->cur, h->lam, h->lam, flags ? h->flags : nullptr, cnt, mv);
+    if (st != SRM_OK) return st;
+    if (flags) {
+        CK(cudaMemcpyAsync(flags, h->flags, (size_t)h->n, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+    }
+    if (colliding) *colliding = cnt;
+    return SRM_OK;
+}
+
+srm_status srm_plt_state(srm_plt *h, double *x, double *u, double *lambda, double *rho, uint64_t *sweep)
+{
+    if (!h) return fail(SRM_E_ARG, "null handle");
+    const size_t nn = (size_t)h->n;
+    if (x || u) {
+        std::vector<double> hx(4 * nn), hu(4 * nn);
+        CK(cudaMemcpyAsync(hx.data(), h->X[h->cur], sizeof(double) * 4 * nn, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaMemcpyAsync(hu.data(), h->U[h->cur], sizeof(double) * 4 * nn, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        for (size_t i = 0; i < nn; i++)
+            for (int a = 0; a < 3; a++) {
+                if (x) x[3 * i + a] = hx[4 * i + a];
+                if (u) u[3 * i + a] = hu[4 * i + a];
+            }
+    }
+    if (lambda) *lambda = h->lam;
+    if (rho) *rho = density(h);
+    if (sweep) *sweep = h->sweep;
+    return SRM_OK;
+}
+
+srm_status srm_plt_collide_pairs(const double *dj, const double *ni, const double *nj, int64_t m, double a,
+                                 double t, uint8_t *out, void *cuda_stream)
+{
+    if (m < 0 || !(a > 0.0) || !(t > 0.0)) return fail(SRM_E_ARG, "m >= 0, a > 0, t > 0");
+    if (m == 0) return SRM_OK;
+    if (!dj || !ni || !nj || !out) return fail(SRM_E_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t vb = sizeof(double) * 3 * (size_t)m;
+    double *d = nullptr;
+    uint8_t *o = nullptr;
+    if (cudaMallocAsync((void **)&d, 3 * vb, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SRM_E_NOMEM, "device allocation failed");
+    }
+    if (cudaMallocAsync((void **)&o, (size_t)m, s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(d, s);
+        return fail(SRM_E_NOMEM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(d, dj, vb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 3 * m, ni, vb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 6 * m, nj, vb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        srm::plt::k_ppairs<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(d, d + 3 * m, d + 6 * m, (long long)m, a, t, o);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, o, (size_t)m, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    cudaFreeAsync(o, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(SRM_E_CUDA, std::string("pair decisions: ") + cudaGetErrorString(e));
+    return SRM_OK;
+}
+
+void srm_plt_destroy(srm_plt *h)
+{
+    if (!h) return;
+    void *bufs[] = {h->X[0], h->X[1], h->U[0], h->U[1], h->cell_of, h->count, h->start,
+                    h->members, h->stamp, h->ctr, h->acc, h->flags};
+    for (void *b : bufs)
+        if (b) cudaFreeAsync(b, h->s);
+    cudaStreamSynchronize(h->s);
+    if (h->pin) cudaFreeHost(h->pin);
+    delete h;
+}
+
+}  // extern "C"

@@ -182,6 +182,57 @@ def ensemble_member(i: int, count: int = 256, seed0: int = 0, n_lo: float = 1e3,
     return _mono(f"ensemble[{i}]", dim, n, phi_t, f0, seed0 + i)
 
 
+@dataclass
+class PlateletWorkload:
+    """Thin platelets (spherodisks, Section 3.3) in a box: base sizes (a0,
+    t0) of the target (scale 1), starting scale lambda0, centres x and unit
+    normals u (n x 3) of a collision-free start, and SRM parameters."""
+    name: str
+    box: tuple
+    a0: float
+    t0: float
+    lambda0: float
+    x: np.ndarray
+    u: np.ndarray
+    rho_t: float
+    seed: int
+    c_w: float
+    c_m: float
+    c_r: float
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+
+def platelets(seed: int = 7, n: int = 20_000, aspect: float = 100.0, rho_t: float = 5.0, f0: float = 0.1,
+              c_w: float = 0.01, c_m_rel: float = 0.02, c_r: float = 0.02, box: float = 1.0) -> PlateletWorkload:
+    """n identical platelets of aspect ratio D / (2 t) = aspect in a cubic box,
+    sized so that the target is the number density rho_t of Eq. 1 (rho =
+    n D^3 / V) at scale 1.  Start: random sequential addition of the bounding
+    spheres (radius a + t) at volume fraction f0 -- bounding spheres that do
+    not overlap leave the platelets apart -- with uniform random normals.
+    Default parameters are those of a "house of cards" run: swelling of 1% per
+    iteration against short migration steps (c_m = c_m_rel D, twice the
+    thickness at aspect 100) and small turns (c_r)."""
+    V = box ** 3
+    D = (rho_t * V / n) ** (1.0 / 3.0)
+    t0 = D / (2.0 * aspect)
+    a0 = D / 2.0 - t0
+    Rb = a0 + t0
+    lam0 = (f0 * V / (n * 4.0 / 3.0 * math.pi)) ** (1.0 / 3.0) / Rb
+    x = rsa(3, (box,) * 3, np.full(n, lam0 * Rb), seed)
+    w = uniforms(seed, 0x4E524D4C, 2 * n)  # "NRML"
+    z = 2.0 * w[:n] - 1.0
+    ph = 2.0 * math.pi * w[n:]
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    u = np.stack([s * np.cos(ph), s * np.sin(ph), z], axis=1)
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    return PlateletWorkload("platelets", (box,) * 3, a0, t0, lam0, x, u, rho_t, seed, c_w, c_m_rel * D, c_r,
+                            extra={"aspect": aspect, "D": D, "f0": f0})
+
+
 RECIPES = {
     "disks_1k": disks_1k,
     "spheres_100k": spheres_100k,
