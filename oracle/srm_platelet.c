@@ -17,7 +17,8 @@
  *     a = lambda a0, t = lambda t0 (Alg 1, the shape is kept);
  *   - the number density of Eq. 1 is rho = N D^3 / V with V the box volume;
  *   - two platelets collide when the distance between their disks is at
- *     most t_i + t_j (closed inequality, as for spheres);
+ *     most t_i + t_j (closed inequality, as for spheres), decided in
+ *     binary32 with the widening described below;
  *   - try l of Alg 3 moves the centre by c_m u (u from stream 0, as for
  *     spheres) and turns the normal to (n + c_r v) / |n + c_r v| with v a
  *     second uniform direction (stream 1), 0 <= c_r < 1;
@@ -43,11 +44,20 @@
  * sqrt(max(0, |h| - V r sin)^2 + max(0, e - V r)^2) bounds the distance
  * from below.  Intervals whose bound is above the threshold are dropped, a
  * midpoint at or below it is a collision (both compared as squares: h^2 +
- * e^2 <= thr^2).  An interval still undecided at
- * 2^-30 of the circle, or after 4096 evaluations of one rim, counts as a
- * collision (a near-contact the bisection cannot resolve is reported as
- * contact).  Cheap exact separations come first: the
- * bounding spheres, and the two slabs along the normals.
+ * e^2 <= thr^2).  An interval still undecided at 2^-20 of the circle, or
+ * after 4096 evaluations of one rim, counts as a collision (a near-contact
+ * the bisection cannot resolve is reported as contact).  Cheap exact
+ * separations come first: the bounding spheres, and the two slabs along the
+ * normals.
+ *
+ * Precision.  The decision is evaluated in binary32 (the paper fixes no
+ * precision for it) on the pair's relative geometry: the centre difference
+ * is formed in binary64 under the minimum image and then rounded, like the
+ * normals and sizes.  Its threshold is widened from t_i + t_j by 2^-16 a,
+ * more than the binary32 rounding of every quantity in the test (a few
+ * ulps of 3 a), so a pair whose true distance is at most t_i + t_j is
+ * always reported (the widening only ever adds contacts).  Centres, normals,
+ * draws and moves stay in binary64.
  */
 #include <math.h>
 #include <stdint.h>
@@ -59,73 +69,88 @@ double orc_wrap(double x, double L);
 void orc_grid(int dim, const double L[3], double lam, double rmax, double c_m, int64_t n[3], double w[3]);
 
 #define PLT_TOP 3        /* first level evaluated: 8 intervals of the circle */
-#define PLT_DEPTH 30     /* finest level */
+#define PLT_DEPTH 20     /* finest level (binary32 still separates its midpoints) */
 #define PLT_EVALS 4096   /* evaluations per rim */
+#define PLT_SLACK 0x1p-16f /* threshold widening, in units of the disk radius */
 
+static float dot3f(const float a[3], const float b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 /* Orthonormal basis (e1, e2) of the plane of the unit normal n: e1 is n
  * crossed with the coordinate axis of smallest |n_k| (the first such axis),
  * normalised; e2 = n x e1. */
-void orc_plt_basis(const double n[3], double e1[3], double e2[3])
+static void basis_f(const float n[3], float e1[3], float e2[3])
 {
-    double ax = fabs(n[0]), ay = fabs(n[1]), az = fabs(n[2]);
+    float ax = fabsf(n[0]), ay = fabsf(n[1]), az = fabsf(n[2]);
     int k = 0;
-    double m = ax;
+    float m = ax;
     if (ay < m) {
         k = 1;
         m = ay;
     }
     if (az < m) k = 2;
-    double c[3];
+    float c[3];
     if (k == 0) {
-        c[0] = 0.0; c[1] = n[2]; c[2] = -n[1];
+        c[0] = 0.0f; c[1] = n[2]; c[2] = -n[1];
     } else if (k == 1) {
-        c[0] = -n[2]; c[1] = 0.0; c[2] = n[0];
+        c[0] = -n[2]; c[1] = 0.0f; c[2] = n[0];
     } else {
-        c[0] = n[1]; c[1] = -n[0]; c[2] = 0.0;
+        c[0] = n[1]; c[1] = -n[0]; c[2] = 0.0f;
     }
-    double r = sqrt(dot3(c, c));
+    float r = sqrtf(dot3f(c, c));
     for (int a = 0; a < 3; a++) e1[a] = c[a] / r;
     e2[0] = n[1] * e1[2] - n[2] * e1[1];
     e2[1] = n[2] * e1[0] - n[0] * e1[2];
     e2[2] = n[0] * e1[1] - n[1] * e1[0];
 }
 
+void orc_plt_basis(const double n[3], double e1[3], double e2[3])
+{
+    const float nf[3] = {(float)n[0], (float)n[1], (float)n[2]};
+    float a[3], b[3];
+    basis_f(nf, a, b);
+    for (int k = 0; k < 3; k++) {
+        e1[k] = a[k];
+        e2[k] = b[k];
+    }
+}
+
 /* Point p against the disk of centre cd, unit normal nd, radius b: h =
  * height above the plane, e = distance of the projection from cd minus b,
  * or 0 when the projection lies in the disk. */
-static void point_disk_he(const double p[3], const double cd[3], const double nd[3], double b, double *h,
-                          double *e)
+static void point_disk_he(const float p[3], const float cd[3], const float nd[3], float b, float *h, float *e)
 {
-    double q[3] = {p[0] - cd[0], p[1] - cd[1], p[2] - cd[2]};
-    double hh = dot3(q, nd);
-    double r[3] = {q[0] - hh * nd[0], q[1] - hh * nd[1], q[2] - hh * nd[2]};
-    double rr = dot3(r, r);
+    float q[3] = {p[0] - cd[0], p[1] - cd[1], p[2] - cd[2]};
+    float hh = dot3f(q, nd);
+    float r[3] = {q[0] - hh * nd[0], q[1] - hh * nd[1], q[2] - hh * nd[2]};
+    float rr = dot3f(r, r);
     *h = hh;
-    *e = rr <= b * b ? 0.0 : sqrt(rr) - b;
+    *e = rr <= b * b ? 0.0f : sqrtf(rr) - b;
 }
 
-/* Distance from point p to that disk: sqrt(h^2 + e^2). */
+/* Distance from point p to that disk: sqrt(h^2 + e^2) (binary32). */
 double orc_plt_point_disk(const double p[3], const double cd[3], const double nd[3], double b)
 {
-    double h, e;
-    point_disk_he(p, cd, nd, b, &h, &e);
-    return sqrt(h * h + e * e);
+    const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+    const float cf[3] = {(float)cd[0], (float)cd[1], (float)cd[2]};
+    const float nf[3] = {(float)nd[0], (float)nd[1], (float)nd[2]};
+    float h, e;
+    point_disk_he(pf, cf, nf, (float)b, &h, &e);
+    return sqrtf(h * h + e * e);
 }
 
 /* Point of the circle (centre cc, basis e1 e2, radius a) at parameter tau in
  * [0, 4): tau < 2 gives s = tau - 1 and the half circle
  * ((1 - s^2) e1 + 2 s e2) / (1 + s^2), tau >= 2 gives s = tau - 3 and the
  * opposite half (the same point negated). */
-static void rim_point(const double cc[3], const double e1[3], const double e2[3], double a, double tau, double p[3])
+static void rim_point(const float cc[3], const float e1[3], const float e2[3], float a, float tau, float p[3])
 {
-    int first = tau < 2.0;
-    double s = first ? tau - 1.0 : tau - 3.0;
-    double s2 = s * s;
-    double inv = 1.0 / (1.0 + s2);
-    double C = (1.0 - s2) * inv, S = (2.0 * s) * inv;
-    double sa = first ? a : -a;
+    int first = tau < 2.0f;
+    float s = first ? tau - 1.0f : tau - 3.0f;
+    float s2 = s * s;
+    float inv = 1.0f / (1.0f + s2);
+    float C = (1.0f - s2) * inv, S = (2.0f * s) * inv;
+    float sa = first ? a : -a;
     for (int k = 0; k < 3; k++) p[k] = cc[k] + sa * (C * e1[k] + S * e2[k]);
 }
 
@@ -135,31 +160,31 @@ static void rim_point(const double cc[3], const double e1[3], const double e2[3]
  * intervals of level 3, left half first.  Returns 1 (yes or undecided) or 0
  * (every point is farther than thr); *evals receives the number of
  * midpoints evaluated. */
-int orc_plt_rim_near_disk(const double cc[3], const double e1[3], const double e2[3], double a,
-                          const double cd[3], const double nd[3], double b, double sn, double thr, int *evals)
+static int rim_near_disk_f(const float cc[3], const float e1[3], const float e2[3], float a, const float cd[3],
+                           const float nd[3], float b, float sn, float thr, int *evals)
 {
     int d = PLT_TOP, ne = 0;
     int64_t k = 0;
-    double thr2 = thr * thr;
+    float thr2 = thr * thr;
     for (;;) {
-        double w = ldexp(4.0, -d);
-        double lo = (double)k * w;
-        double p[3];
-        rim_point(cc, e1, e2, a, lo + 0.5 * w, p);
-        double h, e;
+        float w = ldexpf(4.0f, -d);
+        float lo = (float)k * w;
+        float p[3];
+        rim_point(cc, e1, e2, a, lo + 0.5f * w, p);
+        float h, e;
         point_disk_he(p, cd, nd, b, &h, &e);
         ne++;
         if (h * h + e * e <= thr2) {
             if (evals) *evals = ne;
             return 1;
         }
-        double off = lo < 2.0 ? 1.0 : 3.0;
-        double sl = lo - off, sr = (lo + w) - off;
-        double m2 = (sl <= 0.0 && sr >= 0.0) ? 0.0 : (sl * sl < sr * sr ? sl * sl : sr * sr);
-        double r = (a * (2.0 - m2)) * (0.5 * w);
-        double hl = fabs(h) - r * sn, el = e - r;
-        if (hl < 0.0) hl = 0.0;
-        if (el < 0.0) el = 0.0;
+        float off = lo < 2.0f ? 1.0f : 3.0f;
+        float sl = lo - off, sr = (lo + w) - off;
+        float m2 = (sl <= 0.0f && sr >= 0.0f) ? 0.0f : (sl * sl < sr * sr ? sl * sl : sr * sr);
+        float r = (a * (2.0f - m2)) * (0.5f * w);
+        float hl = fabsf(h) - r * sn, el = e - r;
+        if (hl < 0.0f) hl = 0.0f;
+        if (el < 0.0f) el = 0.0f;
         if (!(hl * hl + el * el > thr2)) {
             if (d == PLT_DEPTH || ne >= PLT_EVALS) {
                 if (evals) *evals = ne;
@@ -181,30 +206,51 @@ int orc_plt_rim_near_disk(const double cc[3], const double e1[3], const double e
     }
 }
 
+int orc_plt_rim_near_disk(const double cc[3], const double e1[3], const double e2[3], double a,
+                          const double cd[3], const double nd[3], double b, double sn, double thr, int *evals)
+{
+    float c1[3], f1[3], f2[3], c2[3], n2[3];
+    for (int k = 0; k < 3; k++) {
+        c1[k] = (float)cc[k];
+        f1[k] = (float)e1[k];
+        f2[k] = (float)e2[k];
+        c2[k] = (float)cd[k];
+        n2[k] = (float)nd[k];
+    }
+    return rim_near_disk_f(c1, f1, f2, (float)a, c2, n2, (float)b, (float)sn, (float)thr, evals);
+}
+
 /* Do the spherodisks i and j (disk radius a, half-thickness t each) collide?
- * dj = centre of j minus centre of i (minimum image); ni, nj unit normals.
- * Steps: bounding spheres (|dj| > 2 a + 2 t: no); slab along ni (|dj.ni| -
- * a sin > 2 t: no) and along nj, with sin the sine of the angle between the
- * normals; then the rim of i against the disk of j and the rim of j against
- * the disk of i. */
+ * dj = centre of j minus centre of i (minimum image, binary64); ni, nj unit
+ * normals.  The test runs in binary32 on dj, ni, nj, a and t rounded to
+ * binary32, against the threshold 2 t + 2^-16 a (the widening exceeds every
+ * binary32 rounding of the test, so a pair at distance <= 2 t is always
+ * found).  Steps: bounding spheres (|dj| > 2 a + thr: no); slab along ni
+ * (|dj.ni| - a sin > thr: no) and along nj, with sin the sine of the angle
+ * between the normals; then the rim of i against the disk of j and the rim
+ * of j against the disk of i. */
 int orc_plt_collide(const double dj[3], const double ni[3], const double nj[3], double a, double t)
 {
-    double thr = t + t;
-    double reach = (a + a) + thr;
-    if (dot3(dj, dj) > reach * reach) return 0;
-    double c = dot3(ni, nj);
-    double s2 = 1.0 - c * c;
-    if (s2 < 0.0) s2 = 0.0;
-    double sn = sqrt(s2);
-    double ext = a * sn;
-    if (fabs(dot3(dj, ni)) - ext > thr) return 0;
-    if (fabs(dot3(dj, nj)) - ext > thr) return 0;
-    double ei1[3], ei2[3], ej1[3], ej2[3];
-    const double zero[3] = {0.0, 0.0, 0.0};
-    orc_plt_basis(ni, ei1, ei2);
-    orc_plt_basis(nj, ej1, ej2);
-    if (orc_plt_rim_near_disk(zero, ei1, ei2, a, dj, nj, a, sn, thr, NULL)) return 1;
-    if (orc_plt_rim_near_disk(dj, ej1, ej2, a, zero, ni, a, sn, thr, NULL)) return 1;
+    const float d[3] = {(float)dj[0], (float)dj[1], (float)dj[2]};
+    const float u[3] = {(float)ni[0], (float)ni[1], (float)ni[2]};
+    const float v[3] = {(float)nj[0], (float)nj[1], (float)nj[2]};
+    const float af = (float)a, tf = (float)t;
+    float thr = (tf + tf) + af * PLT_SLACK;
+    float reach = (af + af) + thr;
+    if (dot3f(d, d) > reach * reach) return 0;
+    float c = dot3f(u, v);
+    float s2 = 1.0f - c * c;
+    if (s2 < 0.0f) s2 = 0.0f;
+    float sn = sqrtf(s2);
+    float ext = af * sn;
+    if (fabsf(dot3f(d, u)) - ext > thr) return 0;
+    if (fabsf(dot3f(d, v)) - ext > thr) return 0;
+    float ei1[3], ei2[3], ej1[3], ej2[3];
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    basis_f(u, ei1, ei2);
+    basis_f(v, ej1, ej2);
+    if (rim_near_disk_f(zero, ei1, ei2, af, d, v, af, sn, thr, NULL)) return 1;
+    if (rim_near_disk_f(d, ej1, ej2, af, zero, u, af, sn, thr, NULL)) return 1;
     return 0;
 }
 
