@@ -13,12 +13,17 @@
  * V the box volume.
  *
  * Contact.  Two platelets collide when the distance between their disks is
- * at most t_i + t_j.  The library decides this in binary64 on the rims of the
- * two disks (the distance between two disks is reached at a rim point of one
- * of them) by bisection with a certified lower bound; a near-contact that the
- * bisection cannot resolve within 2^-30 of the circle or 4096 evaluations per
+ * at most t_i + t_j.  The library decides this on the rims of the two disks
+ * (the distance between two disks is reached at a rim point of one of them)
+ * by bisection with a certified lower bound; a near-contact that the
+ * bisection cannot resolve within 2^-20 of the circle or 4096 evaluations per
  * rim counts as contact.  Cheap exact separations come first (bounding
- * spheres, slabs along the two normals).
+ * spheres, slabs along the two normals).  The test runs in binary32 on the
+ * pair's relative geometry (centre difference formed in binary64 under the
+ * minimum image, then rounded) against the threshold t_i + t_j + 2^-16 a:
+ * the widening exceeds the binary32 rounding of the test, so every pair
+ * closer than t_i + t_j is found; pairs within the widening count as
+ * touching.  Centres, normals, draws and moves are binary64.
  *
  * Move.  Try l of Algorithm 3 moves the centre by c_m u (u a uniform
  * direction, the same draw as for spheres) and turns the normal to

@@ -2,10 +2,12 @@
 // contact, the rotational migration move, and the binning, sweep and check
 // kernels with the host control of Algorithm 1 for them.
 //
-// Binary64 throughout.  This translation unit is compiled with
-// --fmad=false: every multiply and add below is one IEEE operation in the
-// order written (division and square root are correctly rounded), so the
-// results equal the binary64 reference bit for bit.
+// Centres, normals, draws and moves in binary64; the contact test in
+// binary32 on the pair's relative geometry with a widened threshold (see
+// collide).  This translation unit is compiled with --fmad=false: every
+// multiply and add below is one IEEE operation in the order written
+// (division and square root are correctly rounded), so the results equal
+// the reference bit for bit.
 //
 // Layout in HBM: centres and normals as double4 (x, y, z, unused) in
 // particle-id order, two copies each (P and the swollen copy Q of Algorithm
@@ -18,7 +20,7 @@
 // cell's platelets one after the other in id order: all lanes form the same
 // trial, lanes 0..26 each scan one of the 27 cells around the trial's cell
 // for platelets within bounding-sphere reach, all 32 lanes then decide the
-// staged pairs (binary64, the cost of the method), and a warp vote accepts
+// staged pairs (binary32, the cost of the method), and a warp vote accepts
 // the first trial without a collision.  Lane 0 writes the new state; the
 // cell's stamp is released at the end.
 #include <cmath>
@@ -33,9 +35,10 @@
 namespace srm {
 namespace plt {
 
-constexpr int TOP = 3;       // first level evaluated: 8 intervals of the circle
-constexpr int DEPTH = 30;    // finest level
-constexpr int EVALS = 4096;  // evaluations per rim
+constexpr int TOP = 3;                // first level evaluated: 8 intervals of the circle
+constexpr int DEPTH = 20;             // finest level (binary32 still separates its midpoints)
+constexpr int EVALS = 4096;           // evaluations per rim
+constexpr float SLACK = 0x1p-16f;     // threshold widening, in units of the disk radius
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ double dot3(const double a[3], const double b[3])
@@ -43,33 +46,38 @@ __device__ __forceinline__ double dot3(const double a[3], const double b[3])
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+__device__ __forceinline__ float dot3f(const float a[3], const float b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
 // Orthonormal basis of the plane of the unit normal n: e1 = n x axis_k /
 // |n x axis_k| with k the axis of smallest |n_k| (first on ties), e2 = n x e1.
-__device__ __forceinline__ void basis(const double n[3], double e1[3], double e2[3])
+__device__ __forceinline__ void basis(const float n[3], float e1[3], float e2[3])
 {
-    const double ax = fabs(n[0]), ay = fabs(n[1]), az = fabs(n[2]);
+    const float ax = fabsf(n[0]), ay = fabsf(n[1]), az = fabsf(n[2]);
     int k = 0;
-    double m = ax;
+    float m = ax;
     if (ay < m) {
         k = 1;
         m = ay;
     }
     if (az < m) k = 2;
-    double c[3];
+    float c[3];
     if (k == 0) {
-        c[0] = 0.0;
+        c[0] = 0.0f;
         c[1] = n[2];
         c[2] = -n[1];
     } else if (k == 1) {
         c[0] = -n[2];
-        c[1] = 0.0;
+        c[1] = 0.0f;
         c[2] = n[0];
     } else {
         c[0] = n[1];
         c[1] = -n[0];
-        c[2] = 0.0;
+        c[2] = 0.0f;
     }
-    const double r = sqrt(dot3(c, c));
+    const float r = sqrtf(dot3f(c, c));
     for (int a = 0; a < 3; a++) e1[a] = c[a] / r;
     e2[0] = n[1] * e1[2] - n[2] * e1[1];
     e2[1] = n[2] * e1[0] - n[0] * e1[2];
@@ -78,15 +86,15 @@ __device__ __forceinline__ void basis(const double n[3], double e1[3], double e2
 
 // Height h of p above the disk's plane and excess e of its projected
 // distance from the centre over the radius b (0 inside).
-__device__ __forceinline__ void point_disk_he(const double p[3], const double cd[3], const double nd[3], double b,
-                                              double &h, double &e)
+__device__ __forceinline__ void point_disk_he(const float p[3], const float cd[3], const float nd[3], float b,
+                                              float &h, float &e)
 {
-    const double q[3] = {p[0] - cd[0], p[1] - cd[1], p[2] - cd[2]};
-    const double hh = dot3(q, nd);
-    const double r[3] = {q[0] - hh * nd[0], q[1] - hh * nd[1], q[2] - hh * nd[2]};
-    const double rr = dot3(r, r);
+    const float q[3] = {p[0] - cd[0], p[1] - cd[1], p[2] - cd[2]};
+    const float hh = dot3f(q, nd);
+    const float r[3] = {q[0] - hh * nd[0], q[1] - hh * nd[1], q[2] - hh * nd[2]};
+    const float rr = dot3f(r, r);
     h = hh;
-    e = rr <= b * b ? 0.0 : sqrt(rr) - b;
+    e = rr <= b * b ? 0.0f : sqrtf(rr) - b;
 }
 
 // Is a point of the circle (centre cc, basis e1 e2, radius a) within thr of
@@ -97,37 +105,37 @@ __device__ __forceinline__ void point_disk_he(const double p[3], const double cd
 // half first: a midpoint with h^2 + e^2 <= thr^2 is a collision; an interval
 // whose lower bound max(0, |h| - V r sn)^2 + max(0, e - V r)^2 (V = a (2 -
 // min s^2) >= 2 a / (1 + min s^2), the rim speed; r the half-width) exceeds
-// thr^2 is dropped; an interval still open at level 30 or after 4096
-// evaluations counts as a collision.
-__device__ __noinline__ bool rim_near_disk(const double cc[3], const double e1[3], const double e2[3], double a,
-                                           const double cd[3], const double nd[3], double b, double sn, double thr)
+// thr^2 is dropped; an interval still open at level 20 or after 4096
+// evaluations counts as a collision.  Binary32 throughout.
+__device__ __noinline__ bool rim_near_disk(const float cc[3], const float e1[3], const float e2[3], float a,
+                                           const float cd[3], const float nd[3], float b, float sn, float thr)
 {
     int d = TOP, ne = 0;
-    long long k = 0;
-    const double thr2 = thr * thr;
+    int k = 0;
+    const float thr2 = thr * thr;
     for (;;) {
-        const double w = __longlong_as_double((long long)(1023 + 2 - d) << 52);  // 4 / 2^d
-        const double lo = (double)k * w;
-        const double tau = lo + 0.5 * w;
-        const bool first = tau < 2.0;
-        const double s = first ? tau - 1.0 : tau - 3.0;
-        const double s2 = s * s;
-        const double inv = 1.0 / (1.0 + s2);
-        const double C = (1.0 - s2) * inv, S = (2.0 * s) * inv;
-        const double sa = first ? a : -a;
-        double p[3];
+        const float w = __int_as_float((127 + 2 - d) << 23);  // 4 / 2^d
+        const float lo = (float)k * w;
+        const float tau = lo + 0.5f * w;
+        const bool first = tau < 2.0f;
+        const float s = first ? tau - 1.0f : tau - 3.0f;
+        const float s2 = s * s;
+        const float inv = 1.0f / (1.0f + s2);
+        const float C = (1.0f - s2) * inv, S = (2.0f * s) * inv;
+        const float sa = first ? a : -a;
+        float p[3];
         for (int j = 0; j < 3; j++) p[j] = cc[j] + sa * (C * e1[j] + S * e2[j]);
-        double h, e;
+        float h, e;
         point_disk_he(p, cd, nd, b, h, e);
         ne++;
         if (h * h + e * e <= thr2) return true;
-        const double off = lo < 2.0 ? 1.0 : 3.0;
-        const double sl = lo - off, sr = (lo + w) - off;
-        const double m2 = (sl <= 0.0 && sr >= 0.0) ? 0.0 : (sl * sl < sr * sr ? sl * sl : sr * sr);
-        const double r = (a * (2.0 - m2)) * (0.5 * w);
-        double hl = fabs(h) - r * sn, el = e - r;
-        if (hl < 0.0) hl = 0.0;
-        if (el < 0.0) el = 0.0;
+        const float off = lo < 2.0f ? 1.0f : 3.0f;
+        const float sl = lo - off, sr = (lo + w) - off;
+        const float m2 = (sl <= 0.0f && sr >= 0.0f) ? 0.0f : (sl * sl < sr * sr ? sl * sl : sr * sr);
+        const float r = (a * (2.0f - m2)) * (0.5f * w);
+        float hl = fabsf(h) - r * sn, el = e - r;
+        if (hl < 0.0f) hl = 0.0f;
+        if (el < 0.0f) el = 0.0f;
         if (!(hl * hl + el * el > thr2)) {
             if (d == DEPTH || ne >= EVALS) return true;
             d++;
@@ -144,27 +152,34 @@ __device__ __noinline__ bool rim_near_disk(const double cc[3], const double e1[3
 }
 
 // Contact of two platelets with disk radius a and half-thickness t: dj =
-// centre of j minus centre of i (minimum image).  Bounding spheres, the two
+// centre of j minus centre of i (minimum image, binary64).  Evaluated in
+// binary32 on the rounded dj, normals and sizes against the threshold
+// 2 t + 2^-16 a (the widening exceeds every binary32 rounding of the test,
+// so a pair at distance <= 2 t is always found): bounding spheres, the two
 // slabs along the normals, then the rim of i against the disk of j and the
 // rim of j against the disk of i.
 __device__ __forceinline__ bool collide(const double dj[3], const double ni[3], const double nj[3], double a, double t)
 {
-    const double thr = t + t;
-    const double reach = (a + a) + thr;
-    if (dot3(dj, dj) > reach * reach) return false;
-    const double c = dot3(ni, nj);
-    double s2 = 1.0 - c * c;
-    if (s2 < 0.0) s2 = 0.0;
-    const double sn = sqrt(s2);
-    const double ext = a * sn;
-    if (fabs(dot3(dj, ni)) - ext > thr) return false;
-    if (fabs(dot3(dj, nj)) - ext > thr) return false;
-    double ei1[3], ei2[3], ej1[3], ej2[3];
-    const double zero[3] = {0.0, 0.0, 0.0};
-    basis(ni, ei1, ei2);
-    basis(nj, ej1, ej2);
-    if (rim_near_disk(zero, ei1, ei2, a, dj, nj, a, sn, thr)) return true;
-    return rim_near_disk(dj, ej1, ej2, a, zero, ni, a, sn, thr);
+    const float d[3] = {(float)dj[0], (float)dj[1], (float)dj[2]};
+    const float u[3] = {(float)ni[0], (float)ni[1], (float)ni[2]};
+    const float v[3] = {(float)nj[0], (float)nj[1], (float)nj[2]};
+    const float af = (float)a, tf = (float)t;
+    const float thr = (tf + tf) + af * SLACK;
+    const float reach = (af + af) + thr;
+    if (dot3f(d, d) > reach * reach) return false;
+    const float c = dot3f(u, v);
+    float s2 = 1.0f - c * c;
+    if (s2 < 0.0f) s2 = 0.0f;
+    const float sn = sqrtf(s2);
+    const float ext = af * sn;
+    if (fabsf(dot3f(d, u)) - ext > thr) return false;
+    if (fabsf(dot3f(d, v)) - ext > thr) return false;
+    float ei1[3], ei2[3], ej1[3], ej2[3];
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    basis(u, ei1, ei2);
+    basis(v, ej1, ej2);
+    if (rim_near_disk(zero, ei1, ei2, af, d, v, af, sn, thr)) return true;
+    return rim_near_disk(d, ej1, ej2, af, zero, u, af, sn, thr);
 }
 
 // Uniform direction of try l from stream tag (0: translation, the draw of
@@ -375,7 +390,9 @@ __device__ bool trial_collides(const PltDev &d, int32_t pid, const double q[3], 
 {
     int cnt = 0;
     bool hit = false;
-    const double reach = (d.a + d.a) + (d.t + d.t);
+    // a superset of the pairs that pass collide's first test (its threshold
+    // is widened by 2^-16 a and rounded to binary32)
+    const double reach = ((d.a + d.a) + (d.t + d.t)) * 1.001;
     const double reach2 = reach * reach;
     int32_t b0 = 0, e0 = 0;
     if (lane < 27) {
