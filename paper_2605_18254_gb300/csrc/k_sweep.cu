@@ -275,7 +275,7 @@ __device__ __forceinline__ void wait_lower_colours(RveDev *st, const uint32_t *c
             atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
             continue;
         }
-        for (int it = 0; ld_acquire(&st->done[c]) != epoch; it++) {
+        for (int it = 0; ld_relaxed(&st->done[c]) != epoch; it++) {
             if (it >= limit) {
                 atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
                 break;
@@ -283,9 +283,10 @@ __device__ __forceinline__ void wait_lower_colours(RveDev *st, const uint32_t *c
             __nanosleep(64);
         }
     }
-    // the producer's writes happen before its release store, which
-    // synchronises with this lane's acquire load; the warp barrier orders
-    // that load before every lane's later reads
+    // the producer's writes happen before its release store; this lane's
+    // relaxed loads that saw it, followed by the fence, synchronise with it;
+    // the warp barrier orders the fence before every lane's later reads
+    fence_acquire();
     __syncwarp();
 }
 

@@ -107,9 +107,12 @@ __device__ __forceinline__ void point_disk_he(const float p[3], const float cd[3
 // min s^2) >= 2 a / (1 + min s^2), the rim speed; r the half-width) exceeds
 // thr^2 is dropped; an interval still open at level 20 or after 4096
 // evaluations counts as a collision.  Binary32 throughout.
-__device__ __noinline__ bool rim_near_disk(const float cc[3], const float e1[3], const float e2[3], float a,
-                                           const float cd[3], const float nd[3], float b, float sn, float thr)
+__device__ __noinline__ bool rim_near_disk(const float3 cc3, const float3 e13, const float3 e23, float a,
+                                           const float3 cd3, const float3 nd3, float b, float sn, float thr)
 {
+    // by value: the geometry stays in registers through the bisection
+    const float cc[3] = {cc3.x, cc3.y, cc3.z}, e1[3] = {e13.x, e13.y, e13.z}, e2[3] = {e23.x, e23.y, e23.z};
+    const float cd[3] = {cd3.x, cd3.y, cd3.z}, nd[3] = {nd3.x, nd3.y, nd3.z};
     int d = TOP, ne = 0;
     int k = 0;
     const float thr2 = thr * thr;
@@ -178,8 +181,13 @@ __device__ __forceinline__ bool collide(const double dj[3], const double ni[3], 
     const float zero[3] = {0.0f, 0.0f, 0.0f};
     basis(u, ei1, ei2);
     basis(v, ej1, ej2);
-    if (rim_near_disk(zero, ei1, ei2, af, d, v, af, sn, thr)) return true;
-    return rim_near_disk(d, ej1, ej2, af, zero, u, af, sn, thr);
+    const float3 z3 = make_float3(zero[0], zero[1], zero[2]), d3 = make_float3(d[0], d[1], d[2]);
+    const float3 u3 = make_float3(u[0], u[1], u[2]), v3 = make_float3(v[0], v[1], v[2]);
+    if (rim_near_disk(z3, make_float3(ei1[0], ei1[1], ei1[2]), make_float3(ei2[0], ei2[1], ei2[2]), af, d3, v3, af,
+                      sn, thr))
+        return true;
+    return rim_near_disk(d3, make_float3(ej1[0], ej1[1], ej1[2]), make_float3(ej2[0], ej2[1], ej2[2]), af, z3, u3, af,
+                         sn, thr);
 }
 
 // Uniform direction of try l from stream tag (0: translation, the draw of
@@ -361,19 +369,22 @@ __device__ bool wait_lower(const PltDev &d, int cx, int cy, int cz, int chi, int
         if (nchi >= chi) continue;
         const uint32_t *st = &d.stamp[nx + d.n[0] * (ny + d.n[1] * nz)];
         int polls = 0;
-        while (ld_acquire(st) != d.epoch) {
+        while (ld_relaxed(st) != d.epoch) {
             if (d.wait_limit < 0 || ++polls > d.wait_limit) {
                 atomicExch(&d.ctr[1], (uint32_t)STATUS_WAIT_TIMEOUT);
                 ok = false;
                 break;
             }
-            if ((polls & 255) == 0 && ld_acquire(&d.ctr[1]) != 0u) {
+            if ((polls & 255) == 0 && ld_relaxed(&d.ctr[1]) != 0u) {
                 ok = false;
                 break;
             }
             __nanosleep(polls < 1024 ? 64 : 1000);
         }
     }
+    // relaxed loads that saw the release stores, then the fence: the
+    // cells' writes are visible to this lane, and after the vote to the warp
+    fence_acquire();
     return __all_sync(FULL, ok);
 }
 

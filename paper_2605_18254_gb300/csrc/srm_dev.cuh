@@ -125,6 +125,23 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Polling without acquire semantics, and the fence that completes an
+// acquire pattern once a relaxed load has seen the release store: a waiting
+// warp then orders its later reads once per dependency instead of on every
+// poll, so that the polls of waiting warps do not disturb the L1 contents
+// of the warps at work on the same SM.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acquire()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 // Largest r with off[r] <= x (off non-decreasing, off[0] = 0).
 __device__ __forceinline__ int find_seg(const int32_t *off, int B, int x)
 {
