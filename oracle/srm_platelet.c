@@ -44,9 +44,11 @@
  * sqrt(max(0, |h| - V r sin)^2 + max(0, e - V r)^2) bounds the distance
  * from below.  Intervals whose bound is above the threshold are dropped, a
  * midpoint at or below it is a collision (both compared as squares: h^2 +
- * e^2 <= thr^2).  An interval still undecided at 2^-20 of the circle, or
- * after 4096 evaluations of one rim, counts as a collision (a near-contact
- * the bisection cannot resolve is reported as contact).  Cheap exact
+ * e^2 <= thr^2).  Each of the 8 first-level arcs of a rim is bisected on
+ * its own; an arc still undecided at 2^-20 of the circle, or after 512
+ * evaluations, counts as a collision (a near-contact the bisection cannot
+ * resolve is reported as contact).  The arcs are independent, so the
+ * decision is the OR of 16 arc results (2 rims x 8 arcs) in any order.  Cheap exact
  * separations come first: the bounding spheres, and the two slabs along the
  * normals.
  *
@@ -70,7 +72,7 @@ void orc_grid(int dim, const double L[3], double lam, double rmax, double c_m, i
 
 #define PLT_TOP 3        /* first level evaluated: 8 intervals of the circle */
 #define PLT_DEPTH 20     /* finest level (binary32 still separates its midpoints) */
-#define PLT_EVALS 4096   /* evaluations per rim */
+#define PLT_EVALS 512    /* evaluations per level-3 interval (4096 per rim) */
 #define PLT_SLACK 0x1p-16f /* threshold widening, in units of the disk radius */
 
 static float dot3f(const float a[3], const float b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -154,17 +156,18 @@ static void rim_point(const float cc[3], const float e1[3], const float e2[3], f
     for (int k = 0; k < 3; k++) p[k] = cc[k] + sa * (C * e1[k] + S * e2[k]);
 }
 
-/* Is some point of the circle (cc, e1, e2, a) within thr of the disk (cd,
- * nd, b)?  sn = sine of the angle between the two normals.  Depth-first
- * bisection over tau, intervals [k w, (k+1) w) with w = 4 / 2^d, from the 8
- * intervals of level 3, left half first.  Returns 1 (yes or undecided) or 0
- * (every point is farther than thr); *evals receives the number of
- * midpoints evaluated. */
-static int rim_near_disk_f(const float cc[3], const float e1[3], const float e2[3], float a, const float cd[3],
-                           const float nd[3], float b, float sn, float thr, int *evals)
+/* Is some point of the arc tau in [k0/2, (k0+1)/2) (one of the 8 intervals
+ * of level 3) of the circle (cc, e1, e2, a) within thr of the disk (cd, nd,
+ * b)?  sn = sine of the angle between the two normals.  Depth-first
+ * bisection, intervals [k w, (k+1) w) with w = 4 / 2^d, left half first.
+ * Returns 1 (yes, or undecided at level 20 or after 512 evaluations) or 0;
+ * *evals receives the number of midpoints evaluated.  The 8 intervals are
+ * independent, so the answer for the whole rim is their OR in any order. */
+static int arc_near_disk_f(const float cc[3], const float e1[3], const float e2[3], float a, const float cd[3],
+                           const float nd[3], float b, float sn, float thr, int k0, int *evals)
 {
     int d = PLT_TOP, ne = 0;
-    int64_t k = 0;
+    int64_t k = k0;
     float thr2 = thr * thr;
     for (;;) {
         float w = ldexpf(4.0f, -d);
@@ -198,12 +201,31 @@ static int rim_near_disk_f(const float cc[3], const float e1[3], const float e2[
             k >>= 1;
             d--;
         }
-        k++;
-        if (d == PLT_TOP && k == 8) {
+        if (d == PLT_TOP) {
             if (evals) *evals = ne;
             return 0;
         }
+        k++;
     }
+}
+
+/* The whole rim: the 8 level-3 arcs in order, stopping at the first that
+ * reports contact; *evals receives the evaluations of the arcs visited. */
+static int rim_near_disk_f(const float cc[3], const float e1[3], const float e2[3], float a, const float cd[3],
+                           const float nd[3], float b, float sn, float thr, int *evals)
+{
+    int total = 0;
+    for (int k0 = 0; k0 < 8; k0++) {
+        int ne = 0;
+        int r = arc_near_disk_f(cc, e1, e2, a, cd, nd, b, sn, thr, k0, &ne);
+        total += ne;
+        if (r) {
+            if (evals) *evals = total;
+            return 1;
+        }
+    }
+    if (evals) *evals = total;
+    return 0;
 }
 
 int orc_plt_rim_near_disk(const double cc[3], const double e1[3], const double e2[3], double a,
