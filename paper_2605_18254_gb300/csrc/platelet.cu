@@ -37,7 +37,7 @@ namespace plt {
 
 constexpr int TOP = 3;                // first level evaluated: 8 intervals of the circle
 constexpr int DEPTH = 20;             // finest level (binary32 still separates its midpoints)
-constexpr int EVALS = 4096;           // evaluations per rim
+constexpr int EVALS = 512;            // evaluations per level-3 arc (4096 per rim)
 constexpr float SLACK = 0x1p-16f;     // threshold widening, in units of the disk radius
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -97,24 +97,24 @@ __device__ __forceinline__ void point_disk_he(const float p[3], const float cd[3
     e = rr <= b * b ? 0.0f : sqrtf(rr) - b;
 }
 
-// Is a point of the circle (centre cc, basis e1 e2, radius a) within thr of
-// the disk (cd, nd, b)?  sn: sine of the angle between the normals.  The
-// circle is parametrised by tau in [0, 4): s = tau - 1 on the first half,
-// ((1 - s^2) e1 + 2 s e2) / (1 + s^2), s = tau - 3 and the negated point on
-// the second.  Depth-first bisection from the 8 intervals of width 1/2, left
-// half first: a midpoint with h^2 + e^2 <= thr^2 is a collision; an interval
-// whose lower bound max(0, |h| - V r sn)^2 + max(0, e - V r)^2 (V = a (2 -
-// min s^2) >= 2 a / (1 + min s^2), the rim speed; r the half-width) exceeds
-// thr^2 is dropped; an interval still open at level 20 or after 4096
-// evaluations counts as a collision.  Binary32 throughout.
-__device__ __noinline__ bool rim_near_disk(const float3 cc3, const float3 e13, const float3 e23, float a,
-                                           const float3 cd3, const float3 nd3, float b, float sn, float thr)
+// Is a point of the arc tau in [k0/2, (k0+1)/2) (one of the 8 arcs of level
+// 3) of the circle (centre cc, basis e1 e2, radius a) within thr of the disk
+// (cd, nd, b)?  sn: sine of the angle between the normals.  The circle is
+// parametrised by tau in [0, 4): s = tau - 1 on the first half, ((1 - s^2)
+// e1 + 2 s e2) / (1 + s^2), s = tau - 3 and the negated point on the second.
+// Depth-first bisection, left half first: a midpoint with h^2 + e^2 <= thr^2
+// is a collision; an interval whose lower bound max(0, |h| - V r sn)^2 +
+// max(0, e - V r)^2 (V = a (2 - min s^2) >= 2 a / (1 + min s^2), the rim
+// speed; r the half-width) exceeds thr^2 is dropped; an interval still open
+// at level 20, or after 512 evaluations of the arc, counts as a collision.
+// Binary32 throughout; the geometry is passed by value (registers).
+__device__ __noinline__ bool arc_near_disk(const float3 cc3, const float3 e13, const float3 e23, float a,
+                                           const float3 cd3, const float3 nd3, float b, float sn, float thr, int k0)
 {
-    // by value: the geometry stays in registers through the bisection
     const float cc[3] = {cc3.x, cc3.y, cc3.z}, e1[3] = {e13.x, e13.y, e13.z}, e2[3] = {e23.x, e23.y, e23.z};
     const float cd[3] = {cd3.x, cd3.y, cd3.z}, nd[3] = {nd3.x, nd3.y, nd3.z};
     int d = TOP, ne = 0;
-    int k = 0;
+    int k = k0;
     const float thr2 = thr * thr;
     for (;;) {
         const float w = __int_as_float((127 + 2 - d) << 23);  // 4 / 2^d
@@ -149,19 +149,31 @@ __device__ __noinline__ bool rim_near_disk(const float3 cc3, const float3 e13, c
             k >>= 1;
             d--;
         }
+        if (d == TOP) return false;
         k++;
-        if (d == TOP && k == 8) return false;
     }
 }
 
-// Contact of two platelets with disk radius a and half-thickness t: dj =
-// centre of j minus centre of i (minimum image, binary64).  Evaluated in
-// binary32 on the rounded dj, normals and sizes against the threshold
-// 2 t + 2^-16 a (the widening exceeds every binary32 rounding of the test,
-// so a pair at distance <= 2 t is always found): bounding spheres, the two
-// slabs along the normals, then the rim of i against the disk of j and the
-// rim of j against the disk of i.
-__device__ __forceinline__ bool collide(const double dj[3], const double ni[3], const double nj[3], double a, double t)
+// The whole rim: its 8 arcs, stopping at the first that reports contact.
+__device__ __forceinline__ bool rim_near_disk(const float3 cc, const float3 e1, const float3 e2, float a,
+                                              const float3 cd, const float3 nd, float b, float sn, float thr)
+{
+    for (int k0 = 0; k0 < 8; k0++)
+        if (arc_near_disk(cc, e1, e2, a, cd, nd, b, sn, thr, k0)) return true;
+    return false;
+}
+
+// The binary32 part of a pair test up to the rims: rounded centre
+// difference d and normals, widened threshold, bounding spheres and the two
+// slabs.  Returns false if these separate the pair, else fills the inputs of
+// the rim tests.
+struct PairGeom {
+    float3 d, u, v;
+    float af, sn, thr;
+};
+
+__device__ __forceinline__ bool pair_pretest(const double dj[3], const double ni[3], const double nj[3], double a,
+                                             double t, PairGeom &g)
 {
     const float d[3] = {(float)dj[0], (float)dj[1], (float)dj[2]};
     const float u[3] = {(float)ni[0], (float)ni[1], (float)ni[2]};
@@ -177,17 +189,43 @@ __device__ __forceinline__ bool collide(const double dj[3], const double ni[3], 
     const float ext = af * sn;
     if (fabsf(dot3f(d, u)) - ext > thr) return false;
     if (fabsf(dot3f(d, v)) - ext > thr) return false;
-    float ei1[3], ei2[3], ej1[3], ej2[3];
-    const float zero[3] = {0.0f, 0.0f, 0.0f};
-    basis(u, ei1, ei2);
-    basis(v, ej1, ej2);
-    const float3 z3 = make_float3(zero[0], zero[1], zero[2]), d3 = make_float3(d[0], d[1], d[2]);
-    const float3 u3 = make_float3(u[0], u[1], u[2]), v3 = make_float3(v[0], v[1], v[2]);
-    if (rim_near_disk(z3, make_float3(ei1[0], ei1[1], ei1[2]), make_float3(ei2[0], ei2[1], ei2[2]), af, d3, v3, af,
-                      sn, thr))
-        return true;
-    return rim_near_disk(d3, make_float3(ej1[0], ej1[1], ej1[2]), make_float3(ej2[0], ej2[1], ej2[2]), af, z3, u3, af,
-                         sn, thr);
+    g.d = make_float3(d[0], d[1], d[2]);
+    g.u = make_float3(u[0], u[1], u[2]);
+    g.v = make_float3(v[0], v[1], v[2]);
+    g.af = af;
+    g.sn = sn;
+    g.thr = thr;
+    return true;
+}
+
+// Arc k0 of rim `which` (0: the rim of i against the disk of j; 1: the rim
+// of j against the disk of i) of a pair that passed the pre-tests.
+__device__ __forceinline__ bool pair_arc(const PairGeom &g, int which, int k0)
+{
+    const float n[3] = {which ? g.v.x : g.u.x, which ? g.v.y : g.u.y, which ? g.v.z : g.u.z};
+    float e1[3], e2[3];
+    basis(n, e1, e2);
+    const float3 zero = make_float3(0.0f, 0.0f, 0.0f);
+    const float3 b1 = make_float3(e1[0], e1[1], e1[2]), b2 = make_float3(e2[0], e2[1], e2[2]);
+    if (which == 0) return arc_near_disk(zero, b1, b2, g.af, g.d, g.v, g.af, g.sn, g.thr, k0);
+    return arc_near_disk(g.d, b1, b2, g.af, zero, g.u, g.af, g.sn, g.thr, k0);
+}
+
+// Contact of two platelets with disk radius a and half-thickness t: dj =
+// centre of j minus centre of i (minimum image, binary64).  Evaluated in
+// binary32 on the rounded dj, normals and sizes against the threshold
+// 2 t + 2^-16 a (the widening exceeds every binary32 rounding of the test,
+// so a pair at distance <= 2 t is always found): bounding spheres, the two
+// slabs along the normals, then the rim of i against the disk of j and the
+// rim of j against the disk of i (the OR of their 16 arcs).
+__device__ __forceinline__ bool collide(const double dj[3], const double ni[3], const double nj[3], double a, double t)
+{
+    PairGeom g;
+    if (!pair_pretest(dj, ni, nj, a, t, g)) return false;
+    for (int which = 0; which < 2; which++)
+        for (int k0 = 0; k0 < 8; k0++)
+            if (pair_arc(g, which, k0)) return true;
+    return false;
 }
 
 // Uniform direction of try l from stream tag (0: translation, the draw of
@@ -388,24 +426,35 @@ __device__ bool wait_lower(const PltDev &d, int cx, int cy, int cz, int chi, int
     return __all_sync(FULL, ok);
 }
 
-constexpr int SLOT = 16;  // candidates a lane stages per trial (more are tested in place)
+constexpr int SLOT = 16;   // candidates a lane stages per trial (more are tested in place)
+constexpr int PAIRS = 64;  // pairs per trial queued for the rim tests (more are tested in place)
+
+struct WarpScratch {
+    int32_t slot[27 * SLOT];
+    int32_t flat[27 * SLOT];
+    PairGeom pair[PAIRS];
+    int npair;
+};
 
 // Is the trial (q, u) of platelet pid clear of every platelet listed in the
-// 27 cells around q's cell?  Lanes 0..26 scan one cell each and stage the
-// platelets inside bounding-sphere reach; the staged pairs are then decided
-// by all 32 lanes, 32 at a time, stopping at the first collision.  A lane
-// with more than SLOT candidates decides the rest itself.  Returns the same
-// answer on every lane.
+// 27 cells around q's cell?  Three phases, each spread over the lanes:
+// lanes 0..26 scan one cell each and stage the platelets within
+// bounding-sphere reach; the staged candidates get the binary32 pre-tests
+// (bounding spheres, slabs) and those not separated are queued; the queued
+// pairs' 16 arcs each (2 rims x 8 first-level arcs) are bisected one per
+// lane, stopping at the first contact.  Overflowing stages and queues are
+// tested in place by the lane that holds them.  The answer is the OR of the
+// same pair decisions as the reference, on every lane.
 __device__ bool trial_collides(const PltDev &d, int32_t pid, const double q[3], const double u[3], int lane,
-                               int32_t *slot, int32_t *flat)
+                               WarpScratch &ws)
 {
     int cnt = 0;
     bool hit = false;
-    // a superset of the pairs that pass collide's first test (its threshold
+    // a superset of the pairs that pass the first pre-test (its threshold
     // is widened by 2^-16 a and rounded to binary32)
     const double reach = ((d.a + d.a) + (d.t + d.t)) * 1.001;
     const double reach2 = reach * reach;
-    int32_t b0 = 0, e0 = 0;
+    if (lane == 0) ws.npair = 0;
     if (lane < 27) {
         int32_t qc[3];
         cell_of_point(d, q, qc);
@@ -413,9 +462,8 @@ __device__ bool trial_collides(const PltDev &d, int32_t pid, const double q[3], 
         const int ny = wrapc(qc[1] + (lane / 3) % 3 - 1, d.n[1]);
         const int nz = wrapc(qc[2] + lane / 9 - 1, d.n[2]);
         const int nc = nx + d.n[0] * (ny + d.n[1] * nz);
-        b0 = d.start[nc];
-        e0 = d.start[nc + 1];
-        for (int32_t j = b0; j < e0; j++) {
+        const int32_t e0 = d.start[nc + 1];
+        for (int32_t j = d.start[nc]; j < e0; j++) {
             const int32_t tj = d.members[j];
             if (tj == pid) continue;
             const double4_32a xt = d.X[tj];
@@ -423,7 +471,7 @@ __device__ bool trial_collides(const PltDev &d, int32_t pid, const double q[3], 
             min_image(d, xt, q, dj);
             if (dot3(dj, dj) > reach2) continue;
             if (cnt < SLOT) {
-                slot[lane * SLOT + cnt] = tj;
+                ws.slot[lane * SLOT + cnt] = tj;
                 cnt++;
             } else if (!hit) {
                 const double4_32a ut = d.U[tj];
@@ -432,27 +480,41 @@ __device__ bool trial_collides(const PltDev &d, int32_t pid, const double q[3], 
             }
         }
     }
-    // flatten the staged candidates
     int incl = cnt;
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(FULL, incl, o);
         if (lane >= o) incl += y;
     }
     const int total = __shfl_sync(FULL, incl, 31);
-    for (int i = 0; i < cnt; i++) flat[incl - cnt + i] = slot[lane * SLOT + i];
+    for (int i = 0; i < cnt; i++) ws.flat[incl - cnt + i] = ws.slot[lane * SLOT + i];
     __syncwarp();
-    bool found = __any_sync(FULL, hit);
-    for (int r0 = 0; r0 < total && !found; r0 += 32) {
-        const int i = r0 + lane;
-        bool h = false;
-        if (i < total) {
-            const int32_t tj = flat[i];
-            const double4_32a xt = d.X[tj], ut = d.U[tj];
-            double dj[3];
-            min_image(d, xt, q, dj);
-            const double nt[3] = {ut.x, ut.y, ut.z};
-            h = collide(dj, u, nt, d.a, d.t);
+    if (__any_sync(FULL, hit)) return true;
+    // pre-tests, queueing the pairs that need their rims
+    for (int i = lane; i < total && !hit; i += 32) {
+        const int32_t tj = ws.flat[i];
+        const double4_32a xt = d.X[tj], ut = d.U[tj];
+        double dj[3];
+        min_image(d, xt, q, dj);
+        const double nt[3] = {ut.x, ut.y, ut.z};
+        PairGeom g;
+        if (!pair_pretest(dj, u, nt, d.a, d.t, g)) continue;
+        const int slot = atomicAdd(&ws.npair, 1);
+        if (slot < PAIRS) {
+            ws.pair[slot] = g;
+        } else {
+            for (int which = 0; which < 2 && !hit; which++)
+                for (int k0 = 0; k0 < 8 && !hit; k0++) hit = pair_arc(g, which, k0);
         }
+    }
+    __syncwarp();
+    if (__any_sync(FULL, hit)) return true;
+    const int np = ws.npair < PAIRS ? ws.npair : PAIRS;
+    const int tasks = 16 * np;
+    bool found = false;
+    for (int r0 = 0; r0 < tasks && !found; r0 += 32) {
+        const int tsk = r0 + lane;
+        bool h = false;
+        if (tsk < tasks) h = pair_arc(ws.pair[tsk >> 4], (tsk >> 3) & 1, tsk & 7);
         found = __any_sync(FULL, h);
     }
     __syncwarp();
@@ -462,8 +524,7 @@ __device__ bool trial_collides(const PltDev &d, int32_t pid, const double q[3], 
 // One sweep of Algorithm 3 over the cells in canonical colour order.
 __global__ void __launch_bounds__(128) k_psweep(PltDev d)
 {
-    __shared__ int32_t s_slot[4][27 * SLOT];
-    __shared__ int32_t s_flat[4][27 * SLOT];
+    __shared__ WarpScratch s_ws[4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int S0 = d.n[0] / 3, S1 = d.n[1] / 3, S2 = d.n[2] / 3;
     const int per = S0 * S1 * S2;
@@ -487,7 +548,7 @@ __global__ void __launch_bounds__(128) k_psweep(PltDev d)
             for (int l = 0; l < d.N_l; l++) {
                 double q[3], u[3];
                 trial(d, (uint64_t)pid, (uint64_t)l, x0, u0, q, u);
-                if (!trial_collides(d, pid, q, u, lane, s_slot[wib], s_flat[wib])) {
+                if (!trial_collides(d, pid, q, u, lane, s_ws[wib])) {
                     if (lane == 0) {
                         double4_32a nx4, nu4;
                         nx4.x = q[0];
