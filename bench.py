@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -83,7 +84,9 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # samples of the timed region; SRM_CLOCKS_DIR keeps them where a caller wants them
+        base = os.environ.get("SRM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(base, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -1,6 +1,6 @@
 /*
  * srm_analysis.c -- FP64 reference of the structure descriptors used to
- * judge generated microstructures (Section 3.2: nearest-neighbour distance
+ * assess generated microstructures (Section 3.2: nearest-neighbour distance
  * distributions, Fig. 4d; local volume fraction = particle area or volume
  * over the area or volume of its Voronoi cell, Figs. 5 and 7) and the radial
  * distribution function of the centres.  TEST INFRASTRUCTURE ONLY: plain
