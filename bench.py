@@ -744,19 +744,26 @@ def run_platelets(args, rank, world, local_rank):
                     ok=bool(info["converged"]) and cnt == 0 and abs(st["rho"] - w.rho_t) < 1e-9,
                     launches=5 * (sweeps + checks), relax_acc=acc, rho=st["rho"])
 
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
     for _ in range(args.warmup):
         one_step()
     res = []
+    if dist:
+        dist.barrier()
     with ClockSampler(local_rank) as clk:
         for _ in range(args.steps):
             res.append(one_step())
     dev = sum(r["dev_s"] for r in res)
     e2e = sum(r["e2e_s"] for r in res)
     upd = sum(r["upd"] for r in res)
+    # replicas: the slowest rank's times, the updates of all ranks
+    dev, e2e, upd = combine_ranks(dev, e2e, upd, dist, torch.device("cuda", local_rank))
     if rank != 0:
         return
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         import oracle
         o = oracle.PlateletSystem(w.box, w.x, w.u, w.a0, w.t0, lam=w.lambda0, lam_t=1.0, c_w=w.c_w, c_m=w.c_m,
                                   c_r=w.c_r, seed=w.seed)

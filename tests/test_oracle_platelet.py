@@ -411,3 +411,26 @@ def test_iterations_keep_p_collision_free_and_reach_density():
         if s.lam < lam_t:
             assert s.lam == pytest.approx(1.15 ** m, rel=1e-13)
     assert s.lam == lam_t
+
+
+def test_rejected_swell_is_discarded_and_p_shaken():
+    """Two coaxial platelets whose gap one swell step closes, with steps far
+    too short to reopen it: every round of the N_k loop leaves them in
+    contact, the swollen state is discarded, P (at the old scale) is swept
+    N_shake times, the scale stays and P stays collision-free (Alg 1)."""
+    a0, t0 = 0.1, 0.01
+    n = np.array([0.0, 0.0, 1.0])
+    x = np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 1.0 + 2 * t0 * 1.005]])
+    u = np.stack([n, n])
+    s = oracle.PlateletSystem((2.0, 2.0, 2.0), x, u, a0, t0, lam=1.0, lam_t=2.0, c_w=0.01, c_m=1e-7, c_r=0.0,
+                              N_k=4, N_l=3, N_shake=5, seed=3)
+    acc, info = s.iterate()
+    assert acc == 0
+    assert info == dict(k_sweeps=4, overlapping=2, shake_sweeps=5)
+    assert s.lam == 1.0 and s.sweep_counter == 4 + 5
+    assert s.counters()["shaken"] == 1
+    _, npairs = s.pairs_brute()
+    assert npairs == 0
+    X, U = s.state()
+    np.testing.assert_array_equal(U, u)  # no rotation with c_r = 0
+    assert np.all(np.abs(X - x) <= 5 * 1e-7 + 1e-15)  # each sweep moves a platelet at most c_m
