@@ -147,7 +147,7 @@ srm_status srm_plt_state(srm_plt *h, double *x, double *u, double *lambda, doubl
  * dj[3k..3k+2] (minimum image already taken), unit normals ni and nj, disk
  * radius a and half-thickness t for both.  out[k] = 1 if they collide.
  * Host arrays; runs on the given stream with its own temporary buffers.
- * SRM_E_ARG for m < 0, a <= 0 or t <= 0. */
+ * SRM_E_ARG for m outside [0, 2^31), a <= 0 or t <= 0. */
 srm_status srm_plt_collide_pairs(const double *dj, const double *ni, const double *nj, int64_t m, double a,
                                  double t, uint8_t *out, void *cuda_stream);
 

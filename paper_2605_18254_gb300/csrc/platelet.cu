@@ -696,7 +696,7 @@ void dfree(srm_plt *h, void *p)
 srm_status ensure_cells(srm_plt *h, int64_t ncells)
 {
     if (ncells <= h->ncells_cap) return SRM_OK;
-    if (ncells > 0x7fffffffLL - 1) return fail(SRM_E_ARG, "cell grid too fine");
+    if (ncells > (1LL << 30)) return fail(SRM_E_ARG, "cell grid too fine (more than 2^30 cells)");
     dfree(h, h->count);
     dfree(h, h->start);
     dfree(h, h->stamp);
@@ -1057,7 +1057,8 @@ srm_status srm_plt_state(srm_plt *h, double *x, double *u, double *lambda, doubl
 srm_status srm_plt_collide_pairs(const double *dj, const double *ni, const double *nj, int64_t m, double a,
                                  double t, uint8_t *out, void *cuda_stream)
 {
-    if (m < 0 || !(a > 0.0) || !(t > 0.0)) return fail(SRM_E_ARG, "m >= 0, a > 0, t > 0");
+    if (m < 0 || m > 0x7fffffffLL || !(a > 0.0) || !(t > 0.0))
+        return fail(SRM_E_ARG, "0 <= m < 2^31, a > 0, t > 0");
     if (m == 0) return SRM_OK;
     if (!dj || !ni || !nj || !out) return fail(SRM_E_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)cuda_stream;
