@@ -733,6 +733,15 @@ def run_platelets(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     x_host = torch.from_numpy(np.ascontiguousarray(w.x)).pin_memory()
     u_host = torch.from_numpy(np.ascontiguousarray(w.u)).pin_memory()
+    last = {}
+
+    def alignment(x, u):
+        """Mean |n_i . n_j| over pairs of centres closer than D (1/2 for
+        independent uniform orientations): the local order that relaxation
+        grows (Section 3.3, Fig. 8)."""
+        from scipy.spatial import cKDTree
+        p = cKDTree(x, boxsize=np.asarray(w.box)).query_pairs(D, output_type="ndarray")
+        return float(np.mean(np.abs(np.sum(u[p[:, 0]] * u[p[:, 1]], axis=1))))
 
     def one_step():
         flush.fill_(1)
@@ -752,6 +761,7 @@ def run_platelets(args, rank, world, local_rank):
         e[4].record(stream)
         torch.cuda.synchronize()
         g.close()
+        last["relaxed"] = (x, u)
         sweeps = info["sweeps"] + relax
         checks = info["sweeps"] - info["shaken"] * 10 + 1
         return dict(dev_s=e[1].elapsed_time(e[3]) / 1e3, gen_s=e[1].elapsed_time(e[2]) / 1e3,
@@ -793,6 +803,14 @@ def run_platelets(args, rank, world, local_rank):
                          f"{dt:.1f} s, single-threaded reference: binary64 state, binary32 contact test, reaching rho = "
                          f"{w.rho_t * o.lam ** 3:.2f}; the early sweeps are the cheapest ones)"}
     r0 = res[0]
+    # neighbour alignment of the house of cards (a generation alone) and after the relaxation
+    g = srm.Platelets(w.box, w.x, w.u, w.a0, w.t0, w.lambda0, 1.0, w.seed, c_w=w.c_w, c_m=w.c_m, c_r=w.c_r,
+                      stream=stream.cuda_stream)
+    g.run_to_target(4000)
+    hx, hu, _ = g.state()
+    g.close()
+    order = {"house_of_cards": alignment(hx, hu), "relaxed": alignment(*last["relaxed"]),
+             "measure": "mean |n_i . n_j| over pairs of centres closer than D; 0.5 for random orientations"}
     line = {
         "metric": "platelet-updates/s and time to the target number density (Section 3.3)",
         "value": upd / dev, "unit": "particle-updates/s", "n_gpus": world, "steps": args.steps,
@@ -807,7 +825,7 @@ def run_platelets(args, rank, world, local_rank):
         "time_to_target_s": sum(r["gen_s"] for r in res) / args.steps,
         "relaxation_s": sum(r["relax_s"] for r in res) / args.steps,
         "sweeps_per_step": r0["sweeps"], "iterations": r0["iters"], "shaken": r0["shaken"],
-        "certified": all(r["ok"] for r in res),
+        "certified": all(r["ok"] for r in res), "alignment": order,
         "e2e": {"value": upd / e2e, "unit": "particle-updates/s",
                 "h2d_bytes_per_step": int(2 * w.n * 3 * 8), "d2h_bytes_per_step": int(2 * w.n * 3 * 8 + w.n)},
         "cpu_baseline": cpu,
