@@ -25,13 +25,17 @@ def lvf_spread(c_w, c_m_rel, seed, n=2000, phi=0.5):
     assert abs(s.phi() - phi) < 1e-12
     assert oracle.certify(2, (1.0, 1.0), X, R)[0] == 0
     _, lvf = oracle.voronoi_lvf(2, (1.0, 1.0), X, R, (200, 200))
-    return float(np.std(lvf))
+    _, _, gap = oracle.nn(2, (1.0, 1.0), X, R)
+    return float(np.std(lvf)), float(np.mean(gap)) / (2.0 * float(R[0]))
 
 
 def test_clustered_regime_spreads_local_volume_fraction():
-    eq = np.mean([lvf_spread(0.002, 0.5, s) for s in (1, 2)])
-    cl = np.mean([lvf_spread(0.01, 0.03, s) for s in (1, 2)])
-    assert cl > 1.4 * eq, (cl, eq)
+    """LVF spread (Fig. 5) and the nearest-neighbour gaps (Fig. 4d: the
+    clustered configuration has its neighbours closer)."""
+    eq = np.mean([lvf_spread(0.002, 0.5, s) for s in (1, 2)], axis=0)
+    cl = np.mean([lvf_spread(0.01, 0.03, s) for s in (1, 2)], axis=0)
+    assert cl[0] > 1.4 * eq[0], (cl, eq)
+    assert cl[1] < 0.7 * eq[1], (cl, eq)
 
 
 def dense_run(dim, n, phi, seed, c_w, c_m_rel, cap_s=120.0):
