@@ -15,9 +15,9 @@
  * Contact.  Two platelets collide when the distance between their disks is
  * at most t_i + t_j.  The library decides this on the rims of the two disks
  * (the distance between two disks is reached at a rim point of one of them)
- * by bisection with a certified lower bound; a near-contact that the
- * bisection cannot resolve within 2^-20 of the circle or 4096 evaluations per
- * rim counts as contact.  Cheap exact separations come first (bounding
+ * by bisection with a certified lower bound, each of a rim's 8 first-level
+ * arcs on its own; a near-contact that the bisection cannot resolve within
+ * 2^-20 of the circle or 512 evaluations of an arc counts as contact.  Cheap exact separations come first (bounding
  * spheres, slabs along the two normals).  The test runs in binary32 on the
  * pair's relative geometry (centre difference formed in binary64 under the
  * minimum image, then rounded) against the threshold t_i + t_j + 2^-16 a:
