@@ -468,3 +468,17 @@ def test_relaxation_aligns_neighbours():
     relaxed = neighbour_alignment(X, U, D)
     assert abs(hoc - 0.5) < 0.03, hoc
     assert relaxed > hoc + 0.06, (hoc, relaxed)
+
+
+def test_decision_monotone_in_threshold():
+    """A larger half-thickness never turns a contact into a separation: the
+    bisection prunes fewer intervals and keeps every hit (the flip-threshold
+    bisection of the pins above relies on this)."""
+    rng = np.random.default_rng(31)
+    ts = np.geomspace(1e-4, 0.3, 25)
+    for _ in range(150):
+        ni, nj = rand_units(rng, 2)
+        dj = rng.normal(size=3)
+        dj *= rng.uniform(0.0, 2.4) / np.linalg.norm(dj)
+        got = [oracle.plt_collide(dj, ni, nj, 1.0, t) for t in ts]
+        assert all(a <= b for a, b in zip(got, got[1:])), got
