@@ -359,17 +359,19 @@ void srm_batch_destroy(srm_batch *b);
  * Certification without device allocation.
  *
  * The paper has no counterpart to this call: it exists for callers that may
- * not allocate device memory at all -- code running inside someone else's
- * CUDA graph capture or memory pool budget, plug-ins of a host application
- * that owns every device allocation, real-time paths where an allocation
- * could block or fail.  Such a caller keeps the configuration in its own
- * device buffers and passes them in; the call computes the same binary64
- * certification as srm_certify (colliding pairs i < j by index, and the
- * smallest gap S - (R_i + R_j) over pairs in neighbouring cells of a grid
- * with cells at least 2 R_max wide), with all working memory in one static
- * device array of the library (about 1.9 MB, held by every GPU that loads
- * the library until the process exits).  It calls no cudaMalloc, cudaFree
- * or allocating library routine.
+ * not allocate device memory at all -- plug-ins of a host application that
+ * owns every device allocation (its own pool or a fixed arena, so a
+ * cudaMalloc from a library would bypass its accounting), code that runs
+ * under a fixed device-memory budget where a new allocation could fail,
+ * and latency-bound paths where an allocation could block.  Such a caller
+ * keeps the configuration in its own device buffers and passes them in; the
+ * call computes the same binary64 certification as srm_certify (colliding
+ * pairs i < j by index, and the smallest gap S - (R_i + R_j) over pairs in
+ * neighbouring cells of a grid with cells at least 2 R_max wide), with all
+ * working memory in one static device array of the library (1,966,592
+ * bytes = 1.97 MB = 1.88 MiB, held by every GPU that loads the library until
+ * the process exits).  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
  *
  * dim: 2 or 3; box: L[0..dim); n: particles, 1 <= n <= 32768
  * (SRM_NOALLOC_MAX_PARTICLES, larger n is rejected with SRM_E_ARG); xyz:
@@ -377,7 +379,9 @@ void srm_batch_destroy(srm_batch *b);
  * radii: device pointer to n binary64 radii; overlap_pairs, min_gap: host
  * pointers receiving the results; cuda_stream: stream to run on (NULL: the
  * legacy default stream), synchronised before returning.  Boxes narrower
- * than 4 R_max on some axis are rejected (SRM_E_ARG).
+ * than 4 R_max on some axis, and radii that are negative, infinite or NaN,
+ * are rejected (SRM_E_ARG).  A CUDA error already pending on the calling
+ * thread when the call starts is reported (SRM_E_CUDA) and left pending.
  *
  * The first call on a device looks up the device address of the static
  * array (cudaGetSymbolAddress) with that device current; make that first

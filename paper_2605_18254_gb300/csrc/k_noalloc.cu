@@ -35,12 +35,15 @@ struct NaHeader {
     unsigned long long gap_key;  // order-preserving key of the smallest gap
     int32_t n[3];
     int32_t ncells;
-    int32_t error;               // 1: box narrower than 4 R_max on some axis
+    int32_t error;               // 1: box narrower than 4 R_max on some axis;
+                                 // 2: a radius that is negative, infinite or NaN
     int32_t pad;
     double w[3];
 };
 
-// The working memory of every call on this device (about 1.8 MB).
+// The working memory of every call on this device: 1,966,592 bytes (1.97 MB,
+// 1.88 MiB), the figure include/srm.h states.
+static_assert(NaLayout::total == 1966592, "scratch size changed: update the figure in include/srm.h");
 static __device__ __align__(256) unsigned char g_na_scratch[NaLayout::total];
 
 struct NaView {
@@ -69,8 +72,18 @@ __global__ void __launch_bounds__(1024) k_na_setup(unsigned char *base, int dim,
 {
     NaView v = na_view(base);
     __shared__ double smax[32];
+    __shared__ int bad_sh;
+    if (threadIdx.x == 0) bad_sh = 0;
+    __syncthreads();
     double m = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, R[i]);
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double r = R[i];
+        // fmax would skip a NaN and leave R_max too small for the grid
+        if (!(r >= 0.0) || isinf(r)) bad = 1;
+        else m = fmax(m, r);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) bad_sh = 1;
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
     __syncthreads();
@@ -96,7 +109,7 @@ __global__ void __launch_bounds__(1024) k_na_setup(unsigned char *base, int dim,
             nc *= (int)k;
         }
         v.h->ncells = nc;
-        v.h->error = err;
+        v.h->error = bad_sh ? 2 : err;
         v.h->pairs = 0ull;
         v.h->gap_key = srm::dkey(__longlong_as_double(0x7ff0000000000000LL));
         nc_sh = nc;
@@ -255,20 +268,50 @@ extern "C" srm_status srm_certify_noalloc(int32_t dim, const double box[3], int6
         }
         base = static_cast<unsigned char *>(g_na_ptr[dev]);
     }
+    // An error left by earlier work on this thread is reported as such and
+    // left pending for its owner (cudaPeekAtLastError does not clear it);
+    // the checks after each launch below then see this call's own errors.
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return fail(SRM_E_CUDA, std::string("a CUDA error from earlier work on this thread is pending: ") +
+                                    cudaGetErrorString(pending));
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const double L[3] = {box[0], box[1], dim == 3 ? box[2] : 1.0};
     const int nn = (int)n, nb = (nn + 255) / 256;
+    cudaError_t e = cudaSuccess;
+    auto launched = [&e](const char *name) {
+        if (e != cudaSuccess) return;
+        const cudaError_t x = cudaGetLastError();
+        if (x != cudaSuccess) {
+            e = x;
+            srm::set_last_error(std::string("launch of ") + name + ": " + cudaGetErrorString(x));
+        }
+    };
     k_na_setup<<<1, 1024, 0, s>>>(base, dim, L[0], L[1], L[2], nn, radii);
-    k_na_count<<<nb, 256, 0, s>>>(base, dim, nn, xyz);
-    k_na_scan<<<1, 1024, 0, s>>>(base);
-    k_na_scatter<<<nb, 256, 0, s>>>(base, dim, nn, xyz, radii);
-    if (dim == 2) k_na_pairs<2><<<nb, 256, 0, s>>>(base, nn, L[0], L[1], L[2]);
-    else k_na_pairs<3><<<nb, 256, 0, s>>>(base, nn, L[0], L[1], L[2]);
-    cudaError_t e = cudaGetLastError();
+    launched("k_na_setup");
+    if (e == cudaSuccess) {
+        k_na_count<<<nb, 256, 0, s>>>(base, dim, nn, xyz);
+        launched("k_na_count");
+    }
+    if (e == cudaSuccess) {
+        k_na_scan<<<1, 1024, 0, s>>>(base);
+        launched("k_na_scan");
+    }
+    if (e == cudaSuccess) {
+        k_na_scatter<<<nb, 256, 0, s>>>(base, dim, nn, xyz, radii);
+        launched("k_na_scatter");
+    }
+    if (e == cudaSuccess) {
+        if (dim == 2) k_na_pairs<2><<<nb, 256, 0, s>>>(base, nn, L[0], L[1], L[2]);
+        else k_na_pairs<3><<<nb, 256, 0, s>>>(base, nn, L[0], L[1], L[2]);
+        launched("k_na_pairs");
+    }
+    if (e != cudaSuccess) return SRM_E_CUDA;  // message set by `launched`
     NaHeader hdr;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hdr, base + NaLayout::hdr, sizeof(hdr), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(SRM_E_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    if (hdr.error == 2) return fail(SRM_E_ARG, "radii must be finite and non-negative");
     if (hdr.error) return fail(SRM_E_ARG, "box narrower than 4 R_max on some axis");
     const unsigned long long key = hdr.gap_key;
     const unsigned long long b = (key >> 63) ? (key & 0x7fffffffffffffffULL) : ~key;

@@ -1,16 +1,19 @@
 """srm_certify_noalloc, the certification for callers that cannot allocate
-device memory (code inside another library's graph capture or memory
-budget, host applications that own every device allocation).  The call takes
-the caller's device buffers and keeps its working memory in a static device
-array of the library.  Here it is called through the C interface on two
-calls in a row and must give exactly the results of srm_certify on the same
-configuration: the same binary64 predicate on the same values, over grids
-that both contain every pair closer than 2 R_max (which holds the smallest
-gap in the dense and overlapping states used).  This file is collected last
-so that a failure here leaves every other test already run."""
+device memory (plug-ins of a host application that owns every device
+allocation, code under a fixed device-memory budget, latency-bound paths
+where an allocation could block).  The call takes the caller's device
+buffers and keeps its working memory in a static device array of the
+library.  Here it is called through the C interface on two calls in a row
+and must give exactly the results of srm_certify on the same configuration,
+and of the reference's O(N^2) brute force: the same binary64 predicate on
+the same values, over grids that both contain every pair closer than 2 R_max
+(which holds the smallest gap in the dense and overlapping states used).
+This file is collected last so that a failure here leaves every other test
+already run."""
 import numpy as np
 import pytest
 
+import oracle
 import srm_inputs
 import paper_2605_18254_gb300 as srm
 
@@ -27,6 +30,9 @@ def _certify_both(g, w, stream):
     out = []
     for _ in range(2):  # two calls in a row share the static working memory
         out.append(srm.srm_certify_noalloc(w.dim, w.box, w.n, xd.data_ptr(), rd.data_ptr(), stream))
+    # the reference's brute force over all pairs (pair count and smallest gap)
+    _, bf_pairs, bf_gap = oracle.pairs_brute(w.dim, w.box, x, R)
+    assert (bf_pairs, bf_gap) == (ref_pairs, ref_gap)
     return (ref_pairs, ref_gap), out
 
 
@@ -60,3 +66,20 @@ def test_noalloc_rejects_beyond_maximum():
     with pytest.raises(srm.SrmError) as e:
         srm.srm_certify_noalloc(3, (1.0, 1.0, 1.0), n, xd.data_ptr(), rd.data_ptr())
     assert e.value.status == 1 and "SRM_NOALLOC_MAX_PARTICLES" in e.value.message
+
+
+def test_noalloc_rejects_nan_radius():
+    import torch
+    w = srm_inputs._mono("noalloc_nan", 3, 500, 0.35, 0.3, 23)  # dense RSA state at 0.3
+    x = torch.from_numpy(np.ascontiguousarray(w.x)).cuda()
+    r = np.ascontiguousarray(w.radii * 1.0)
+    r[17] = np.nan
+    rd = torch.from_numpy(r).cuda()
+    with pytest.raises(srm.SrmError) as e:
+        srm.srm_certify_noalloc(3, w.box, w.n, x.data_ptr(), rd.data_ptr())
+    assert e.value.status == 1 and "finite" in e.value.message
+    # a valid call right after it works on the same static memory
+    r[17] = r[16]
+    rd = torch.from_numpy(r).cuda()
+    pairs, gap = srm.srm_certify_noalloc(3, w.box, w.n, x.data_ptr(), rd.data_ptr())
+    assert (pairs, gap) == oracle.pairs_brute(3, w.box, w.x, r)[1:]
