@@ -48,18 +48,37 @@
 namespace srm {
 
 constexpr int NEAR_CAP = 64;
-constexpr int PRE_NH = 64;    // home particles whose first trials are copied up front
+constexpr int PRE_NH = 32;    // home particles whose first trials are copied up front
 constexpr int PRE_TRIALS = 2; // trials drawn ahead of the sweep per particle
 
 template <bool F32>
 struct SweepSmem {
     using PT = typename std::conditional<F32, float4, double4_32a>::type;
     using DT = typename std::conditional<F32, float, double>::type;
-    static __host__ __device__ constexpr size_t bytes(int cap)
+    // general path: stencil, culled candidates (FP64 form: plus binary32
+    // copies), near list, pre-drawn directions
+    static __host__ __device__ constexpr size_t bytes_general(int cap)
     {
         return (ST_HDR + (size_t)cap * sizeof(PT) + (F32 ? 0 : (size_t)cap * sizeof(float4)) +
                 (size_t)NEAR_CAP * sizeof(PT) + (size_t)PRE_NH * PRE_TRIALS * sizeof(PT) + 31) /
                32 * 32;
+    }
+    // staged path: stencil, every candidate, near bits (one word per
+    // 32-candidate chunk and home particle of a group), stencil cell of each
+    // candidate, binary32 copies of a group's home particles, the pre-tests
+    // of trials 0 and 1 of a group's particles, pre-drawn directions
+    static __host__ __device__ constexpr size_t off_bits(int cap) { return ST_HDR + (size_t)cap * sizeof(PT); }
+    static __host__ __device__ constexpr size_t off_cid(int cap) { return off_bits(cap) + (size_t)cap * 4; }
+    static __host__ __device__ constexpr size_t off_hap(int cap) { return (off_cid(cap) + (size_t)cap + 15) / 16 * 16; }
+    static __host__ __device__ constexpr size_t off_shit(int cap) { return off_hap(cap) + 32 * sizeof(float4); }
+    static __host__ __device__ constexpr size_t off_pre(int cap) { return (off_shit(cap) + 32 + 31) / 32 * 32; }
+    static __host__ __device__ constexpr size_t bytes_staged(int cap)
+    {
+        return (off_pre(cap) + (size_t)PRE_NH * PRE_TRIALS * sizeof(PT) + 31) / 32 * 32;
+    }
+    static __host__ __device__ constexpr size_t bytes(int cap)
+    {
+        return bytes_general(cap) > bytes_staged(cap) ? bytes_general(cap) : bytes_staged(cap);
     }
 };
 
@@ -100,11 +119,12 @@ __device__ __forceinline__ bool hit_f32(const float q[3], float Rq, const float4
 // Trial position of the FP32 form: p + c_m u per axis, one rounding.
 __device__ __forceinline__ float trial_f32(float p, float cm, float u) { return __fmaf_rn(cm, u, p); }
 
-// 16-byte asynchronous copy global -> shared (completes at cp_async_wait).
+// 16-byte asynchronous copy global -> shared (completes at cp_async_wait),
+// through L2 only (no L1 line that another SM's writes could leave stale).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -120,6 +140,22 @@ __device__ __forceinline__ int nth_set(unsigned m, int k)
         if (p <= 31 && __popc(m & ((1u << p) - 1u)) <= k) pos = p;
     }
     return pos;
+}
+
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit j of lane i
+// = entry (i, j)): lane j returns column j (bit i = entry (i, j)).  Five
+// steps of the block recursion: at step s, lanes with bit s clear swap their
+// upper s-blocks with the lower s-blocks of lane ^ s.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
+{
+    const uint32_t lo[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const int sft = 16 >> i;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sft);
+        x = (lane & sft) ? ((x & ~lo[i]) | ((y & ~lo[i]) >> sft)) : ((x & lo[i]) | ((y & lo[i]) << sft));
+    }
+    return x;
 }
 
 // ---------------------------------------------------------------------------
@@ -341,7 +377,7 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
                        reinterpret_cast<const unsigned char *>(src) + 16 * (size_t)e);
     }
     int nst, center;
-    const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
+    const uint32_t T = list_stencil(st, cs, hx, hy, hz, chi, S, nst, center);
     // population of the 3^d cells around the home cell (Algorithm 5's own
     // candidate set; the listed stencil is larger when H = 2)
     uint32_t T3 = 0;
@@ -560,11 +596,459 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// The staged path of one cell: every candidate of the stencil is copied to
+// shared memory (cp.async, 16 bytes per lane and copy), so that the cell's
+// service time -- which lies on the chain of the colour order -- holds one
+// memory round trip instead of a load per chunk:
+//  * cells not of lower colour (the home cell and those that wait for it)
+//    cannot change before this cell finishes, so they are copied before the
+//    wait; each lower-colour cell is copied by the lane that polled it, as
+//    soon as its stamp is seen;
+//  * FP32 form: candidates are then shifted into the home cell's frame;
+//  * near bits: per group of 32 home particles, one pass over the candidates
+//    marks every candidate within R_i + R_t + c_m of home particle i (plus
+//    c_m for home candidates, which may move before i's turn) -- a superset
+//    of everything a trial of i can touch -- and a ballot per particle turns
+//    the marks into one word per 32-candidate chunk;
+//  * each particle's trials test the marked candidates of every chunk, one
+//    chunk per lane, reading current positions (moves update the copies).
+// The decisions are the predicate of Algorithm 5 on the same values as the
+// general path, so the results are the same.  Returns false, having issued
+// nothing, when the stencil holds more than cap candidates.
+// ---------------------------------------------------------------------------
+template <int DIM, bool F32>
+__device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, unsigned char *base, int cap,
+                                                  CellCount &cc)
+{
+    using SM = SweepSmem<F32>;
+    using PT = typename SM::PT;
+    using DT = typename SM::DT;
+    constexpr int PIECES = (int)(sizeof(PT) / 16);
+    const int lane = threadIdx.x & 31;
+    StencilSmem &S = *reinterpret_cast<StencilSmem *>(base);
+    PT *cpos = reinterpret_cast<PT *>(base + ST_HDR);
+    uint32_t *wbits = reinterpret_cast<uint32_t *>(base + SM::off_bits(cap));
+    uint8_t *cid = base + SM::off_cid(cap);
+    float4 *hap = reinterpret_cast<float4 *>(base + SM::off_hap(cap));
+    uint32_t *shit = reinterpret_cast<uint32_t *>(base + SM::off_shit(cap));
+    PT *pre = reinterpret_cast<PT *>(base + SM::off_pre(cap));
+    uint8_t *const flags = st->flags;
+
+    const Slot d = st->slot[st->dst_idx];
+    PT *pos = reinterpret_cast<PT *>(d.pos);
+    const uint32_t *cs = st->cell_start;
+    const int s0 = st->sub[0], s1 = st->sub[1];
+    const float w[3] = {(float)st->gw[0], (float)st->gw[1], (float)st->gw[2]};
+    const uint64_t seed = st->seed, sweep = st->sweep;
+    const double c_m = st->c_m;
+    const float cmf = (float)c_m;
+    const float g1 = 1.0f + st->guard;
+    const int N_l = st->N_l;
+
+    const int hx = 3 * (t % s0) + chi % 3;
+    const int hy = 3 * ((t / s0) % s1) + (chi / 3) % 3;
+    const int hz = DIM == 3 ? 3 * (t / (s0 * s1)) + chi / 9 : 0;
+    const int cell = hx + st->gn[0] * (hy + st->gn[1] * hz);
+    const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
+    if (nh == 0) return true;  // nothing moves: nobody waits for an empty cell
+    int nst, center;
+    const uint32_t T = list_stencil(st, cs, hx, hy, hz, chi, S, nst, center);
+    if (T > (uint32_t)cap) return false;
+    const uint32_t epoch = (uint32_t)(st->sweep + 1);
+    // the pre-drawn directions of the cell's particles
+    const uint32_t npre = nh < (uint32_t)PRE_NH ? nh : (uint32_t)PRE_NH;
+    {
+        const PT *src = reinterpret_cast<const PT *>(st->dirs) + 2 * (size_t)hb;
+        for (uint32_t e = lane; e < npre * PRE_TRIALS * PIECES; e += 32)
+            cp_async16(reinterpret_cast<unsigned char *>(pre) + 16 * (size_t)e,
+                       reinterpret_cast<const unsigned char *>(src) + 16 * (size_t)e);
+    }
+    // id of home particle `lane` (the draws of later trials; loaded now,
+    // used after the wait)
+    uint32_t my_pid = (uint32_t)lane < nh ? d.pid[hb + lane] : 0u;
+    // candidates of cells that cannot change before this cell finishes
+    for (uint32_t k = lane; k < T; k += 32) {
+        const int j = find_cell(S, nst, k);
+        cid[k] = (uint8_t)j;
+        if (!S.low[j]) {
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(pos + S.b[j] + (k - S.o[j]));
+#pragma unroll
+            for (int q = 0; q < PIECES; q++)
+                cp_async16(reinterpret_cast<unsigned char *>(cpos + k) + 16 * q, src + 16 * q);
+        }
+    }
+    // lower-colour cells: wait for each (bounded), then copy it
+    {
+        const int limit = st->wait_limit;
+        for (int j = lane; j < nst; j += 32) {
+            if (!S.low[j]) continue;
+            const uint32_t nj = S.o[j + 1] - S.o[j];
+            if (nj == 0) continue;
+            if (limit < 0) {
+                atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
+            } else {
+                const uint32_t *stamp = &st->done[S.cell[j]];
+                for (int it = 0; ld_relaxed(stamp) != epoch; it++) {
+                    if (it >= limit) {
+                        atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            // the producer's writes happen before its release store; this
+            // lane's relaxed load that saw it, followed by the fence,
+            // synchronises with it before the copies below
+            fence_acquire();
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(pos + S.b[j]);
+            unsigned char *dst = reinterpret_cast<unsigned char *>(cpos + S.o[j]);
+            for (uint32_t e = 0; e < nj * PIECES; e++) cp_async16(dst + 16 * (size_t)e, src + 16 * (size_t)e);
+        }
+    }
+    cp_async_wait();
+    __syncwarp();
+    // population of the 3^d cells around the home cell (Algorithm 5's own
+    // candidate set; the listed stencil is larger when H = 2)
+    uint32_t T3 = 0;
+    for (int j = lane; j < nst; j += 32)
+        if (S.sh[j][0] >= -1 && S.sh[j][0] <= 1 && S.sh[j][1] >= -1 && S.sh[j][1] <= 1 && S.sh[j][2] >= -1 &&
+            S.sh[j][2] <= 1)
+            T3 += S.o[j + 1] - S.o[j];
+    T3 = __reduce_add_sync(0xffffffffu, T3);
+    // FP64 form: binary32 copies relative to the home corner, for the culls
+    const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
+    auto approx = [&](const PT &c) -> float4 {
+        if constexpr (F32) {
+            return c;
+        } else {
+            double ex = c.x - ox, ey = c.y - oy, ez = DIM == 3 ? c.z - oz : 0.0;
+            if (ex > st->halfL[0]) ex -= st->L[0];
+            if (ex < -st->halfL[0]) ex += st->L[0];
+            if (ey > st->halfL[1]) ey -= st->L[1];
+            if (ey < -st->halfL[1]) ey += st->L[1];
+            if (DIM == 3) {
+                if (ez > st->halfL[2]) ez -= st->L[2];
+                if (ez < -st->halfL[2]) ez += st->L[2];
+            }
+            return make_float4((float)ex, (float)ey, (float)ez, (float)c.w);
+        }
+    };
+    // largest home radius
+    float rh = 0.f;
+    for (uint32_t m = lane; m < nh; m += 32) rh = fmaxf(rh, (float)cpos[m].w);
+    for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
+    // FP32 form: shift into the home cell's frame; both forms: keep the
+    // candidates that can reach the home cell (the cull of the general
+    // path), compacted in place -- a chunk's entries are read before any
+    // is written, and writes land at or below the chunk's first index.  The
+    // home particles lead the list and are all kept, at their own index.
+    uint32_t Tk = 0;
+    for (uint32_t k0 = 0; k0 < T; k0 += 32) {
+        const uint32_t k = k0 + (uint32_t)lane;
+        bool keep = false;
+        PT c;
+        if (k < T) {
+            c = cpos[k];
+            if constexpr (F32) {
+                const int j = cid[k];
+                c.x = __fmaf_rn((float)S.sh[j][0], w[0], c.x);
+                c.y = __fmaf_rn((float)S.sh[j][1], w[1], c.y);
+                c.z = __fmaf_rn((float)S.sh[j][2], w[2], c.z);
+            }
+            const float4 ca = approx(c);
+            const float r = rh + ca.w + 2.f * cmf;
+            keep = k < nh || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) cpos[Tk + __popc(bal & ((1u << lane) - 1u))] = c;
+        Tk += __popc(bal);
+        __syncwarp();
+    }
+    const uint32_t nchunks = (Tk + 31) / 32;
+    // trials tested at once: lanes form `tpar` groups of G lanes, lane
+    // (group t, position c) tests trial t against the marked candidates of
+    // chunk c
+    const int tpar = nchunks <= 4 ? 8 : (nchunks <= 8 ? 4 : (nchunks <= 16 ? 2 : 1));
+    const int G = 32 / tpar, tsub = lane / G, csub = lane % G;
+    for (uint32_t g0 = 0; g0 < nh; g0 += 32) {
+        const uint32_t gn = nh - g0 < 32u ? nh - g0 : 32u;
+        if (g0 > 0) my_pid = (uint32_t)lane < gn ? d.pid[hb + g0 + lane] : 0u;
+        if constexpr (!F32) {
+            if ((uint32_t)lane < gn) hap[lane] = approx(cpos[g0 + lane]);
+            __syncwarp();
+        }
+        // near bits: lane i of chunk ch marks bit mm when candidate ch*32+i
+        // is within R + R_t + c_m (+ c_m for home candidates) of home
+        // particle g0+mm; the 32 x 32 bit matrix is then transposed across
+        // the lanes, so that lane mm holds the chunk's word of particle g0+mm
+        for (uint32_t ch = 0; ch < nchunks; ch++) {
+            const uint32_t k = ch * 32 + (uint32_t)lane;
+            uint32_t bits = 0;
+            if (k < Tk) {
+                const float4 ca = approx(cpos[k]);
+                const float base_r = ca.w + cmf + (k < nh ? cmf : 0.f);
+                for (uint32_t mm = 0; mm < gn; mm += 4) {
+                    float4 pm[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint32_t hq = mm + q < gn ? mm + q : gn - 1;
+                        if constexpr (F32) pm[q] = cpos[g0 + hq];
+                        else pm[q] = hap[hq];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint32_t hm = g0 + mm + q;
+                        if (mm + q < gn && k != hm && within_f32(pm[q], ca, pm[q].w + base_r, DIM))
+                            bits |= 1u << (mm + q);
+                    }
+                }
+            }
+            bits = transpose32(bits, lane);
+            if ((uint32_t)lane < gn) wbits[ch * 32 + lane] = bits;
+        }
+        __syncwarp();
+        // pre-tests: trials 0 and 1 of every particle of the group against
+        // its marked candidates outside the home cell -- positions that do
+        // not change while this cell runs, and trial positions that depend
+        // only on the particle's own position, unchanged before its turn --
+        // one lane per (particle, trial): lane pi of round r takes particle
+        // 16 r + pi / 2, trial pi % 2; bit pi of shit[r] = that trial hits
+        for (uint32_t r0 = 0; r0 < 2 * gn; r0 += 32) {
+            const uint32_t pi = r0 + (uint32_t)lane;
+            const uint32_t mm = pi >> 1, m = g0 + mm;
+            const int tt = (int)(pi & 1);
+            bool hit = false;
+            double q[3] = {0.0, 0.0, 0.0};
+            float qf[3] = {0.f, 0.f, 0.f};
+            if (pi < 2 * gn && m < (uint32_t)PRE_NH && tt < N_l) {
+                const PT p = cpos[m];
+                const PT e = pre[PRE_TRIALS * m + tt];
+                if constexpr (F32) {
+                    qf[0] = trial_f32(p.x, cmf, e.x);
+                    qf[1] = trial_f32(p.y, cmf, e.y);
+                    qf[2] = DIM == 3 ? trial_f32(p.z, cmf, e.z) : p.z;
+                } else {
+                    q[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, e.x)), st->L[0]);
+                    q[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, e.y)), st->L[1]);
+                    q[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, e.z)), st->L[2]) : p.z;
+                }
+                for (uint32_t ch = 0; ch < nchunks && !hit; ch++) {
+                    uint32_t wd = wbits[ch * 32 + mm];
+                    // drop the home candidates (indices below nh)
+                    if (ch * 32 < nh) wd &= nh - ch * 32 >= 32 ? 0u : ~((1u << (nh - ch * 32)) - 1u);
+                    while (wd && !hit) {
+                        const int bt = __ffs(wd) - 1;
+                        wd &= wd - 1;
+                        const PT c = cpos[ch * 32 + bt];
+                        cc.examined++;
+                        if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
+                        else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                    }
+                }
+            }
+            const uint32_t hbits = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) shit[r0 >> 5] = hbits;
+            // the trial position replaces its direction (read at the turn)
+            if (pi < 2 * gn && m < (uint32_t)PRE_NH && tt < N_l) {
+                if constexpr (F32) pre[PRE_TRIALS * m + tt] = make_float4(qf[0], qf[1], qf[2], 0.f);
+                else pre[PRE_TRIALS * m + tt] = make_double4_32a(q[0], q[1], q[2], 0.0);
+            }
+        }
+        __syncwarp();
+        // the group's particles, ascending id
+        for (uint32_t m = g0; m < g0 + gn; m++) {
+            const uint32_t gi = hb + m;
+            const uint32_t pid_m = __shfl_sync(0xffffffffu, my_pid, (int)(m - g0));
+            const PT p = cpos[m];
+            const uint32_t word = (uint32_t)csub < nchunks ? wbits[csub * 32 + (m - g0)] : 0u;
+            const bool have_pre = m < (uint32_t)PRE_NH;
+            bool done = false;
+            int l0 = 0;
+            PT np;
+            if (have_pre && nh <= 32) {
+                // trials 0 and 1, whose positions and pre-tests (candidates
+                // outside the home cell) the pre-test pass left: lane h tests
+                // both against home particle h at its current position when
+                // h is marked near this particle
+                const int lmax = N_l < PRE_TRIALS ? N_l : PRE_TRIALS;
+                const uint32_t sb = (shit[(2 * (m - g0)) >> 5] >> ((2 * (m - g0)) & 31)) & 3u;
+                const uint32_t hw = wbits[m - g0] & (nh == 32 ? 0xffffffffu : (1u << nh) - 1u);
+                const PT q0 = pre[PRE_TRIALS * m], q1 = pre[PRE_TRIALS * m + 1];
+                bool h0 = false, h1 = false;
+                if ((hw >> lane) & 1u) {
+                    const PT c = cpos[lane];
+                    cc.examined += lmax;
+                    if constexpr (F32) {
+                        const float a0[3] = {q0.x, q0.y, q0.z}, a1[3] = {q1.x, q1.y, q1.z};
+                        h0 = hit_f32<DIM>(a0, p.w, c, g1);
+                        h1 = lmax > 1 && hit_f32<DIM>(a1, p.w, c, g1);
+                    } else {
+                        const double a0[3] = {q0.x, q0.y, q0.z}, a1[3] = {q1.x, q1.y, q1.z};
+                        h0 = collide_exact<DIM>(a0, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        h1 = lmax > 1 && collide_exact<DIM>(a1, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                    }
+                }
+                const bool f0 = (sb & 1u) || __any_sync(0xffffffffu, h0);
+                const bool f1 = lmax < 2 || (sb & 2u) || __any_sync(0xffffffffu, h1);
+                if (!f0 || !f1) {
+                    const PT qa = !f0 ? q0 : q1;
+                    if constexpr (F32) np = make_float4(qa.x, qa.y, qa.z, p.w);
+                    else np = make_double4_32a(qa.x, qa.y, qa.z, p.w);
+                    done = true;
+                    cc.trials += !f0 ? 1 : 2;
+                } else {
+                    cc.trials += lmax;
+                }
+                l0 = lmax;
+            } else if (have_pre) {
+                // the same with more than 32 home particles: lane t takes
+                // trial t and walks the marked home candidates
+                const int lmax = N_l < PRE_TRIALS ? N_l : PRE_TRIALS;
+                const uint32_t sb = (shit[(2 * (m - g0)) >> 5] >> ((2 * (m - g0)) & 31)) & 3u;
+                double qt[3] = {0.0, 0.0, 0.0};
+                float qs[3] = {0.f, 0.f, 0.f};
+                bool hit = false;
+                if (lane < lmax) {
+                    const PT e = pre[PRE_TRIALS * m + lane];  // the trial position
+                    if constexpr (F32) {
+                        qs[0] = e.x;
+                        qs[1] = e.y;
+                        qs[2] = e.z;
+                    } else {
+                        qt[0] = e.x;
+                        qt[1] = e.y;
+                        qt[2] = e.z;
+                    }
+                    hit = (sb >> lane) & 1u;
+                    for (uint32_t ch = 0; ch * 32 < nh && !hit; ch++) {
+                        uint32_t wd = wbits[ch * 32 + (m - g0)];
+                        const uint32_t nin = nh - ch * 32;  // home candidates in this chunk
+                        if (nin < 32) wd &= (1u << nin) - 1u;
+                        while (wd && !hit) {
+                            const int bt = __ffs(wd) - 1;
+                            wd &= wd - 1;
+                            const PT c = cpos[ch * 32 + bt];
+                            cc.examined++;
+                            if constexpr (F32) hit = hit_f32<DIM>(qs, p.w, c, g1);
+                            else hit = collide_exact<DIM>(qt, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        }
+                    }
+                }
+                const unsigned clean = ~__ballot_sync(0xffffffffu, hit) & ((1u << lmax) - 1u);
+                if (clean) {
+                    const int sl = __ffs(clean) - 1;
+                    if constexpr (F32) {
+                        np = make_float4(__shfl_sync(0xffffffffu, qs[0], sl), __shfl_sync(0xffffffffu, qs[1], sl),
+                                         __shfl_sync(0xffffffffu, qs[2], sl), p.w);
+                    } else {
+                        np = make_double4_32a(__shfl_sync(0xffffffffu, qt[0], sl), __shfl_sync(0xffffffffu, qt[1], sl),
+                                              __shfl_sync(0xffffffffu, qt[2], sl), p.w);
+                    }
+                    done = true;
+                    cc.trials += sl + 1;
+                } else {
+                    cc.trials += lmax;
+                }
+                l0 = lmax;
+            }
+            while (!done && l0 < N_l) {
+                // later trials eight at a time, drawn by the lanes
+                const int lmax = N_l - l0 < 8 ? N_l - l0 : 8;
+                double qt[3] = {0.0, 0.0, 0.0};
+                float qs[3] = {0.f, 0.f, 0.f};
+                DT u[3] = {(DT)0, (DT)0, (DT)0};
+                draw8<DIM, F32>(seed, sweep, (uint64_t)pid_m, l0, u);
+                if (lane < lmax) {
+                    if constexpr (F32) {
+                        qs[0] = trial_f32(p.x, cmf, u[0]);
+                        qs[1] = trial_f32(p.y, cmf, u[1]);
+                        qs[2] = DIM == 3 ? trial_f32(p.z, cmf, u[2]) : p.z;
+                    } else {
+                        qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, u[0])), st->L[0]);
+                        qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, u[1])), st->L[1]);
+                        qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, u[2])), st->L[2]) : p.z;
+                    }
+                }
+                l0 += lmax;
+                // rounds of tpar trials; the first clean trial of a round,
+                // in trial order, is the move
+                for (int lb = 0; lb < lmax && !done; lb += tpar) {
+                    const int tr = lb + tsub;  // this lane's trial (valid if < lmax)
+                    const int src = tr < lmax ? tr : 0;
+                    double q[3] = {0.0, 0.0, 0.0};
+                    float qf[3] = {0.f, 0.f, 0.f};
+                    if constexpr (F32) {
+                        qf[0] = __shfl_sync(0xffffffffu, qs[0], src);
+                        qf[1] = __shfl_sync(0xffffffffu, qs[1], src);
+                        qf[2] = __shfl_sync(0xffffffffu, qs[2], src);
+                    } else {
+                        q[0] = __shfl_sync(0xffffffffu, qt[0], src);
+                        q[1] = __shfl_sync(0xffffffffu, qt[1], src);
+                        q[2] = __shfl_sync(0xffffffffu, qt[2], src);
+                    }
+                    bool hit = false;
+                    if (tr < lmax) {
+                        uint32_t wd = word;
+                        while (wd && !hit) {
+                            const int bt = __ffs(wd) - 1;
+                            wd &= wd - 1;
+                            const PT c = cpos[csub * 32 + bt];
+                            cc.examined++;
+                            if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
+                            else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        }
+                    }
+                    const unsigned hb_ = __ballot_sync(0xffffffffu, hit);
+                    const int nr = lmax - lb < tpar ? lmax - lb : tpar;  // trials in this round
+                    int acc = -1;
+                    for (int tt = 0; tt < nr; tt++) {
+                        const unsigned gm = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (tt * G);
+                        if (!(hb_ & gm)) {
+                            acc = tt;
+                            break;
+                        }
+                    }
+                    cc.trials += acc >= 0 ? acc + 1 : nr;
+                    if (acc >= 0) {
+                        const int sl = lb + acc;
+                        if constexpr (F32) {
+                            np = make_float4(__shfl_sync(0xffffffffu, qs[0], sl), __shfl_sync(0xffffffffu, qs[1], sl),
+                                             __shfl_sync(0xffffffffu, qs[2], sl), p.w);
+                        } else {
+                            np = make_double4_32a(__shfl_sync(0xffffffffu, qt[0], sl),
+                                                  __shfl_sync(0xffffffffu, qt[1], sl),
+                                                  __shfl_sync(0xffffffffu, qt[2], sl), p.w);
+                        }
+                        done = true;
+                    }
+                }
+            }
+            if (done) {
+                if (lane == 0) {
+                    cpos[m] = np;
+                    pos[gi] = np;
+                }
+                cc.moved++;
+            }
+            if (lane == 0) flags[gi] = done ? 1 : 0;
+            __syncwarp();
+        }
+    }
+    cc.alg5 += cc.trials * (unsigned long long)(T3 - 1);
+    // lane 0 wrote every global update of this cell (positions, flags), so
+    // its release store publishes them
+    if (lane == 0) st_release(&st->done[cell], epoch);
+    __syncwarp();
+    return true;
+}
+
 // Blocks per SM the register allocation must allow (build-time knobs; the
 // defaults are the fastest measured without spills: 96 registers for the
 // FP32 form, 128 for the FP64 form).
 #ifndef SRM_SWEEP_MIN_BLOCKS
-#define SRM_SWEEP_MIN_BLOCKS 5
+#define SRM_SWEEP_MIN_BLOCKS 4
 #endif
 #ifndef SRM_SWEEP_MIN_BLOCKS_F64
 #define SRM_SWEEP_MIN_BLOCKS_F64 4
@@ -599,7 +1083,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, F32 ? SRM_SWEEP_MIN_BLOCKS : SR
         RveDev *st = bd->rv[r];
         if (!st->active || st->dim != DIM || t >= st->nsub) continue;
         CellCount cc;
-        sweep_cell<DIM, F32>(st, chi, t, base, cap, cc);
+        if (!sweep_cell_staged<DIM, F32>(st, chi, t, base, cap, cc)) sweep_cell<DIM, F32>(st, chi, t, base, cap, cc);
         const unsigned examined = __reduce_add_sync(0xffffffffu, cc.examined);
         if (lane == 0) {
             if (cc.moved) atomicAdd(&st->red[3], (unsigned long long)cc.moved);
@@ -612,7 +1096,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32, F32 ? SRM_SWEEP_MIN_BLOCKS : SR
     }
 }
 
-int sweep_cap_max(bool f32) { return f32 ? 512 : 256; }
+// The staged path keeps one near-bit word per 32-candidate chunk in a lane:
+// at most 32 chunks.
+int sweep_cap_max(bool f32) { return f32 ? 1024 : 384; }
 
 static size_t sweep_smem(bool f32, int cap)
 {

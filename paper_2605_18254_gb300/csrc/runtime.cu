@@ -84,61 +84,21 @@ int64_t cells_for(int dim, const double L[3], double rmax, double c_m, double la
     return tot;
 }
 
-// Staging capacity of the warp-per-cell sweep: the 95th percentile of the
-// stencil population of the starting positions on the grid of the target
-// scale (the coarsest grid of the run), times the part of the stencil volume
-// within reach of the home cell, with slack.  Denser cells stage what fits
-// and read the rest from global memory (same results).
+// Staging capacity of the warp-per-cell sweep: the sweep copies a cell's
+// whole stencil (3^d cells) to shared memory when it fits, so the capacity
+// is sized from the mean stencil population on the grid of the target scale
+// (the coarsest grid of the run, whose cells hold the most particles), 3^d
+// N / cells, with room for 1.8 times the mean (measured at the end of the
+// 1e6-sphere clustered run: median 1.07, maximum 1.76 times the mean).
+// Denser cells take the general path, which culls and reads what does not
+// fit from global memory (same results); the autotuner also tries half and
+// twice this capacity.
 static int staging_estimate(const Prep &q)
 {
     int64_t pa[3];
     const int64_t nc = cells_for(q.dim, q.L, q.rmax, q.p.c_m, q.lam_t, pa);
-    std::vector<uint32_t> occ((size_t)nc, 0u);
-    for (int64_t i = 0; i < q.n; i++) {
-        int64_t lin = 0, mul = 1;
-        for (int a = 0; a < q.dim; a++) {
-            const double wa = q.L[a] / (double)pa[a];
-            int64_t c = (int64_t)(q.x[(size_t)i * q.dim + a] / wa);
-            c = ((c % pa[a]) + pa[a]) % pa[a];
-            lin += c * mul;
-            mul *= pa[a];
-        }
-        occ[(size_t)lin]++;
-    }
-    std::vector<uint32_t> tpop;
-    tpop.reserve((size_t)q.n);
-    const int zr = q.dim == 3 ? 1 : 0;
-    for (int64_t c = 0; c < nc; c++) {
-        if (!occ[(size_t)c]) continue;
-        const int64_t cx = c % pa[0], cy = (c / pa[0]) % pa[1], cz = c / (pa[0] * pa[1]);
-        uint32_t t = 0;
-        for (int dz = -zr; dz <= zr; dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    const int64_t ex = (cx + dx + pa[0]) % pa[0], ey = (cy + dy + pa[1]) % pa[1],
-                                  ez = (cz + dz + pa[2]) % pa[2];
-                    t += occ[(size_t)(ex + pa[0] * (ey + pa[1] * ez))];
-                }
-        for (uint32_t k = 0; k < occ[(size_t)c]; k++) tpop.push_back(t);  // per particle
-    }
-    uint32_t t95 = 0;
-    if (!tpop.empty()) {
-        const size_t qi = tpop.size() * 95 / 100;
-        std::nth_element(tpop.begin(), tpop.begin() + (ptrdiff_t)qi, tpop.end());
-        t95 = tpop[qi];
-    }
-    // staged = candidates within R_home,max + R_t + 2 c_m of the home box;
-    // radii taken as 1.2 x the mean (capped at the largest), since a cell
-    // holds few particles and most candidates are of typical size
-    double rsum = 0.0;
-    for (double v : q.r) rsum += v;
-    const double rtyp = std::min(q.rmax, 1.2 * rsum / (double)(q.r.empty() ? 1 : q.r.size()));
-    const double wt = q.L[0] / (double)pa[0];
-    const double reach = 2.0 * (2.0 * q.lam_t * rtyp + 2.0 * q.p.c_m);
-    double frac = (wt + reach) / (3.0 * wt);
-    frac = frac > 1.0 ? 1.0 : frac;
-    frac = q.dim == 3 ? frac * frac * frac : frac * frac;
-    int64_t cap = (int64_t)(1.25 * frac * (double)t95) + 16;
+    const double mean = (q.dim == 3 ? 27.0 : 9.0) * (double)q.n / (double)(nc > 0 ? nc : 1);
+    int64_t cap = (int64_t)(1.8 * mean) + 32;
     cap = (cap + 31) / 32 * 32;
     return (int)(cap < 64 ? 64 : cap);
 }
@@ -237,7 +197,7 @@ srm_status prepare(int32_t dim, const double box[3], const srm_radii *radii, dou
     if (q.ncells_need > 0x7ffffff0LL) return fail(SRM_E_ARG, "too many cells (radii too small for the box)");
     q.nsub_need = 1;
     for (int a = 0; a < dim; a++) q.nsub_need *= per[a] / 3;
-    q.cap_est = place ? staging_estimate(q) : 64;
+    q.cap_est = staging_estimate(q);
     return SRM_OK;
 }
 
