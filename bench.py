@@ -800,7 +800,7 @@ def run_platelets(args, rank, world, local_rank):
         sw = o.counters()["sweeps"]
         cpu = {"value": w.n * sw / dt, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"the first {o.counters()['iters']} iterations of the same generation ({sw} sweeps, "
-                         f"{dt:.1f} s, single-threaded reference: binary64 state, binary32 contact test, reaching rho = "
+                         f"{dt:.1f} s, single-threaded binary64 reference, reaching rho = "
                          f"{w.rho_t * o.lam ** 3:.2f}; the early sweeps are the cheapest ones)"}
     r0 = res[0]
     # neighbour alignment of the house of cards (a generation alone) and after the relaxation

@@ -76,7 +76,8 @@ def _load():
                 "orc_unit_dir_stream": ([_u64, _u64, _u64, _u64, _int, _int, P(_d)], _int),
                 "orc_plt_basis": ([P(_d), P(_d), P(_d)], None),
                 "orc_plt_point_disk": ([P(_d), P(_d), P(_d), _d], _d),
-                "orc_plt_rim_near_disk": ([P(_d), P(_d), P(_d), _d, P(_d), P(_d), _d, _d, _d, P(_int)], _int),
+                "orc_plt_rim_near_disk": ([P(_d), P(_d), _d, P(_d), P(_d), _d, _d, P(_int)], _int),
+                "orc_plt_set_contact": ([ctypes.c_void_p, ctypes.c_void_p], None),
                 "orc_plt_collide": ([P(_d), P(_d), P(_d), _d, _d], _int),
                 "orc_plt_trial": ([_u64, _u64, _u64, _u64, P(_d), _d, _d, P(_d), P(_d), P(_d), P(_d)], None),
                 "orc_plt_create": ([P(_d), _i64, P(_d), P(_d), _d, _d, _d, _d, _d, _d, _d, _int, _int, _int,
@@ -323,11 +324,8 @@ def plt_point_disk(p, cd, nd, b) -> float:
 def plt_rim_near_disk(cc, n_c, a, cd, nd, b, thr):
     """(decision, evaluations) for the rim of the disk (cc, n_c, a) against
     the disk (cd, nd, b) at distance thr."""
-    e1, e2 = plt_basis(n_c)
-    c = float(np.dot(_v3(n_c), _v3(nd)))
-    sn = float(np.sqrt(max(0.0, 1.0 - c * c)))
     ev = _int(0)
-    r = _load().orc_plt_rim_near_disk(_dp(_v3(cc)), _dp(e1), _dp(e2), a, _dp(_v3(cd)), _dp(_v3(nd)), b, sn, thr,
+    r = _load().orc_plt_rim_near_disk(_dp(_v3(cc)), _dp(_v3(n_c)), a, _dp(_v3(cd)), _dp(_v3(nd)), b, thr,
                                       ctypes.byref(ev))
     return int(r), int(ev.value)
 
@@ -364,7 +362,10 @@ class PlateletSystem:
     rotation rate c_r."""
 
     def __init__(self, box, x, u, a0, t0, lam=1.0, lam_t=None, c_w=0.01, c_m=0.01, c_r=0.0, N_k=10, N_l=10,
-                 N_shake=10, seed=1, sweep=0):
+                 N_shake=10, seed=1, sweep=0, contact=None):
+        """contact: address of another contact predicate with the signature
+        of orc_plt_collide for the sweeps and checks (tests only; None: the
+        reference's binary64 decision)."""
         if not 1 <= N_l < (1 << 16):
             raise ValueError("N_l must be in [1, 65535] (the try index takes 16 counter bits)")
         if not 0.0 <= c_r < 1.0:
@@ -377,6 +378,8 @@ class PlateletSystem:
         self.a0, self.t0 = float(a0), float(t0)
         self._h = lib.orc_plt_create(_dp(self.box), self.n, _dp(x), _dp(u), a0, t0, lam,
                                      lam if lam_t is None else lam_t, c_w, c_m, c_r, N_k, N_l, N_shake, seed, sweep)
+        if contact is not None:
+            lib.orc_plt_set_contact(self._h, contact)
 
     def __del__(self):
         h = getattr(self, "_h", None)

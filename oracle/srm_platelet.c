@@ -7,7 +7,8 @@
  * rotation.  Only the tests, the smoke check and the CPU leg of the
  * benchmark load it; the product library never does, and it shares no code
  * with the CUDA path.  Built like srm_oracle.c (gcc -O2 -ffp-contract=off):
- * every operation is one IEEE binary64 operation in source order.
+ * every arithmetic operation is one IEEE binary64 operation in source order;
+ * cos, sin and sqrt are the C library's binary64 functions.
  *
  * Readings fixed here (the paper names the shape and the parameters only):
  *   - a spherodisk is the set of points within distance t of a flat circular
@@ -18,7 +19,7 @@
  *   - the number density of Eq. 1 is rho = N D^3 / V with V the box volume;
  *   - two platelets collide when the distance between their disks is at
  *     most t_i + t_j (closed inequality, as for spheres), decided in
- *     binary32 with the widening described below;
+ *     binary64 as described below;
  *   - try l of Alg 3 moves the centre by c_m u (u from stream 0, as for
  *     spheres) and turns the normal to (n + c_r v) / |n + c_r v| with v a
  *     second uniform direction (stream 1), 0 <= c_r < 1;
@@ -27,39 +28,41 @@
  *     2 lambda (a0 + t0).
  *
  * Collision decision.  The distance between two disks is reached at a point
- * of one of the two rims (if the closest pair were interior to both disks,
- * the disks would be parallel and the overlap of their projections, bounded
- * by rim arcs, contains rim points at the same distance; if the disks cross,
- * an end of one disk's chord on the line where the planes meet lies inside
- * the other disk).  So the platelets collide exactly when some rim point of
- * one disk lies within t_i + t_j of the other disk.  The rim is walked by
- * bisection.  The rim point moves at most 2 a / (1 + s^2) <= a (2 - s^2)
- * =: V per unit of the rational parameter s (1 / (1 + x) <= 1 - x / 2 on
- * [0, 1]), and its distance to the other disk is
- * sqrt(h^2 + e^2) with h its height above that disk's plane and e the
- * excess of its projected distance from that disk's centre over the radius
- * (0 inside).  Along the rim h changes at most at V sin(theta) (the rim lies
- * in its own plane; theta is the angle between the normals) and e at most
- * at V, so over an interval of half-width r around its midpoint,
- * sqrt(max(0, |h| - V r sin)^2 + max(0, e - V r)^2) bounds the distance
- * from below.  Intervals whose bound is above the threshold are dropped, a
- * midpoint at or below it is a collision (both compared as squares: h^2 +
- * e^2 <= thr^2).  Each of the 8 first-level arcs of a rim is bisected on
- * its own; an arc still undecided at 2^-20 of the circle, or after 512
- * evaluations, counts as a collision (a near-contact the bisection cannot
- * resolve is reported as contact).  The arcs are independent, so the
- * decision is the OR of 16 arc results (2 rims x 8 arcs) in any order.  Cheap exact
- * separations come first: the bounding spheres, and the two slabs along the
- * normals.
+ * of one of the two rims: if the closest pair of points were interior to
+ * both disks the disks would be parallel, and then the overlap of their
+ * projections, which is bounded by rim arcs, contains rim points at the
+ * same distance; if the disks cross, an end of one disk's chord on the line
+ * where the planes meet lies inside the other disk.  So the platelets
+ * collide exactly when some rim point of one disk lies within t_i + t_j of
+ * the other disk.
  *
- * Precision.  The decision is evaluated in binary32 (the paper fixes no
- * precision for it) on the pair's relative geometry: the centre difference
- * is formed in binary64 under the minimum image and then rounded, like the
- * normals and sizes.  Its threshold is widened from t_i + t_j by 2^-16 a,
- * more than the binary32 rounding of every quantity in the test (a few
- * ulps of 3 a), so a pair whose true distance is at most t_i + t_j is
- * always reported (the widening only ever adds contacts).  Centres, normals,
- * draws and moves stay in binary64.
+ * The distance from a point p to a disk (centre c, unit normal m, radius b)
+ * is sqrt(h^2 + e^2), with h = (p - c).m its height above the disk's plane
+ * and e the excess of its in-plane distance from c over b (0 inside).  On a
+ * rim p(phi) = c_r + a (cos phi e1 + sin phi e2), the point moves at speed a
+ * per radian along a tangent that lies in the rim's own plane, so h changes
+ * at most at a sin(theta) (theta the angle between the two normals, sin
+ * theta = |n_i x n_j|) and e at most at a.  Over an arc of half-width r
+ * around phi_m the distance is therefore at least
+ *     sqrt(max(0, |h(phi_m)| - a r sin theta)^2 + max(0, e(phi_m) - a r)^2),
+ * a Lipschitz lower bound.  The rim is searched by branch and bound: an arc
+ * whose midpoint is within the threshold decides "collision"; an arc whose
+ * lower bound is above it is dropped; any other arc is halved (depth
+ * first).  An arc still undecided at half-width 2^-40 rad counts as contact:
+ * the distance there is within 2 a 2^-40 (2e-12 a) of the threshold.  As a
+ * safety net a rim that needs more than 2^20 evaluations also counts as
+ * contact; it only happens for pairs within rounding of touching.  Cheap
+ * exact separations come first: the bounding spheres (every point of a disk
+ * is within a of its centre), and the two slabs (disk j lies within
+ * a sin(theta) of the plane through its centre parallel to disk i).  The
+ * pair is evaluated in a frame centred between the two platelets, so that
+ * swapping them gives the same operations and the same answer.
+ *
+ * Tests may substitute another contact predicate for the sweeps and checks
+ * (orc_plt_set_contact) -- the binary32 decision of the CUDA kernel, kept as
+ * a kernel specification beside the tests -- to compare whole sweeps with
+ * the GPU bit for bit; the reference's own predicate, and the one of its
+ * brute-force certification, is the binary64 decision above.
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,211 +73,154 @@ int orc_unit_dir_stream(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l,
 double orc_wrap(double x, double L);
 void orc_grid(int dim, const double L[3], double lam, double rmax, double c_m, int64_t n[3], double w[3]);
 
-#define PLT_TOP 3        /* first level evaluated: 8 intervals of the circle */
-#define PLT_DEPTH 20     /* finest level (binary32 still separates its midpoints) */
-#define PLT_EVALS 512    /* evaluations per level-3 interval (4096 per rim) */
-#define PLT_SLACK 0x1p-16f /* threshold widening, in units of the disk radius */
+#define PLT_MIN_HALF_WIDTH 0x1p-40 /* radians: finest arc of the rim search */
+#define PLT_MAX_EVALS (1 << 20)    /* evaluations per rim before counting as contact */
 
-static float dot3f(const float a[3], const float b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
 
 /* Orthonormal basis (e1, e2) of the plane of the unit normal n: e1 is n
  * crossed with the coordinate axis of smallest |n_k| (the first such axis),
  * normalised; e2 = n x e1. */
-static void basis_f(const float n[3], float e1[3], float e2[3])
+void orc_plt_basis(const double n[3], double e1[3], double e2[3])
 {
-    float ax = fabsf(n[0]), ay = fabsf(n[1]), az = fabsf(n[2]);
+    double ax = fabs(n[0]), ay = fabs(n[1]), az = fabs(n[2]);
     int k = 0;
-    float m = ax;
+    double m = ax;
     if (ay < m) {
         k = 1;
         m = ay;
     }
     if (az < m) k = 2;
-    float c[3];
-    if (k == 0) {
-        c[0] = 0.0f; c[1] = n[2]; c[2] = -n[1];
-    } else if (k == 1) {
-        c[0] = -n[2]; c[1] = 0.0f; c[2] = n[0];
-    } else {
-        c[0] = n[1]; c[1] = -n[0]; c[2] = 0.0f;
-    }
-    float r = sqrtf(dot3f(c, c));
+    double axis[3] = {0.0, 0.0, 0.0};
+    axis[k] = 1.0;
+    double c[3];
+    cross3(n, axis, c);
+    double r = sqrt(dot3(c, c));
     for (int a = 0; a < 3; a++) e1[a] = c[a] / r;
-    e2[0] = n[1] * e1[2] - n[2] * e1[1];
-    e2[1] = n[2] * e1[0] - n[0] * e1[2];
-    e2[2] = n[0] * e1[1] - n[1] * e1[0];
-}
-
-void orc_plt_basis(const double n[3], double e1[3], double e2[3])
-{
-    const float nf[3] = {(float)n[0], (float)n[1], (float)n[2]};
-    float a[3], b[3];
-    basis_f(nf, a, b);
-    for (int k = 0; k < 3; k++) {
-        e1[k] = a[k];
-        e2[k] = b[k];
-    }
+    cross3(n, e1, e2);
 }
 
 /* Point p against the disk of centre cd, unit normal nd, radius b: h =
  * height above the plane, e = distance of the projection from cd minus b,
  * or 0 when the projection lies in the disk. */
-static void point_disk_he(const float p[3], const float cd[3], const float nd[3], float b, float *h, float *e)
+static void point_disk_he(const double p[3], const double cd[3], const double nd[3], double b, double *h, double *e)
 {
-    float q[3] = {p[0] - cd[0], p[1] - cd[1], p[2] - cd[2]};
-    float hh = dot3f(q, nd);
-    float r[3] = {q[0] - hh * nd[0], q[1] - hh * nd[1], q[2] - hh * nd[2]};
-    float rr = dot3f(r, r);
+    double q[3] = {p[0] - cd[0], p[1] - cd[1], p[2] - cd[2]};
+    double hh = dot3(q, nd);
+    double r[3] = {q[0] - hh * nd[0], q[1] - hh * nd[1], q[2] - hh * nd[2]};
+    double rr = dot3(r, r);
     *h = hh;
-    *e = rr <= b * b ? 0.0f : sqrtf(rr) - b;
+    *e = rr <= b * b ? 0.0 : sqrt(rr) - b;
 }
 
-/* Distance from point p to that disk: sqrt(h^2 + e^2) (binary32). */
+/* Distance from point p to that disk: sqrt(h^2 + e^2). */
 double orc_plt_point_disk(const double p[3], const double cd[3], const double nd[3], double b)
 {
-    const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
-    const float cf[3] = {(float)cd[0], (float)cd[1], (float)cd[2]};
-    const float nf[3] = {(float)nd[0], (float)nd[1], (float)nd[2]};
-    float h, e;
-    point_disk_he(pf, cf, nf, (float)b, &h, &e);
-    return sqrtf(h * h + e * e);
+    double h, e;
+    point_disk_he(p, cd, nd, b, &h, &e);
+    return sqrt(h * h + e * e);
 }
 
-/* Point of the circle (centre cc, basis e1 e2, radius a) at parameter tau in
- * [0, 4): tau < 2 gives s = tau - 1 and the half circle
- * ((1 - s^2) e1 + 2 s e2) / (1 + s^2), tau >= 2 gives s = tau - 3 and the
- * opposite half (the same point negated). */
-static void rim_point(const float cc[3], const float e1[3], const float e2[3], float a, float tau, float p[3])
+/* Is some point of the rim of the disk (centre cc, in-plane basis e1 e2,
+ * radius a) within thr of the disk (cd, nd, b)?  sn = sine of the angle
+ * between the two normals.  Branch and bound over the rim angle (see the
+ * header); *evals (may be NULL) receives the number of rim points
+ * evaluated. */
+static int rim_within(const double cc[3], const double e1[3], const double e2[3], double a, const double cd[3],
+                      const double nd[3], double b, double sn, double thr, int *evals)
 {
-    int first = tau < 2.0f;
-    float s = first ? tau - 1.0f : tau - 3.0f;
-    float s2 = s * s;
-    float inv = 1.0f / (1.0f + s2);
-    float C = (1.0f - s2) * inv, S = (2.0f * s) * inv;
-    float sa = first ? a : -a;
-    for (int k = 0; k < 3; k++) p[k] = cc[k] + sa * (C * e1[k] + S * e2[k]);
-}
-
-/* Is some point of the arc tau in [k0/2, (k0+1)/2) (one of the 8 intervals
- * of level 3) of the circle (cc, e1, e2, a) within thr of the disk (cd, nd,
- * b)?  sn = sine of the angle between the two normals.  Depth-first
- * bisection, intervals [k w, (k+1) w) with w = 4 / 2^d, left half first.
- * Returns 1 (yes, or undecided at level 20 or after 512 evaluations) or 0;
- * *evals receives the number of midpoints evaluated.  The 8 intervals are
- * independent, so the answer for the whole rim is their OR in any order. */
-static int arc_near_disk_f(const float cc[3], const float e1[3], const float e2[3], float a, const float cd[3],
-                           const float nd[3], float b, float sn, float thr, int k0, int *evals)
-{
-    int d = PLT_TOP, ne = 0;
-    int64_t k = k0;
-    float thr2 = thr * thr;
-    for (;;) {
-        float w = ldexpf(4.0f, -d);
-        float lo = (float)k * w;
-        float p[3];
-        rim_point(cc, e1, e2, a, lo + 0.5f * w, p);
-        float h, e;
+    const double pi = 3.14159265358979323846;
+    const double thr2 = thr * thr;
+    /* pending arcs (midpoint, half-width); depth first, so at most two per
+     * halving level are pending: 2 x 42 levels fit */
+    double mid[96], half[96];
+    int top = 0, ne = 0, hit = 0;
+    mid[0] = pi;
+    half[0] = pi;
+    top = 1;
+    while (top > 0) {
+        top--;
+        double phi = mid[top], r = half[top];
+        double p[3], h, e;
+        double c = cos(phi), s = sin(phi);
+        for (int k = 0; k < 3; k++) p[k] = cc[k] + a * (c * e1[k] + s * e2[k]);
         point_disk_he(p, cd, nd, b, &h, &e);
         ne++;
         if (h * h + e * e <= thr2) {
-            if (evals) *evals = ne;
-            return 1;
+            hit = 1;
+            break;
         }
-        float off = lo < 2.0f ? 1.0f : 3.0f;
-        float sl = lo - off, sr = (lo + w) - off;
-        float m2 = (sl <= 0.0f && sr >= 0.0f) ? 0.0f : (sl * sl < sr * sr ? sl * sl : sr * sr);
-        float r = (a * (2.0f - m2)) * (0.5f * w);
-        float hl = fabsf(h) - r * sn, el = e - r;
-        if (hl < 0.0f) hl = 0.0f;
-        if (el < 0.0f) el = 0.0f;
-        if (!(hl * hl + el * el > thr2)) {
-            if (d == PLT_DEPTH || ne >= PLT_EVALS) {
-                if (evals) *evals = ne;
-                return 1;
-            }
-            d++;
-            k = 2 * k;
-            continue;
+        double hl = fabs(h) - a * r * sn, el = e - a * r;
+        if (hl < 0.0) hl = 0.0;
+        if (el < 0.0) el = 0.0;
+        if (hl * hl + el * el > thr2) continue; /* the whole arc is farther than thr */
+        if (r < PLT_MIN_HALF_WIDTH || ne >= PLT_MAX_EVALS) {
+            hit = 1; /* undecided within 2 a r of the threshold: counted as contact */
+            break;
         }
-        while (d > PLT_TOP && (k & 1)) {
-            k >>= 1;
-            d--;
-        }
-        if (d == PLT_TOP) {
-            if (evals) *evals = ne;
-            return 0;
-        }
-        k++;
+        /* left half on top, so that it is taken first */
+        mid[top] = phi + 0.5 * r;
+        half[top] = 0.5 * r;
+        top++;
+        mid[top] = phi - 0.5 * r;
+        half[top] = 0.5 * r;
+        top++;
     }
+    if (evals) *evals = ne;
+    return hit;
 }
 
-/* The whole rim: the 8 level-3 arcs in order, stopping at the first that
- * reports contact; *evals receives the evaluations of the arcs visited. */
-static int rim_near_disk_f(const float cc[3], const float e1[3], const float e2[3], float a, const float cd[3],
-                           const float nd[3], float b, float sn, float thr, int *evals)
+/* The rim of the disk (cc, normal n_c, radius a) against the disk (cd, nd,
+ * b) at distance thr, with its own basis and angle (for the tests). */
+int orc_plt_rim_near_disk(const double cc[3], const double n_c[3], double a, const double cd[3], const double nd[3],
+                          double b, double thr, int *evals)
 {
-    int total = 0;
-    for (int k0 = 0; k0 < 8; k0++) {
-        int ne = 0;
-        int r = arc_near_disk_f(cc, e1, e2, a, cd, nd, b, sn, thr, k0, &ne);
-        total += ne;
-        if (r) {
-            if (evals) *evals = total;
-            return 1;
-        }
-    }
-    if (evals) *evals = total;
-    return 0;
-}
-
-int orc_plt_rim_near_disk(const double cc[3], const double e1[3], const double e2[3], double a,
-                          const double cd[3], const double nd[3], double b, double sn, double thr, int *evals)
-{
-    float c1[3], f1[3], f2[3], c2[3], n2[3];
-    for (int k = 0; k < 3; k++) {
-        c1[k] = (float)cc[k];
-        f1[k] = (float)e1[k];
-        f2[k] = (float)e2[k];
-        c2[k] = (float)cd[k];
-        n2[k] = (float)nd[k];
-    }
-    return rim_near_disk_f(c1, f1, f2, (float)a, c2, n2, (float)b, (float)sn, (float)thr, evals);
+    double e1[3], e2[3], x[3];
+    orc_plt_basis(n_c, e1, e2);
+    cross3(n_c, nd, x);
+    return rim_within(cc, e1, e2, a, cd, nd, b, sqrt(dot3(x, x)), thr, evals);
 }
 
 /* Do the spherodisks i and j (disk radius a, half-thickness t each) collide?
- * dj = centre of j minus centre of i (minimum image, binary64); ni, nj unit
- * normals.  The test runs in binary32 on dj, ni, nj, a and t rounded to
- * binary32, against the threshold 2 t + 2^-16 a (the widening exceeds every
- * binary32 rounding of the test, so a pair at distance <= 2 t is always
- * found).  Steps: bounding spheres (|dj| > 2 a + thr: no); slab along ni
- * (|dj.ni| - a sin > thr: no) and along nj, with sin the sine of the angle
- * between the normals; then the rim of i against the disk of j and the rim
- * of j against the disk of i. */
+ * dj = centre of j minus centre of i (minimum image); ni, nj unit normals.
+ * The distance between the disks is compared with thr = t_i + t_j = 2 t in
+ * binary64, in the frame whose origin is the midpoint of the two centres
+ * (i at -dj/2, j at +dj/2).  Steps: bounding spheres (|dj| > 2 a + thr: no);
+ * slab along ni (|dj.ni| - a sin(theta) > thr: no) and along nj; the rim of
+ * i against the disk of j; the rim of j against the disk of i. */
 int orc_plt_collide(const double dj[3], const double ni[3], const double nj[3], double a, double t)
 {
-    const float d[3] = {(float)dj[0], (float)dj[1], (float)dj[2]};
-    const float u[3] = {(float)ni[0], (float)ni[1], (float)ni[2]};
-    const float v[3] = {(float)nj[0], (float)nj[1], (float)nj[2]};
-    const float af = (float)a, tf = (float)t;
-    float thr = (tf + tf) + af * PLT_SLACK;
-    float reach = (af + af) + thr;
-    if (dot3f(d, d) > reach * reach) return 0;
-    float c = dot3f(u, v);
-    float s2 = 1.0f - c * c;
-    if (s2 < 0.0f) s2 = 0.0f;
-    float sn = sqrtf(s2);
-    float ext = af * sn;
-    if (fabsf(dot3f(d, u)) - ext > thr) return 0;
-    if (fabsf(dot3f(d, v)) - ext > thr) return 0;
-    float ei1[3], ei2[3], ej1[3], ej2[3];
-    const float zero[3] = {0.0f, 0.0f, 0.0f};
-    basis_f(u, ei1, ei2);
-    basis_f(v, ej1, ej2);
-    if (rim_near_disk_f(zero, ei1, ei2, af, d, v, af, sn, thr, NULL)) return 1;
-    if (rim_near_disk_f(d, ej1, ej2, af, zero, u, af, sn, thr, NULL)) return 1;
+    double thr = t + t;
+    double reach = (a + a) + thr;
+    if (dot3(dj, dj) > reach * reach) return 0;
+    double x[3];
+    cross3(ni, nj, x);
+    double sn = sqrt(dot3(x, x));
+    double ext = a * sn;
+    if (fabs(dot3(dj, ni)) - ext > thr) return 0;
+    if (fabs(dot3(dj, nj)) - ext > thr) return 0;
+    double ci[3], cj[3];
+    for (int k = 0; k < 3; k++) {
+        cj[k] = 0.5 * dj[k];
+        ci[k] = -cj[k];
+    }
+    double ei1[3], ei2[3], ej1[3], ej2[3];
+    orc_plt_basis(ni, ei1, ei2);
+    orc_plt_basis(nj, ej1, ej2);
+    if (rim_within(ci, ei1, ei2, a, cj, nj, a, sn, thr, NULL)) return 1;
+    if (rim_within(cj, ej1, ej2, a, ci, ni, a, sn, thr, NULL)) return 1;
     return 0;
 }
+
+/* Contact predicate of the sweeps and checks (default orc_plt_collide). */
+typedef int (*orc_plt_contact_fn)(const double dj[3], const double ni[3], const double nj[3], double a, double t);
 
 /* ---------------------------------------------------------------------------
  * Platelet system.  Centres X[3 pid + a] and unit normals U[3 pid + a] in id
@@ -293,6 +239,7 @@ typedef struct orc_plt {
     int64_t ncells, cap_cells;
     int64_t *cell_start, *members;
     int64_t iters, accepted_iters, shake_iters, moves_accepted;
+    orc_plt_contact_fn contact;
 } orc_plt;
 
 static int64_t pcell_coord(double x, double w, int64_t n)
@@ -352,7 +299,7 @@ static int pcollide(const orc_plt *s, const double *X, const double *U, double l
                         if (db < -0.5 * s->L[b]) db += s->L[b];
                         d[b] = db;
                     }
-                    if (orc_plt_collide(d, u, &U[3 * j], a, t)) return 1;
+                    if (s->contact(d, u, &U[3 * j], a, t)) return 1;
                 }
             }
     return 0;
@@ -459,8 +406,13 @@ orc_plt *orc_plt_create(const double L[3], int64_t N, const double *X, const dou
     s->N_shake = N_shake;
     s->seed = seed;
     s->sweep = sweep;
+    s->contact = orc_plt_collide;
     return s;
 }
+
+/* Substitutes the contact predicate of the sweeps and checks (NULL: the
+ * reference's binary64 orc_plt_collide).  For tests only. */
+void orc_plt_set_contact(orc_plt *s, orc_plt_contact_fn fn) { s->contact = fn ? fn : orc_plt_collide; }
 
 void orc_plt_destroy(orc_plt *s)
 {

@@ -1,8 +1,8 @@
 """Pins of the platelet reference (spherodisks, Section 3.3).
 
-The contact test runs in binary32 with its threshold widened by 2^-16 a
-(SLACK below): a pair at distance at most 2 t always collides, a pair
-farther than 2 t + SLACK (plus binary32 rounding) never does.
+The contact test decides "disk-to-disk distance <= t_i + t_j" in binary64;
+a pair within 2e-12 a of touching that its rim search cannot resolve counts
+as contact.
 
 * The contact decision against the distance between two disks found by brute
   force (dense point clouds of both disks, nearest pair by a KD-tree, refined
@@ -27,8 +27,7 @@ import oracle
 spatial = pytest.importorskip("scipy.spatial")
 optimize = pytest.importorskip("scipy.optimize")
 
-SLACK = 2.0 ** -16  # threshold widening, in units of the disk radius
-CLEAR = 1e-4        # a gap this much beyond 2 t (times a) is clear of the widening and of rounding
+CLEAR = 1e-9  # a gap this much beyond 2 t (times a) is clear of the rim search's resolution and of rounding
 
 
 def unit(v):
@@ -121,14 +120,14 @@ def test_point_disk_against_sampled_disk():
         P, err = disk_cloud(cd, nd, b, 200, 1600)
         ref = float(np.min(np.linalg.norm(P - p, axis=1)))
         d = oracle.plt_point_disk(p, cd, nd, b)
-        assert ref - err - 1e-5 <= d <= ref + 1e-5  # binary32 evaluation
+        assert ref - err - 1e-12 <= d <= ref + 1e-12
 
 
 def test_point_disk_closed_forms():
     nd = np.array([0.0, 0.0, 1.0])
-    assert oracle.plt_point_disk([0.3, -0.2, 0.7], [0, 0, 0], nd, 1.0) == pytest.approx(0.7, abs=1e-7)
-    assert oracle.plt_point_disk([3.0, 4.0, 0.0], [0, 0, 0], nd, 1.0) == pytest.approx(4.0, abs=1e-6)
-    assert oracle.plt_point_disk([0.0, 2.0, -2.0], [0, 0, 0], nd, 1.0) == pytest.approx(math.sqrt(5.0), abs=1e-6)
+    assert oracle.plt_point_disk([0.3, -0.2, 0.7], [0, 0, 0], nd, 1.0) == pytest.approx(0.7, abs=1e-15)
+    assert oracle.plt_point_disk([3.0, 4.0, 0.0], [0, 0, 0], nd, 1.0) == pytest.approx(4.0, abs=1e-15)
+    assert oracle.plt_point_disk([0.0, 2.0, -2.0], [0, 0, 0], nd, 1.0) == pytest.approx(math.sqrt(5.0), abs=1e-15)
 
 
 def test_basis_orthonormal():
@@ -136,7 +135,7 @@ def test_basis_orthonormal():
     for n in list(rand_units(rng, 200)) + [np.eye(3)[k] for k in range(3)]:
         e1, e2 = oracle.plt_basis(n)
         M = np.stack([e1, e2, n])
-        np.testing.assert_allclose(M @ M.T, np.eye(3), atol=1e-6)  # binary32 basis
+        np.testing.assert_allclose(M @ M.T, np.eye(3), atol=1e-15)
 
 
 @pytest.mark.parametrize("seed", [3, 4])
@@ -153,10 +152,9 @@ def test_decision_threshold_equals_brute_force_distance(seed):
             assert oracle.plt_collide(dj, ni, nj, a, 1e-6) == 1
             continue
         d = flip_threshold(dj, ni, nj, a)
-        # the decision counts contacts within the widening (and near-contacts
-        # it cannot resolve) as contact, never a clear gap: the flip lies in
-        # [lower bound - widening - resolution, upper bound + rounding]
-        assert max(lo, 0.0) - SLACK * a - 1e-5 <= d <= up + 1e-5, (d, lo, up)
+        # the decision may count a near-contact it cannot resolve as contact,
+        # never a clear gap: the flip lies in [lower bound - resolution, upper]
+        assert max(lo, 0.0) - 1e-9 <= d <= up + 1e-9, (d, lo, up)
         checked += 1
     assert checked >= 12
 
@@ -178,7 +176,7 @@ def test_decision_on_near_contacts_matches_brute_force(aspect):
         if up <= 2 * t:
             assert got == 1
             decided += 1
-        elif lo > 2 * t + CLEAR * a:
+        elif lo > 2 * t:
             assert got == 0
             decided += 1
     assert decided >= 50
@@ -204,8 +202,8 @@ def test_stacked_parallel_disks():
             assert oracle.plt_collide(base + n * (2 * t - 1e-12), n, n, a, t) == 1
             assert oracle.plt_collide(base + n * (2 * t + CLEAR * a), n, n, a, t) == 0
             assert oracle.plt_collide(base - n * (2 * t + CLEAR * a), -n, n, a, t) == 0
-            # inside the widening: counted as contact
-            assert oracle.plt_collide(base + n * (2 * t + 0.5 * SLACK * a), n, n, a, t) == 1
+            # no widening: a gap of 2^-17 a beyond 2 t is a separation
+            assert oracle.plt_collide(base + n * (2 * t + 2.0 ** -17 * a), n, n, a, t) == 0
 
 
 def test_disk_standing_on_disk():
@@ -247,7 +245,7 @@ def test_swap_and_rotation_invariance():
         dj = rng.normal(size=3)
         dj *= rng.uniform(0.05, 2.2) / np.linalg.norm(dj)
         c = oracle.plt_collide(dj, ni, nj, a, t)
-        assert oracle.plt_collide(-dj, nj, ni, a, t) == c  # exact: same operations
+        assert oracle.plt_collide(-dj, nj, ni, a, t) == c  # exact: the same operations in the midpoint frame
         # rigid rotation: the same answer unless the pair is within 1e-6 of contact
         if oracle.plt_collide(dj, ni, nj, a, t + 1e-6) == oracle.plt_collide(dj, ni, nj, a, t - 1e-6):
             R = random_rotation(rng)
@@ -298,9 +296,11 @@ def minimage(d, L):
     return d
 
 
-def brute_sweep(X, U, box, a0, t0, lam, c_m, c_r, N_l, seed, sweep):
+def brute_sweep(X, U, box, a0, t0, lam, c_m, c_r, N_l, seed, sweep, collide=None):
     """Alg 3 in the canonical order, each trial tested against every other
-    platelet (no cell list)."""
+    platelet (no cell list), with the reference's contact decision unless
+    another predicate is given."""
+    collide = collide or oracle.plt_collide
     X, U = X.copy(), U.copy()
     box = np.asarray(box, dtype=np.float64)
     cs = 2.5 * (lam * (a0 + t0)) + c_m
@@ -319,7 +319,7 @@ def brute_sweep(X, U, box, a0, t0, lam, c_m, c_r, N_l, seed, sweep):
     for pid in order:
         for l in range(N_l):
             q, u = oracle.plt_trial(seed, sweep, pid, l, box, c_m, c_r, X[pid], U[pid])
-            if not any(oracle.plt_collide(minimage(X[j] - q, box), u, U[j], a, t)
+            if not any(collide(minimage(X[j] - q, box), u, U[j], a, t)
                        for j in range(len(X)) if j != pid):
                 X[pid], U[pid] = q, u
                 acc += 1
@@ -482,3 +482,35 @@ def test_decision_monotone_in_threshold():
         dj *= rng.uniform(0.0, 2.4) / np.linalg.norm(dj)
         got = [oracle.plt_collide(dj, ni, nj, 1.0, t) for t in ts]
         assert all(a <= b for a, b in zip(got, got[1:])), got
+
+
+def test_rim_search_resolves_near_contacts_within_budget():
+    """The rim search decides near-contacts (thresholds 1e-4 and 1e-6 of
+    the rim's distance to the other disk away from it; thin and thick,
+    near-parallel and crossing disks) by its bound, well below its safety cap
+    of 2^20 evaluations per rim.  (A first-order bound needs about
+    1/sqrt(gap) arcs near a flat minimum, so the count grows as the gap
+    shrinks; the cap bounds it.)"""
+    rng = np.random.default_rng(41)
+    worst = {1e-4: 0, 1e-6: 0}
+    for _ in range(60):
+        ni, nj = rand_units(rng, 2)
+        if rng.uniform() < 0.3:
+            nj = unit(ni + 1e-3 * rng.normal(size=3))
+        dj = rng.normal(size=3)
+        dj *= rng.uniform(0.05, 2.1) / np.linalg.norm(dj)
+        # the rim's distance to the other disk, by bisection on the threshold
+        hi, lo = 4.0, 0.0
+        for _ in range(45):
+            mid = 0.5 * (hi + lo)
+            if oracle.plt_rim_near_disk(-0.5 * dj, ni, 1.0, 0.5 * dj, nj, 1.0, mid)[0]:
+                hi = mid
+            else:
+                lo = mid
+        for eps in worst:
+            # (lo = 0: the disks cross, every threshold is a contact)
+            for thr, expect in ((hi * (1 + eps), 1), (lo * (1 - eps), 0))[:2 if lo > 0 else 1]:
+                got, ev = oracle.plt_rim_near_disk(-0.5 * dj, ni, 1.0, 0.5 * dj, nj, 1.0, thr)
+                assert got == expect
+                worst[eps] = max(worst[eps], ev)
+    assert worst[1e-4] < 1 << 13 and worst[1e-6] < 1 << 16, worst
