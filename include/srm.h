@@ -230,6 +230,9 @@ typedef struct srm_state_info {
                                    the particles of the 3^d cells around the home
                                    cell other than the mover (the method's own
                                    candidate set, before any culling)               */
+    uint64_t near_fallback;     /* particles of sweep cells on the general path whose
+                                   near list exceeded its capacity and were tested
+                                   against every staged candidate instead         */
 } srm_state_info;
 
 srm_status srm_get_state(srm_rve *h, srm_state_info *out);

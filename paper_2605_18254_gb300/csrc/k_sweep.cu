@@ -502,6 +502,7 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
         }
         __syncwarp();
         const bool use_near = nn <= NEAR_CAP;
+        if (!use_near && lane == 0) atomicAdd(&st->near_fallback, 1ull);
         bool done = false;
         int l0 = 0;
         PT np;

@@ -338,7 +338,7 @@ srm_status member_load(Group &g, Member &mb, const Prep &q)
     s.it_result = s.it_k = s.it_shake = 0;
     s.it_overlap = s.moved_last = 0;
     s.status = 0;
-    s.pairs_sweep = s.pairs_check = s.stage_overflow = s.trials = s.pairs_alg5 = 0;
+    s.pairs_sweep = s.pairs_check = s.stage_overflow = s.trials = s.pairs_alg5 = s.near_fallback = 0;
     s.wait_limit = q.p.wait_limit == 0 ? (1 << 22) : q.p.wait_limit;
     mb.dim = q.dim;
     mb.n = q.n;
@@ -807,6 +807,7 @@ void fill_state(const Group &g, size_t r, srm_state_info *o)
     o->stage_overflow = s.stage_overflow;
     o->trials = s.trials;
     o->pairs_alg5 = s.pairs_alg5;
+    o->near_fallback = s.near_fallback;
     o->stage_capacity = g.cap;
 }
 

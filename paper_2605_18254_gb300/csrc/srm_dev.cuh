@@ -1,5 +1,5 @@
 // srm_dev.cuh -- device-side state of one RVE and the arithmetic shared by
-// the kernels: Philox4x64-10, the unit-vector sampler, periodic wrap, cell
+// the kernels: Philox4x32-10, the unit-vector sampler, periodic wrap, cell
 // coordinates, and the exact binary64 collision predicate.
 //
 // Every binary64 operation that decides a result is written with an explicit
@@ -78,6 +78,7 @@ struct RveDev {
     unsigned long long stage_overflow;  // cells whose culled stencil exceeded the staging capacity
     unsigned long long trials;          // trial moves evaluated by the sweeps
     unsigned long long pairs_alg5;      // trials x (particles of the 3^d cells around the home cell - 1)
+    unsigned long long near_fallback;   // particles whose near list exceeded its capacity (general path)
     uint32_t *done;       // [ncells_cap] epoch stamp of the last sweep that finished the cell
     int32_t wait_limit;   // polls of one dependency before the sweep gives up (< 0: none)
     // directions of trials 0 and 1 of every particle for the coming sweep,

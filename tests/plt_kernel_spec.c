@@ -24,7 +24,9 @@
  * V r sin(theta) and its in-plane excess at most V r: a certified lower
  * bound.  Each of a rim's 8 first-level arcs is bisected on its own (the
  * kernel spreads them over lanes) and counts as contact when still
- * undecided at level 20 or after 512 evaluations.  Built with
+ * undecided at level 20 or after 512 evaluations (a near-contact the
+ * bisection cannot resolve; spec_plt_collide32_reason tells those apart).
+ * Built with
  * gcc -O2 -ffp-contract=off, like the kernel's --fmad=false.
  */
 #include <math.h>
@@ -98,7 +100,8 @@ static void rim_point(const float cc[3], const float e1[3], const float e2[3], f
  * of level 3) of the circle (cc, e1, e2, a) within thr of the disk (cd, nd,
  * b)?  sn = sine of the angle between the two normals.  Depth-first
  * bisection, intervals [k w, (k+1) w) with w = 4 / 2^d, left half first.
- * Returns 1 (yes, or undecided at level 20 or after 512 evaluations) or 0;
+ * Returns 1 (yes), 2 (undecided at level 20 or after 512 evaluations,
+ * counted as contact) or 0;
  * *evals receives the number of midpoints evaluated.  The 8 intervals are
  * independent, so the answer for the whole rim is their OR in any order. */
 static int arc_near_disk_f(const float cc[3], const float e1[3], const float e2[3], float a, const float cd[3],
@@ -129,7 +132,7 @@ static int arc_near_disk_f(const float cc[3], const float e1[3], const float e2[
         if (!(hl * hl + el * el > thr2)) {
             if (d == PLT_DEPTH || ne >= PLT_EVALS) {
                 if (evals) *evals = ne;
-                return 1;
+                return 2; /* undecided: counted as contact */
             }
             d++;
             k = 2 * k;
@@ -198,4 +201,35 @@ int spec_plt_collide32(const double dj[3], const double ni[3], const double nj[3
     if (rim_near_disk_f(zero, ei1, ei2, af, d, v, af, sn, thr, NULL)) return 1;
     if (rim_near_disk_f(d, ej1, ej2, af, zero, u, af, sn, thr, NULL)) return 1;
     return 0;
+}
+
+/* Why spec_plt_collide32 decides as it does: 0 separated, 1 some rim point
+ * lies within the widened threshold, 2 contact only because some arc was
+ * still undecided at level 20 or after 512 evaluations (a near-contact its
+ * bisection could not resolve).  Evaluates all 16 arcs; nonzero exactly
+ * when spec_plt_collide32 returns 1. */
+int spec_plt_collide32_reason(const double dj[3], const double ni[3], const double nj[3], double a, double t)
+{
+    if (!spec_plt_collide32(dj, ni, nj, a, t)) return 0;
+    const float d[3] = {(float)dj[0], (float)dj[1], (float)dj[2]};
+    const float u[3] = {(float)ni[0], (float)ni[1], (float)ni[2]};
+    const float v[3] = {(float)nj[0], (float)nj[1], (float)nj[2]};
+    const float af = (float)a, tf = (float)t;
+    float thr = (tf + tf) + af * PLT_SLACK;
+    float c = dot3f(u, v);
+    float s2 = 1.0f - c * c;
+    if (s2 < 0.0f) s2 = 0.0f;
+    float sn = sqrtf(s2);
+    float ei1[3], ei2[3], ej1[3], ej2[3];
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    basis_f(u, ei1, ei2);
+    basis_f(v, ej1, ej2);
+    int why = 0;
+    for (int k0 = 0; k0 < 8; k0++) {
+        int r1 = arc_near_disk_f(zero, ei1, ei2, af, d, v, af, sn, thr, k0, NULL);
+        int r2 = arc_near_disk_f(d, ej1, ej2, af, zero, u, af, sn, thr, k0, NULL);
+        if (r1 == 1 || r2 == 1) return 1;
+        if (r1 == 2 || r2 == 2) why = 2;
+    }
+    return why;
 }

@@ -19,6 +19,7 @@ SRC = os.path.join(HERE, "plt_kernel_spec.c")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libplt_kernel_spec.so")
 SLACK = 2.0 ** -16  # threshold widening of the kernel, in units of the disk radius
+BUDGET_GAP = 2.0 ** -12  # largest gap (units of a) at which an exhausted bisection may report contact
 
 _lib = None
 _lock = threading.Lock()
@@ -36,8 +37,9 @@ def lib():
                 os.replace(tmp, SO)
             L = ctypes.CDLL(SO)
             P = ctypes.POINTER(ctypes.c_double)
-            L.spec_plt_collide32.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
-            L.spec_plt_collide32.restype = ctypes.c_int
+            for f in (L.spec_plt_collide32, L.spec_plt_collide32_reason):
+                f.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
+                f.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -50,6 +52,24 @@ def collide32(dj, ni, nj, a, t) -> int:
     P = ctypes.POINTER(ctypes.c_double)
     d, u, v = _v3(dj), _v3(ni), _v3(nj)
     return int(lib().spec_plt_collide32(d.ctypes.data_as(P), u.ctypes.data_as(P), v.ctypes.data_as(P), a, t))
+
+
+def reason(dj, ni, nj, a, t) -> int:
+    """0 separated; 1 a rim point within the widened threshold; 2 contact
+    only because a bisection arc stayed undecided (its budget ran out)."""
+    P = ctypes.POINTER(ctypes.c_double)
+    d, u, v = _v3(dj), _v3(ni), _v3(nj)
+    return int(lib().spec_plt_collide32_reason(d.ctypes.data_as(P), u.ctypes.data_as(P), v.ctypes.data_as(P), a, t))
+
+
+def confirmed_by_reference(oracle, dj, ni, nj, a, t) -> bool:
+    """A contact the specification reports and the binary64 reference does
+    not must be within the widening of touching (plus the binary32 rounding
+    of its inputs: 1.25 SLACK a), or -- when an arc's bisection ran out of
+    budget -- a near-contact within BUDGET_GAP a of touching."""
+    if oracle.plt_collide(dj, ni, nj, a, t + 0.5 * 1.25 * SLACK * a):
+        return True
+    return reason(dj, ni, nj, a, t) == 2 and bool(oracle.plt_collide(dj, ni, nj, a, t + 0.5 * BUDGET_GAP * a))
 
 
 def address() -> int:

@@ -2,10 +2,12 @@
 decision, tests/plt_kernel_spec.c) against the binary64 reference, on the CPU.
 
 The specification decides contact against 2 t + 2^-16 a in binary32, so it
-must find every contact of the reference (distance <= t_i + t_j), and every
+must find every contact of the reference (distance <= t_i + t_j).  Every
 contact only it reports must lie within the widening (plus the binary32
-rounding of its inputs) of touching: the reference reports contact for it at
-a threshold raised by 1.25 x 2^-16 a.  Plus: the reference's sweep run on the
+rounding of its inputs) of touching -- the reference reports contact for it
+at a threshold raised by 1.25 x 2^-16 a -- or be a near-contact whose
+bisection ran out of budget (counted as contact by the kernel), within
+2^-12 a of touching.  Plus: the reference's sweep run on the
 specification's predicate equals a brute-force sweep on the same predicate,
 which is what the GPU sweeps are compared with bit for bit."""
 import numpy as np
@@ -15,7 +17,6 @@ import oracle
 import plt_kernel_spec as spec
 from test_oracle_platelet import brute_sweep, rand_units, start_config
 
-ALLOW = 1.25 * spec.SLACK  # widening plus the binary32 rounding of the inputs, in units of a
 
 
 def pair_set(seed, m, a, t):
@@ -37,13 +38,13 @@ def one_sided(d, ni, nj, a, t):
     ref = np.array([oracle.plt_collide(d[k], ni[k], nj[k], a, t) for k in range(len(d))], dtype=np.uint8)
     got = np.array([spec.collide32(d[k], ni[k], nj[k], a, t) for k in range(len(d))], dtype=np.uint8)
     extra = np.nonzero((got == 1) & (ref == 0))[0]
-    near = [oracle.plt_collide(d[k], ni[k], nj[k], a, t + 0.5 * ALLOW * a) for k in extra]
+    near = [spec.confirmed_by_reference(oracle, d[k], ni[k], nj[k], a, t) for k in extra]
     return ref, got, extra, near
 
 
 @pytest.mark.parametrize("a,t", [(1.0, 1.0 / 199.0), (1.0, 0.1), (0.03, 0.0003)])
 def test_specification_is_one_sided_on_random_pairs(a, t):
-    d, ni, nj = pair_set(int(1 / t), 6000, a, t)
+    d, ni, nj = pair_set(int(1 / t), 20000, a, t)
     ref, got, extra, near = one_sided(d, ni, nj, a, t)
     assert 0.05 < ref.mean() < 0.95
     assert np.all(got[ref == 1] == 1), "a contact of the reference is missing"
@@ -85,3 +86,14 @@ def test_reference_sweep_on_specification_equals_brute_force():
         SX, SU = s.state()
         np.testing.assert_array_equal(SX, X)
         np.testing.assert_array_equal(SU, U)
+
+
+def test_budget_decided_contact_is_a_near_contact():
+    """A pair whose contact the kernel reports only because an arc's
+    bisection ran out of budget (found among the random thick pairs): the
+    reference separates it at 2 t, and confirms contact at 2 t + 2^-12 a."""
+    d, ni, nj = pair_set(10, 20000, 1.0, 0.1)
+    k = 16609
+    assert spec.collide32(d[k], ni[k], nj[k], 1.0, 0.1) == 1 and spec.reason(d[k], ni[k], nj[k], 1.0, 0.1) == 2
+    assert oracle.plt_collide(d[k], ni[k], nj[k], 1.0, 0.1) == 0
+    assert oracle.plt_collide(d[k], ni[k], nj[k], 1.0, 0.1 + 0.5 * spec.BUDGET_GAP) == 1
