@@ -50,6 +50,8 @@ namespace srm {
 constexpr int NEAR_CAP = 64;
 constexpr int PRE_NH = 32;    // home particles whose first trials are copied up front
 constexpr int PRE_TRIALS = 2; // trials drawn ahead of the sweep per particle
+constexpr int NL_CAP = 256;   // staged path: entries of a particle's near index list (in the hap area)
+static_assert(NL_CAP * 2 <= 32 * 16, "the near index list lives in the 32 x float4 hap area");
 
 template <bool F32>
 struct SweepSmem {
@@ -599,24 +601,33 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
 
 // ---------------------------------------------------------------------------
 // The staged path of one cell: every candidate of the stencil is copied to
-// shared memory (cp.async, 16 bytes per lane and copy), so that the cell's
-// service time -- which lies on the chain of the colour order -- holds one
-// memory round trip instead of a load per chunk:
-//  * cells not of lower colour (the home cell and those that wait for it)
-//    cannot change before this cell finishes, so they are copied before the
-//    wait; each lower-colour cell is copied by the lane that polled it, as
-//    soon as its stamp is seen;
-//  * FP32 form: candidates are then shifted into the home cell's frame;
-//  * near bits: per group of 32 home particles, one pass over the candidates
-//    marks every candidate within R_i + R_t + c_m of home particle i (plus
-//    c_m for home candidates, which may move before i's turn) -- a superset
-//    of everything a trial of i can touch -- and a ballot per particle turns
-//    the marks into one word per 32-candidate chunk;
-//  * each particle's trials test the marked candidates of every chunk, one
-//    chunk per lane, reading current positions (moves update the copies).
+// shared memory (cp.async, 16 bytes per copy), so that the cell's service
+// time -- which lies on the chain of the colour order -- holds one memory
+// round trip instead of a load per chunk, and the work that does not
+// depend on lower-colour cells is done before waiting for them:
+//  * the home cell and the cells of higher colour (which wait for this
+//    one) cannot change before this cell finishes; they are copied, culled
+//    (FP32 form: shifted into the home cell's frame) and compacted first;
+//    the positions of trials 0 and 1 of the home particles (pre-drawn
+//    directions, positions unchanged before each particle's turn) are
+//    formed, and both the near bits and the pre-tests of these trials are
+//    computed over these candidates -- all before the wait;
+//  * each lower-colour cell is copied by the lane that polled it as soon as
+//    its stamp is seen, into a list that starts on a 32-candidate chunk;
+//    after the last one: cull, near bits and pre-tests over those chunks;
+//  * near bits: per group of 32 home particles, lane i of a chunk marks
+//    home particle m when candidate i is within R_m + R_t + c_m of it (plus
+//    c_m for home candidates, which may move before m's turn) -- a superset
+//    of everything a trial of m can touch -- and a 32 x 32 bit transpose
+//    across the lanes gives each particle one word per chunk;
+//  * pre-tests: trials 0 and 1 of every particle against its marked
+//    candidates outside the home cell, which do not change while the cell
+//    runs; at a particle's turn only its marked home candidates remain;
+//  * later trials (drawn by the lanes) test every marked candidate, at
+//    current positions (moves update the copies).
 // The decisions are the predicate of Algorithm 5 on the same values as the
 // general path, so the results are the same.  Returns false, having issued
-// nothing, when the stencil holds more than cap candidates.
+// nothing, when the two lists do not fit cap candidates.
 // ---------------------------------------------------------------------------
 template <int DIM, bool F32>
 __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, unsigned char *base, int cap,
@@ -653,11 +664,13 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     const int cell = hx + st->gn[0] * (hy + st->gn[1] * hz);
     const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
     if (nh == 0) return true;  // nothing moves: nobody waits for an empty cell
-    int nst, center;
-    const uint32_t T = list_stencil(st, cs, hx, hy, hz, chi, S, nst, center);
-    if (T > (uint32_t)cap) return false;
+    int nst;
+    uint32_t Tn, Tl;
+    list_stencil_split(st, cs, hx, hy, hz, chi, S, nst, Tn, Tl);
+    const uint32_t Rl = (Tn + 31) / 32 * 32;  // first index of the lower-colour list
+    if (Rl + Tl > (uint32_t)cap) return false;
     const uint32_t epoch = (uint32_t)(st->sweep + 1);
-    // the pre-drawn directions of the cell's particles
+    // the pre-drawn directions of the cell's first particles
     const uint32_t npre = nh < (uint32_t)PRE_NH ? nh : (uint32_t)PRE_NH;
     {
         const PT *src = reinterpret_cast<const PT *>(st->dirs) + 2 * (size_t)hb;
@@ -665,58 +678,21 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
             cp_async16(reinterpret_cast<unsigned char *>(pre) + 16 * (size_t)e,
                        reinterpret_cast<const unsigned char *>(src) + 16 * (size_t)e);
     }
-    // id of home particle `lane` (the draws of later trials; loaded now,
-    // used after the wait)
+    // id of home particle `lane` (the draws of later trials)
     uint32_t my_pid = (uint32_t)lane < nh ? d.pid[hb + lane] : 0u;
-    // candidates of cells that cannot change before this cell finishes
-    for (uint32_t k = lane; k < T; k += 32) {
-        const int j = find_cell(S, nst, k);
-        cid[k] = (uint8_t)j;
-        if (!S.low[j]) {
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(pos + S.b[j] + (k - S.o[j]));
-#pragma unroll
-            for (int q = 0; q < PIECES; q++)
-                cp_async16(reinterpret_cast<unsigned char *>(cpos + k) + 16 * q, src + 16 * q);
-        }
-    }
-    // lower-colour cells: wait for each (bounded), then copy it
-    {
-        const int limit = st->wait_limit;
-        for (int j = lane; j < nst; j += 32) {
-            if (!S.low[j]) continue;
-            const uint32_t nj = S.o[j + 1] - S.o[j];
-            if (nj == 0) continue;
-            if (limit < 0) {
-                atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
-            } else {
-                const uint32_t *stamp = &st->done[S.cell[j]];
-                for (int it = 0; ld_relaxed(stamp) != epoch; it++) {
-                    if (it >= limit) {
-                        atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            // the producer's writes happen before its release store; this
-            // lane's relaxed load that saw it, followed by the fence,
-            // synchronises with it before the copies below
-            fence_acquire();
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(pos + S.b[j]);
-            unsigned char *dst = reinterpret_cast<unsigned char *>(cpos + S.o[j]);
-            for (uint32_t e = 0; e < nj * PIECES; e++) cp_async16(dst + 16 * (size_t)e, src + 16 * (size_t)e);
-        }
-    }
+    // copies of stencil cell j (by the lane that owns it) into a list
+    auto copy_cell = [&](int j, uint32_t list0) {
+        const uint32_t nj = S.n[j], o = list0 + S.o[j];
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(pos + S.b[j]);
+        unsigned char *dst = reinterpret_cast<unsigned char *>(cpos + o);
+        for (uint32_t e = 0; e < nj * PIECES; e++) cp_async16(dst + 16 * (size_t)e, src + 16 * (size_t)e);
+        for (uint32_t e = 0; e < nj; e++) cid[o + e] = (uint8_t)j;
+    };
+    for (int j = lane; j < nst; j += 32)
+        if (!S.low[j]) copy_cell(j, 0);
     cp_async_wait();
     __syncwarp();
-    // population of the 3^d cells around the home cell (Algorithm 5's own
-    // candidate set; the listed stencil is larger when H = 2)
-    uint32_t T3 = 0;
-    for (int j = lane; j < nst; j += 32)
-        if (S.sh[j][0] >= -1 && S.sh[j][0] <= 1 && S.sh[j][1] >= -1 && S.sh[j][1] <= 1 && S.sh[j][2] >= -1 &&
-            S.sh[j][2] <= 1)
-            T3 += S.o[j + 1] - S.o[j];
-    T3 = __reduce_add_sync(0xffffffffu, T3);
+
     // FP64 form: binary32 copies relative to the home corner, for the culls
     const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
     auto approx = [&](const PT &c) -> float4 {
@@ -740,51 +716,74 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     for (uint32_t m = lane; m < nh; m += 32) rh = fmaxf(rh, (float)cpos[m].w);
     for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
     // FP32 form: shift into the home cell's frame; both forms: keep the
-    // candidates that can reach the home cell (the cull of the general
-    // path), compacted in place -- a chunk's entries are read before any
-    // is written, and writes land at or below the chunk's first index.  The
-    // home particles lead the list and are all kept, at their own index.
-    uint32_t Tk = 0;
-    for (uint32_t k0 = 0; k0 < T; k0 += 32) {
-        const uint32_t k = k0 + (uint32_t)lane;
-        bool keep = false;
-        PT c;
-        if (k < T) {
-            c = cpos[k];
-            if constexpr (F32) {
-                const int j = cid[k];
-                c.x = __fmaf_rn((float)S.sh[j][0], w[0], c.x);
-                c.y = __fmaf_rn((float)S.sh[j][1], w[1], c.y);
-                c.z = __fmaf_rn((float)S.sh[j][2], w[2], c.z);
+    // candidates of [src, src + n) that can reach the home cell (the cull of
+    // the general path), compacted to dst <= src -- a chunk's entries are
+    // read before any is written, and writes land at or below the chunk's
+    // first index.  The home particles (indices below nh of the first list)
+    // are all kept, at their own index.
+    auto cull = [&](uint32_t src, uint32_t n, uint32_t dst) -> uint32_t {
+        uint32_t kept = 0;
+        for (uint32_t k0 = 0; k0 < n; k0 += 32) {
+            const uint32_t k = src + k0 + (uint32_t)lane;
+            bool keep = false;
+            PT c;
+            if (k0 + lane < n) {
+                c = cpos[k];
+                if constexpr (F32) {
+                    const int j = cid[k];
+                    c.x = __fmaf_rn((float)S.sh[j][0], w[0], c.x);
+                    c.y = __fmaf_rn((float)S.sh[j][1], w[1], c.y);
+                    c.z = __fmaf_rn((float)S.sh[j][2], w[2], c.z);
+                }
+                const float4 ca = approx(c);
+                const float r = rh + ca.w + 2.f * cmf;
+                keep = (src == 0 && k < nh) || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
             }
-            const float4 ca = approx(c);
-            const float r = rh + ca.w + 2.f * cmf;
-            keep = k < nh || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();
+            if (keep) cpos[dst + kept + __popc(bal & ((1u << lane) - 1u))] = c;
+            kept += __popc(bal);
+            __syncwarp();
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        if (keep) cpos[Tk + __popc(bal & ((1u << lane) - 1u))] = c;
-        Tk += __popc(bal);
-        __syncwarp();
+        return kept;
+    };
+    // first list, padded to a whole chunk with candidates out of reach
+    const uint32_t Tkn = cull(0, Tn, 0);
+    const uint32_t Tkp = (Tkn + 31) / 32 * 32;
+    if (Tkn + lane < Tkp) {
+        PT far;
+        far.x = far.y = far.z = (DT)1e30;
+        far.w = (DT)0;
+        cpos[Tkn + lane] = far;
     }
-    const uint32_t nchunks = (Tk + 31) / 32;
-    // trials tested at once: lanes form `tpar` groups of G lanes, lane
-    // (group t, position c) tests trial t against the marked candidates of
-    // chunk c
-    const int tpar = nchunks <= 4 ? 8 : (nchunks <= 8 ? 4 : (nchunks <= 16 ? 2 : 1));
-    const int G = 32 / tpar, tsub = lane / G, csub = lane % G;
-    for (uint32_t g0 = 0; g0 < nh; g0 += 32) {
-        const uint32_t gn = nh - g0 < 32u ? nh - g0 : 32u;
-        if (g0 > 0) my_pid = (uint32_t)lane < gn ? d.pid[hb + g0 + lane] : 0u;
+    // positions of trials 0 and 1 of the first home particles, in place of
+    // their directions
+    for (uint32_t pi = lane; pi < 2 * npre; pi += 32) {
+        const uint32_t m = pi >> 1;
+        if ((int)(pi & 1) >= N_l) continue;
+        const PT p = cpos[m];
+        const PT e = pre[pi];
+        PT q;
+        if constexpr (F32) {
+            q.x = trial_f32(p.x, cmf, e.x);
+            q.y = trial_f32(p.y, cmf, e.y);
+            q.z = DIM == 3 ? trial_f32(p.z, cmf, e.z) : p.z;
+        } else {
+            q.x = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, e.x)), st->L[0]);
+            q.y = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, e.y)), st->L[1]);
+            q.z = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, e.z)), st->L[2]) : p.z;
+        }
+        q.w = (DT)0;
+        pre[pi] = q;
+    }
+    __syncwarp();
+    // near bits of home particles g0 .. g0+gn-1 over chunks [c0, c1)
+    auto mark = [&](uint32_t g0, uint32_t gn, uint32_t c0, uint32_t c1, uint32_t Tk) {
         if constexpr (!F32) {
             if ((uint32_t)lane < gn) hap[lane] = approx(cpos[g0 + lane]);
             __syncwarp();
         }
-        // near bits: lane i of chunk ch marks bit mm when candidate ch*32+i
-        // is within R + R_t + c_m (+ c_m for home candidates) of home
-        // particle g0+mm; the 32 x 32 bit matrix is then transposed across
-        // the lanes, so that lane mm holds the chunk's word of particle g0+mm
-        for (uint32_t ch = 0; ch < nchunks; ch++) {
+        for (uint32_t ch = c0; ch < c1; ch++) {
             const uint32_t k = ch * 32 + (uint32_t)lane;
             uint32_t bits = 0;
             if (k < Tk) {
@@ -810,32 +809,23 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
             if ((uint32_t)lane < gn) wbits[ch * 32 + lane] = bits;
         }
         __syncwarp();
-        // pre-tests: trials 0 and 1 of every particle of the group against
-        // its marked candidates outside the home cell -- positions that do
-        // not change while this cell runs, and trial positions that depend
-        // only on the particle's own position, unchanged before its turn --
-        // one lane per (particle, trial): lane pi of round r takes particle
-        // 16 r + pi / 2, trial pi % 2; bit pi of shit[r] = that trial hits
-        for (uint32_t r0 = 0; r0 < 2 * gn; r0 += 32) {
+    };
+    // pre-tests of trials 0 and 1 of the first home particles against their
+    // marked candidates outside the home cell in chunks [c0, c1): lane pi of
+    // round r takes particle 16 r + pi / 2, trial pi % 2; bit pi of shit[r]
+    // = that trial hits (or-ed over the calls)
+    auto pretest = [&](uint32_t c0, uint32_t c1) {
+        for (uint32_t r0 = 0; r0 < 2 * npre; r0 += 32) {
             const uint32_t pi = r0 + (uint32_t)lane;
-            const uint32_t mm = pi >> 1, m = g0 + mm;
-            const int tt = (int)(pi & 1);
+            const uint32_t mm = pi >> 1;
             bool hit = false;
-            double q[3] = {0.0, 0.0, 0.0};
-            float qf[3] = {0.f, 0.f, 0.f};
-            if (pi < 2 * gn && m < (uint32_t)PRE_NH && tt < N_l) {
-                const PT p = cpos[m];
-                const PT e = pre[PRE_TRIALS * m + tt];
-                if constexpr (F32) {
-                    qf[0] = trial_f32(p.x, cmf, e.x);
-                    qf[1] = trial_f32(p.y, cmf, e.y);
-                    qf[2] = DIM == 3 ? trial_f32(p.z, cmf, e.z) : p.z;
-                } else {
-                    q[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, e.x)), st->L[0]);
-                    q[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, e.y)), st->L[1]);
-                    q[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, e.z)), st->L[2]) : p.z;
-                }
-                for (uint32_t ch = 0; ch < nchunks && !hit; ch++) {
+            if (pi < 2 * npre && (int)(pi & 1) < N_l) {
+                const float Rm = (float)cpos[mm].w;
+                const double Rd = (double)cpos[mm].w;
+                const PT qq = pre[pi];
+                const float qf[3] = {(float)qq.x, (float)qq.y, (float)qq.z};
+                const double qd[3] = {(double)qq.x, (double)qq.y, (double)qq.z};
+                for (uint32_t ch = c0; ch < c1 && !hit; ch++) {
                     uint32_t wd = wbits[ch * 32 + mm];
                     // drop the home candidates (indices below nh)
                     if (ch * 32 < nh) wd &= nh - ch * 32 >= 32 ? 0u : ~((1u << (nh - ch * 32)) - 1u);
@@ -844,20 +834,78 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                         wd &= wd - 1;
                         const PT c = cpos[ch * 32 + bt];
                         cc.examined++;
-                        if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
-                        else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        if constexpr (F32) hit = hit_f32<DIM>(qf, Rm, c, g1);
+                        else hit = collide_exact<DIM>(qd, Rd, c.x, c.y, c.z, c.w, st->L, st->halfL);
                     }
                 }
             }
             const uint32_t hbits = __ballot_sync(0xffffffffu, hit);
-            if (lane == 0) shit[r0 >> 5] = hbits;
-            // the trial position replaces its direction (read at the turn)
-            if (pi < 2 * gn && m < (uint32_t)PRE_NH && tt < N_l) {
-                if constexpr (F32) pre[PRE_TRIALS * m + tt] = make_float4(qf[0], qf[1], qf[2], 0.f);
-                else pre[PRE_TRIALS * m + tt] = make_double4_32a(q[0], q[1], q[2], 0.0);
-            }
+            if (lane == 0) shit[r0 >> 5] = (c0 == 0 ? 0u : shit[r0 >> 5]) | hbits;
         }
         __syncwarp();
+    };
+    const uint32_t gn0 = nh < 32u ? nh : 32u;
+    mark(0, gn0, 0, Tkp / 32, Tkp);
+    pretest(0, Tkp / 32);
+
+    // lower-colour cells: wait for each (bounded), then copy it
+    {
+        const int limit = st->wait_limit;
+        for (int j = lane; j < nst; j += 32) {
+            if (!S.low[j] || S.n[j] == 0) continue;
+            if (limit < 0) {
+                atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
+            } else {
+                const uint32_t *stamp = &st->done[S.cell[j]];
+                for (int it = 0; ld_relaxed(stamp) != epoch; it++) {
+                    if (it >= limit) {
+                        atomicExch(&st->status, STATUS_WAIT_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            // the producer's writes happen before its release store; this
+            // lane's relaxed load that saw it, followed by the fence,
+            // synchronises with it before the copies below
+            fence_acquire();
+            copy_cell(j, Rl);
+        }
+    }
+    cp_async_wait();
+    __syncwarp();
+    const uint32_t Tk = Tkp + cull(Rl, Tl, Tkp);
+    const uint32_t nchunks = (Tk + 31) / 32;
+    if (nchunks > Tkp / 32) {
+        mark(0, gn0, Tkp / 32, nchunks, Tk);
+        pretest(Tkp / 32, nchunks);
+    }
+    // population of the 3^d cells around the home cell (Algorithm 5's own
+    // candidate set; the listed stencil is larger when H = 2)
+    uint32_t T3 = 0;
+    for (int j = lane; j < nst; j += 32)
+        if (S.sh[j][0] >= -1 && S.sh[j][0] <= 1 && S.sh[j][1] >= -1 && S.sh[j][1] <= 1 && S.sh[j][2] >= -1 &&
+            S.sh[j][2] <= 1)
+            T3 += S.n[j];
+    T3 = __reduce_add_sync(0xffffffffu, T3);
+    // trials tested at once: lanes form `tpar` groups of G lanes, lane
+    // (group t, position c) tests trial t against the marked candidates of
+    // chunk c
+    const int tpar = nchunks <= 4 ? 8 : (nchunks <= 8 ? 4 : (nchunks <= 16 ? 2 : 1));
+    const int G = 32 / tpar, tsub = lane / G, csub = lane % G;
+    // a particle's near list, as candidate indices (the binary32 copies of
+    // the FP64 form's home particles are no longer needed here)
+    uint16_t *nlist = reinterpret_cast<uint16_t *>(hap);
+    // the word of chunk `lane` of home particle mm of the current group
+    auto word_all = [&](uint32_t mm) -> uint32_t {
+        return (uint32_t)lane < nchunks ? wbits[lane * 32 + mm] : 0u;
+    };
+    for (uint32_t g0 = 0; g0 < nh; g0 += 32) {
+        const uint32_t gn = nh - g0 < 32u ? nh - g0 : 32u;
+        if (g0 > 0) {
+            my_pid = (uint32_t)lane < gn ? d.pid[hb + g0 + lane] : 0u;
+            mark(g0, gn, 0, nchunks, Tk);
+        }
         // the group's particles, ascending id
         for (uint32_t m = g0; m < g0 + gn; m++) {
             const uint32_t gi = hb + m;
@@ -954,6 +1002,30 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                 }
                 l0 = lmax;
             }
+            // later trials: the particle's marked candidates (every chunk,
+            // home included) as one index list, so that lanes (t, j) test
+            // trial t against list entries j, j + 4, ... -- eight trials at
+            // once; lists longer than NL_CAP keep the chunk rounds below
+            uint32_t nn = 0;
+            if (!done && l0 < N_l) {
+                const uint32_t cnt = __popc(word_all(m - g0));
+                uint32_t inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                nn = __shfl_sync(0xffffffffu, inc, 31);
+                if (nn <= (uint32_t)NL_CAP) {
+                    uint32_t wd = word_all(m - g0), at = inc - cnt;
+                    while (wd) {
+                        const int bt = __ffs(wd) - 1;
+                        wd &= wd - 1;
+                        nlist[at++] = (uint16_t)(lane * 32 + bt);
+                    }
+                }
+                __syncwarp();
+            }
             while (!done && l0 < N_l) {
                 // later trials eight at a time, drawn by the lanes
                 const int lmax = N_l - l0 < 8 ? N_l - l0 : 8;
@@ -973,6 +1045,51 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                     }
                 }
                 l0 += lmax;
+                if (nn <= (uint32_t)NL_CAP) {
+                    // lane (t, j): trial t = lane / 4 against entries j, j + 4, ...
+                    const int tr = lane >> 2, j0 = lane & 3;
+                    const int src = tr < lmax ? tr : 0;
+                    double q[3] = {0.0, 0.0, 0.0};
+                    float qf[3] = {0.f, 0.f, 0.f};
+                    if constexpr (F32) {
+                        qf[0] = __shfl_sync(0xffffffffu, qs[0], src);
+                        qf[1] = __shfl_sync(0xffffffffu, qs[1], src);
+                        qf[2] = __shfl_sync(0xffffffffu, qs[2], src);
+                    } else {
+                        q[0] = __shfl_sync(0xffffffffu, qt[0], src);
+                        q[1] = __shfl_sync(0xffffffffu, qt[1], src);
+                        q[2] = __shfl_sync(0xffffffffu, qt[2], src);
+                    }
+                    bool hit = false;
+                    if (tr < lmax) {
+                        for (uint32_t jj = j0; jj < nn && !hit; jj += 4) {
+                            const PT c = cpos[nlist[jj]];
+                            cc.examined++;
+                            if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
+                            else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        }
+                    }
+                    const unsigned hb_ = __ballot_sync(0xffffffffu, hit);
+                    int acc = -1;
+                    for (int tt = 0; tt < lmax; tt++)
+                        if (!((hb_ >> (4 * tt)) & 15u)) {
+                            acc = tt;
+                            break;
+                        }
+                    cc.trials += acc >= 0 ? acc + 1 : lmax;
+                    if (acc >= 0) {
+                        if constexpr (F32) {
+                            np = make_float4(__shfl_sync(0xffffffffu, qs[0], acc), __shfl_sync(0xffffffffu, qs[1], acc),
+                                             __shfl_sync(0xffffffffu, qs[2], acc), p.w);
+                        } else {
+                            np = make_double4_32a(__shfl_sync(0xffffffffu, qt[0], acc),
+                                                  __shfl_sync(0xffffffffu, qt[1], acc),
+                                                  __shfl_sync(0xffffffffu, qt[2], acc), p.w);
+                        }
+                        done = true;
+                    }
+                    continue;
+                }
                 // rounds of tpar trials; the first clean trial of a round,
                 // in trial order, is the move
                 for (int lb = 0; lb < lmax && !done; lb += tpar) {

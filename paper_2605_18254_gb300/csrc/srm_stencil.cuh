@@ -15,6 +15,7 @@ struct StencilSmem {
     int32_t cell[MAX_ST];    // linear index of stencil cell j
     int8_t sh[MAX_ST][3];    // unwrapped shift of cell j from the home cell
     uint8_t low[MAX_ST];     // 1: cell j has a lower colour than the home cell
+    uint32_t n[MAX_ST];      // particles of cell j (staged path)
 };
 
 constexpr size_t ST_HDR = (sizeof(StencilSmem) + 31) / 32 * 32;
@@ -75,6 +76,63 @@ __device__ __forceinline__ uint32_t list_stencil(const RveDev *st, const uint32_
     if (lane == 0) S.o[nst] = carry;
     __syncwarp();
     return carry;
+}
+
+// The stencil of the staged path: as list_stencil, but the candidates of
+// the cells that are not of lower colour (the home cell first) are numbered
+// 0 .. n_other-1 and those of the lower-colour cells 0 .. n_low-1 in a second
+// list (o[j] indexes the list of cell j's kind); n[j] holds the counts.
+__device__ __forceinline__ void list_stencil_split(const RveDev *st, const uint32_t *cs, int hx, int hy, int hz,
+                                                   int chi, StencilSmem &S, int &nst, uint32_t &n_other,
+                                                   uint32_t &n_low)
+{
+    const int lane = threadIdx.x & 31;
+    const int H0 = st->H[0], H1 = st->H[1], H2 = st->H[2];
+    const int w0 = 2 * H0 + 1, w1 = 2 * H1 + 1, w2 = 2 * H2 + 1;
+    nst = w0 * w1 * w2;
+    const int center = H0 + w0 * (H1 + w1 * H2);
+    const int n0 = st->gn[0], n1 = st->gn[1], n2 = st->gn[2];
+    uint32_t carry_o = 0, carry_l = 0;
+    for (int base = 0; base < nst; base += 32) {
+        const int j = base + lane;
+        uint32_t co = 0, cl = 0;
+        bool lo = false;
+        if (j < nst) {
+            const int jj = j == 0 ? center : (j == center ? 0 : j);
+            const int dx = jj % w0 - H0, dy = (jj / w0) % w1 - H1, dz = jj / (w0 * w1) - H2;
+            int cx = hx + dx, cy = hy + dy, cz = hz + dz;
+            cx = cx < 0 ? cx + n0 : (cx >= n0 ? cx - n0 : cx);
+            cy = cy < 0 ? cy + n1 : (cy >= n1 ? cy - n1 : cy);
+            cz = cz < 0 ? cz + n2 : (cz >= n2 ? cz - n2 : cz);
+            const int c = cx + n0 * (cy + n1 * cz);
+            const uint32_t b = cs[c];
+            const uint32_t cnt = cs[c + 1] - b;
+            lo = cx % 3 + 3 * (cy % 3) + 9 * (cz % 3) < chi;
+            S.b[j] = b;
+            S.n[j] = cnt;
+            S.cell[j] = c;
+            S.low[j] = (uint8_t)lo;
+            S.sh[j][0] = (int8_t)dx;
+            S.sh[j][1] = (int8_t)dy;
+            S.sh[j][2] = (int8_t)dz;
+            (lo ? cl : co) = cnt;
+        }
+        uint32_t io = co, il = cl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yo = __shfl_up_sync(0xffffffffu, io, o), yl = __shfl_up_sync(0xffffffffu, il, o);
+            if (lane >= o) {
+                io += yo;
+                il += yl;
+            }
+        }
+        if (j < nst) S.o[j] = lo ? carry_l + il - cl : carry_o + io - co;
+        carry_o += __shfl_sync(0xffffffffu, io, 31);
+        carry_l += __shfl_sync(0xffffffffu, il, 31);
+    }
+    n_other = carry_o;
+    n_low = carry_l;
+    __syncwarp();
 }
 
 // Stencil cell holding flattened candidate k (binary search over offsets).

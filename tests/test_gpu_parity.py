@@ -257,14 +257,33 @@ def test_fp64_clustered_polydisperse_iterations_bit_exact(capacity):
         assert g.state()["stage_overflow"] > 0
 
 
-def bimodal_dense(n_big=170, n_small=27000, seed=31):
-    """3D: large spheres (R = 2) among small ones (R = 0.4) at volume
-    fraction 0.3, c_m = 0.8, on a 6 x 6 x 6 grid: a large sphere's near list
-    (centres within R + R_t + c_m) holds more than 64 small spheres."""
-    r = np.concatenate([np.full(n_big, 2.0), np.full(n_small, 0.4)])
-    vol = float(np.sum(4.0 / 3.0 * math.pi * r ** 3))
-    L = (vol / 0.3) ** (1.0 / 3.0)
-    x = srm_inputs.rsa(3, (L, L, L), r, seed)
+def bimodal_dense(n_big=24, per=120, seed=31, L=36.0):
+    """3D: large spheres (R = 2), each ringed by `per` small ones (R = 0.4)
+    in a shell of radii 2.41 .. 3.1, in a box of 6 x 6 x 6 cells; c_m = 0.8:
+    a large sphere's near list (centres within R + R_t + c_m = 3.2) holds
+    `per` > 64 small spheres, and its stencil far exceeds a staging capacity
+    of 64."""
+    rng = np.random.default_rng(seed)
+    big = []
+    while len(big) < n_big:
+        p = rng.uniform(0, L, 3)
+        d = np.array(big) - p if big else np.zeros((0, 3))
+        d -= np.round(d / L) * L
+        if not big or np.min(np.sum(d * d, axis=1)) >= 9.0 ** 2:
+            big.append(p)
+    small = []
+    for c in big:
+        mine = []
+        for _ in range(20000):
+            if len(mine) >= per:
+                break
+            v = rng.normal(size=3)
+            q = c + v / np.linalg.norm(v) * rng.uniform(2.41, 3.1)
+            if not mine or np.min(np.sum((np.array(mine) - q) ** 2, axis=1)) > 0.8 ** 2 * (1 + 1e-9):
+                mine.append(q)
+        small += mine
+    x = np.mod(np.array(big + small), L)
+    r = np.concatenate([np.full(n_big, 2.0), np.full(len(small), 0.4)])
     return srm_inputs.Workload("bimodal", 3, (L, L, L), r, x, 0.35, seed, c_m=0.8)
 
 
@@ -272,11 +291,11 @@ def test_fp64_near_list_overflow_bit_exact():
     """Stencils far beyond the staging capacity (64) and near lists beyond
     theirs: the general path reads the unstaged candidates from global
     memory and tests those particles' trials against every candidate; both
-    sweeps equal the reference bit for bit.  A cell takes milliseconds
-    here, so the neighbour waits get a larger limit, and two trials per
-    particle keep the run short."""
+    sweeps equal the reference bit for bit (and the state counters show
+    that both fallbacks ran)."""
     w = bimodal_dense()
-    g, o = pair(w, N_l=2, wait_limit=1 << 28)
+    assert oracle.grid(3, w.box, 1.02, 2.0, w.c_m)[0].tolist() == [6, 6, 6]
+    g, o = pair(w, wait_limit=1 << 26)
     g.set_tuning(1, 64)
     g.set_scale(1.02)
     o.lam = 1.02
