@@ -91,7 +91,15 @@ typedef struct srm_params {
                              /* sweep before the run fails with                  */
                              /* SRM_E_DEVICE_TIMEOUT (0: 2^22; < 0: give up at   */
                              /* the first dependency -- for tests of the path)   */
-    int32_t reserved;
+    int32_t images;          /* periodicity (Section 2): 0 the minimum image of  */
+                             /* Alg 5; 1 image particles, the other way the      */
+                             /* paper names: a candidate near a face is tested   */
+                             /* at its periodic image x + s L (one rounding per  */
+                             /* axis), then by the plain difference.  Decides    */
+                             /* the FP64 form's arithmetic, certification        */
+                             /* included; the FP32 form's cell-relative offsets  */
+                             /* already place every candidate at its image       */
+                             /* beside the home cell, so it is the same there    */
 } srm_params;
 
 /* Fills p with the defaults: c_w = 0.01, c_m = 0 (must be set), N_k = N_l =

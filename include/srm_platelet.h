@@ -68,6 +68,12 @@ typedef struct srm_plt_params {
                          /* before SRM_E_DEVICE_TIMEOUT (0: 2^22; < 0: give    */
                          /* up at the first dependency -- for tests)           */
     uint64_t sweep0;     /* first value of the sweep counter                   */
+    int32_t images;      /* periodicity (Section 2): 0 the minimum image of    */
+                         /* the centre difference; 1 image platelets: the      */
+                         /* difference to a platelet near a face is taken to   */
+                         /* its periodic image, (x_j + s L) - x_i, one         */
+                         /* rounding per axis                                  */
+    int32_t reserved;
 } srm_plt_params;
 
 /* Defaults: c_w = 0.01, c_m = 0 (must be set), c_r = 0, N_k = N_l =

@@ -33,7 +33,8 @@ def build(force: bool = False) -> str:
     """Compile the reference with plain gcc, no FMA contraction, no fast-math."""
     os.makedirs(_BUILD, exist_ok=True)
     srcs = [_SRC, _SRC_A, _SRC_P]
-    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in srcs):
+    deps = srcs + [os.path.join(_HERE, "orc_images.h")]
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in deps):
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                                "-shared", "-o", tmp] + srcs + ["-lm"])
@@ -60,6 +61,9 @@ def _load():
                 "orc_set_lambda": ([ctypes.c_void_p, _d], None),
                 "orc_get_sweep": ([ctypes.c_void_p], _u64),
                 "orc_set_margin": ([ctypes.c_void_p, P(_d)], None),
+                "orc_set_images": ([ctypes.c_void_p, _int], None),
+                "orc_images_verify": ([ctypes.c_void_p, P(_d)], _i64),
+                "orc_images_count": ([ctypes.c_void_p], _i64),
                 "orc_get_counters": ([ctypes.c_void_p, P(_i64)], None),
                 "orc_phi": ([ctypes.c_void_p, _d], _d),
                 "orc_lambda_for_phi": ([ctypes.c_void_p, _d], _d),
@@ -78,6 +82,8 @@ def _load():
                 "orc_plt_point_disk": ([P(_d), P(_d), P(_d), _d], _d),
                 "orc_plt_rim_near_disk": ([P(_d), P(_d), _d, P(_d), P(_d), _d, _d, P(_int)], _int),
                 "orc_plt_set_contact": ([ctypes.c_void_p, ctypes.c_void_p], None),
+                "orc_plt_set_images": ([ctypes.c_void_p, _int], None),
+                "orc_plt_images_verify": ([ctypes.c_void_p], _i64),
                 "orc_plt_collide": ([P(_d), P(_d), P(_d), _d, _d], _int),
                 "orc_plt_trial": ([_u64, _u64, _u64, _u64, P(_d), _d, _d, P(_d), P(_d), P(_d), P(_d)], None),
                 "orc_plt_create": ([P(_d), _i64, P(_d), P(_d), _d, _d, _d, _d, _d, _d, _d, _int, _int, _int,
@@ -204,7 +210,9 @@ class System:
     scale lambda (R_i = lambda r_i), target scale, and the SRM parameters."""
 
     def __init__(self, dim, box, x, r, lam=1.0, lam_t=None, target_phi=None, c_w=0.01,
-                 c_m=0.01, N_k=10, N_l=10, N_shake=10, seed=1, sweep=0, literal=False):
+                 c_m=0.01, N_k=10, N_l=10, N_shake=10, seed=1, sweep=0, literal=False, images=False):
+        """images: periodicity by explicit image particles instead of the
+        minimum image (Section 2; see orc_set_images in srm_oracle.c)."""
         if not 1 <= N_l < (1 << 16):
             raise ValueError("N_l must be in [1, 65535] (the try index takes 16 counter bits)")
         lib = _load()
@@ -223,6 +231,8 @@ class System:
                                      lt, c_w, c_m, N_k, N_l, N_shake, seed, sweep,
                                      1 if literal else 0)
         self._margin = None
+        self.images = bool(images)
+        lib.orc_set_images(self._h, 1 if images else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -269,6 +279,15 @@ class System:
     @property
     def margins(self):
         return None if self._margin is None else self._margin.copy()
+
+    def images_verify(self) -> int:
+        """Mismatching padded cells between the image entries kept move by
+        move during the last sweep of P and a rebuild from P (0: consistent)."""
+        x = np.ascontiguousarray(self.x, dtype=np.float64).reshape(-1)
+        return int(_lib.orc_images_verify(self._h, _dp(x)))
+
+    def images_count(self) -> int:
+        return int(_lib.orc_images_count(self._h))
 
     def counters(self) -> dict:
         c = np.zeros(5, dtype=np.int64)
@@ -362,10 +381,11 @@ class PlateletSystem:
     rotation rate c_r."""
 
     def __init__(self, box, x, u, a0, t0, lam=1.0, lam_t=None, c_w=0.01, c_m=0.01, c_r=0.0, N_k=10, N_l=10,
-                 N_shake=10, seed=1, sweep=0, contact=None):
+                 N_shake=10, seed=1, sweep=0, contact=None, images=False):
         """contact: address of another contact predicate with the signature
         of orc_plt_collide for the sweeps and checks (tests only; None: the
-        reference's binary64 decision)."""
+        reference's binary64 decision).  images: periodicity by image
+        platelets instead of the minimum image."""
         if not 1 <= N_l < (1 << 16):
             raise ValueError("N_l must be in [1, 65535] (the try index takes 16 counter bits)")
         if not 0.0 <= c_r < 1.0:
@@ -380,6 +400,7 @@ class PlateletSystem:
                                      lam if lam_t is None else lam_t, c_w, c_m, c_r, N_k, N_l, N_shake, seed, sweep)
         if contact is not None:
             lib.orc_plt_set_contact(self._h, contact)
+        lib.orc_plt_set_images(self._h, 1 if images else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -421,6 +442,9 @@ class PlateletSystem:
 
     def run(self, max_iters: int = 1 << 40) -> int:
         return int(_lib.orc_plt_run(self._h, max_iters))
+
+    def images_verify(self) -> int:
+        return int(_lib.orc_plt_images_verify(self._h))
 
     def pairs_brute(self):
         X, U = self.state()

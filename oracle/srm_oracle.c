@@ -33,12 +33,17 @@
  *   - the order of Alg 3's "for each particle" is the canonical coloured
  *     order: for colour chi = sum_a (c_a mod 3) 3^a ascending, for cells of
  *     that colour in lexicographic order, particles of the cell by ascending
- *     id.  A "literal" mode keeps plain id order (Alg 3 as printed).
+ *     id.  A "literal" mode keeps plain id order (Alg 3 as printed);
+ *   - periodicity: the minimum-image convention of Alg 5 by default; an
+ *     "images" mode takes the other way Section 2 names, explicit image
+ *     particles (see orc_set_images below).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include "orc_images.h"
 
 /* ---------------------------------------------------------------------------
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -172,6 +177,10 @@ typedef struct orc_sys {
     int64_t iters, accepted_iters, shake_iters, moves_accepted;
     /* diagnostics for the FP32 tolerance tests (NULL when not wanted) */
     double *margin;
+    /* periodicity by image particles (orc_images.h) instead of the
+     * minimum image */
+    int images;
+    orc_imgtab img;
 } orc_sys;
 
 static void bin(orc_sys *s, const double *X, const double lam_grid)
@@ -200,6 +209,196 @@ static void bin(orc_sys *s, const double *X, const double lam_grid)
     free(cell_of);
 }
 
+/* ---------------------------------------------------------------------------
+ * Image particles (Section 2: the alternative to the minimum image, "after
+ * each particle translation, boundary crossings are detected, and the
+ * corresponding periodic images are added or removed"): the table of
+ * orc_images.h.  A move removes the mover's entries and inserts those of its
+ * new position, so the entries are never stale; collision tests take the
+ * 3^d padded cells around the tested position's cell and plain (not
+ * minimum-image) differences q - (x_t + s L).  The sweep order still comes
+ * from the binning of the sweep's start.
+ * ------------------------------------------------------------------------- */
+static void tab_cell_of(const orc_imgtab *t, const double *x, int64_t c[3])
+{
+    c[0] = c[1] = c[2] = 0;
+    for (int a = 0; a < t->dim; a++) c[a] = cell_coord(x[a], t->w[a], t->n[a]);
+}
+
+static void tab_insert(orc_imgtab *t, int64_t id, const int8_t *sh, int64_t pc)
+{
+    if (t->cnt[pc] == t->cap[pc]) {
+        t->cap[pc] = t->cap[pc] ? 2 * t->cap[pc] : 8;
+        t->id[pc] = (int64_t *)realloc(t->id[pc], sizeof(int64_t) * (size_t)t->cap[pc]);
+        t->sh[pc] = (int8_t *)realloc(t->sh[pc], 3 * (size_t)t->cap[pc]);
+    }
+    int64_t k = t->cnt[pc]++;
+    t->id[pc][k] = id;
+    memcpy(&t->sh[pc][3 * k], sh, 3);
+}
+
+static void tab_remove(orc_imgtab *t, int64_t id, const int8_t *sh, int64_t pc)
+{
+    for (int64_t k = 0; k < t->cnt[pc]; k++)
+        if (t->id[pc][k] == id && memcmp(&t->sh[pc][3 * k], sh, 3) == 0) {
+            int64_t last = --t->cnt[pc];
+            t->id[pc][k] = t->id[pc][last];
+            memcpy(&t->sh[pc][3 * k], &t->sh[pc][3 * last], 3);
+            return;
+        }
+    abort(); /* an entry that should exist is missing: a bug of this file */
+}
+
+/* Calls fn for each entry (shift, padded cell) of particle id in cell c. */
+static void tab_entries(orc_imgtab *t, const int64_t c[3], int64_t id,
+                        void (*fn)(orc_imgtab *, int64_t, const int8_t *, int64_t))
+{
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < t->dim; a++) {
+        lo[a] = c[a] == t->n[a] - 1 ? -1 : 0;
+        hi[a] = c[a] == 0 ? 1 : 0;
+    }
+    for (int sz = lo[2]; sz <= hi[2]; sz++)
+        for (int sy = lo[1]; sy <= hi[1]; sy++)
+            for (int sx = lo[0]; sx <= hi[0]; sx++) {
+                const int8_t sh[3] = {(int8_t)sx, (int8_t)sy, (int8_t)sz};
+                int64_t pc = 0, mul = 1;
+                for (int a = 0; a < 3; a++) {
+                    pc += (a < t->dim ? c[a] + sh[a] * t->n[a] + 1 : 0) * mul;
+                    mul *= t->pn[a];
+                }
+                fn(t, id, sh, pc);
+            }
+}
+
+void orc_imgtab_free(orc_imgtab *t)
+{
+    for (int64_t c = 0; c < t->pcells; c++) {
+        free(t->id[c]);
+        free(t->sh[c]);
+    }
+    free(t->id);
+    free(t->sh);
+    free(t->cnt);
+    free(t->cap);
+    t->id = NULL;
+    t->sh = NULL;
+    t->cnt = t->cap = NULL;
+    t->pcells = 0;
+}
+
+void orc_imgtab_build(orc_imgtab *t, int dim, const int64_t n[3], const double w[3], const double *X, int64_t N)
+{
+    orc_imgtab_free(t);
+    t->dim = dim;
+    for (int a = 0; a < 3; a++) {
+        t->n[a] = n[a];
+        t->w[a] = w[a];
+        t->pn[a] = a < dim ? n[a] + 2 : 1;
+    }
+    t->pcells = t->pn[0] * t->pn[1] * t->pn[2];
+    t->cnt = (int64_t *)calloc((size_t)t->pcells, sizeof(int64_t));
+    t->cap = (int64_t *)calloc((size_t)t->pcells, sizeof(int64_t));
+    t->id = (int64_t **)calloc((size_t)t->pcells, sizeof(int64_t *));
+    t->sh = (int8_t **)calloc((size_t)t->pcells, sizeof(int8_t *));
+    for (int64_t i = 0; i < N; i++) {
+        int64_t c[3];
+        tab_cell_of(t, &X[i * dim], c);
+        tab_entries(t, c, i, tab_insert);
+    }
+}
+
+void orc_imgtab_move(orc_imgtab *t, int64_t id, const double *old, const double *new_)
+{
+    int64_t c0[3], c1[3];
+    tab_cell_of(t, old, c0);
+    tab_cell_of(t, new_, c1);
+    tab_entries(t, c0, id, tab_remove);
+    tab_entries(t, c1, id, tab_insert);
+}
+
+int64_t orc_imgtab_near(const orc_imgtab *t, const double *x, int dx, int dy, int dz)
+{
+    int64_t c[3];
+    tab_cell_of(t, x, c);
+    const int dd[3] = {dx, dy, dz};
+    int64_t pc = 0, mul = 1;
+    for (int a = 0; a < 3; a++) {
+        pc += (a < t->dim ? c[a] + dd[a] + 1 : 0) * mul;
+        mul *= t->pn[a];
+    }
+    return pc;
+}
+
+int64_t orc_imgtab_verify(orc_imgtab *t, const double *X, int64_t N)
+{
+    orc_imgtab r = {0};
+    orc_imgtab_build(&r, t->dim, t->n, t->w, X, N);
+    int64_t bad = 0;
+    for (int64_t c = 0; c < t->pcells; c++) {
+        int ok = t->cnt[c] == r.cnt[c];
+        for (int64_t k = 0; ok && k < t->cnt[c]; k++) {
+            int found = 0;
+            for (int64_t m = 0; m < r.cnt[c] && !found; m++)
+                found = t->id[c][k] == r.id[c][m] && memcmp(&t->sh[c][3 * k], &r.sh[c][3 * m], 3) == 0;
+            ok = found;
+        }
+        bad += !ok;
+    }
+    orc_imgtab_free(&r);
+    return bad;
+}
+
+int64_t orc_imgtab_images(const orc_imgtab *t)
+{
+    int64_t n = 0;
+    for (int64_t c = 0; c < t->pcells; c++)
+        for (int64_t k = 0; k < t->cnt[c]; k++) n += t->sh[c][3 * k] || t->sh[c][3 * k + 1] || t->sh[c][3 * k + 2];
+    return n;
+}
+
+/* Alg 5 with image particles: any entry other than pid's own in the 3^d
+ * padded cells around q's cell within Rq + R_t of q (plain differences to
+ * x_t + s L).  Margins as collide() below. */
+static int collide_images(const orc_sys *s, const double *X, double lam, const double *q, double Rq, int64_t pid,
+                          double *mg)
+{
+    const orc_imgtab *tb = &s->img;
+    int zlo = s->dim == 3 ? -1 : 0, zhi = s->dim == 3 ? 1 : 0;
+    int hit = 0;
+    double best_hit = -1.0, best_miss = INFINITY;
+    for (int sz = zlo; sz <= zhi; sz++)
+        for (int sy = -1; sy <= 1; sy++)
+            for (int sx = -1; sx <= 1; sx++) {
+                int64_t pc = orc_imgtab_near(tb, q, sx, sy, sz);
+                for (int64_t k = 0; k < tb->cnt[pc]; k++) {
+                    int64_t t = tb->id[pc][k];
+                    if (t == pid) continue;
+                    const int8_t *sh = &tb->sh[pc][3 * k];
+                    double d[3] = {0.0, 0.0, 0.0};
+                    for (int a = 0; a < s->dim; a++) {
+                        double y = X[t * s->dim + a] + (double)sh[a] * s->L[a];
+                        d[a] = q[a] - y;
+                    }
+                    double ss = d[0] * d[0] + d[1] * d[1];
+                    if (s->dim == 3) ss = ss + d[2] * d[2];
+                    double S = sqrt(ss);
+                    double Rsum = Rq + lam * s->r[t];
+                    if (S <= Rsum) {
+                        if (!mg) return 1;
+                        hit = 1;
+                        double m = (Rsum - S) / Rsum;
+                        if (m > best_hit) best_hit = m;
+                    } else if (mg) {
+                        double m = (S - Rsum) / Rsum;
+                        if (m < best_miss) best_miss = m;
+                    }
+                }
+            }
+    if (mg) *mg = hit ? best_hit : best_miss;
+    return hit;
+}
+
 /* Alg 5: does a particle of radius Rq at position q (id pid) collide with any
  * other particle listed in the 3^d cells around q's cell?  X holds current
  * positions; the lists may be stale by at most one migration step, which the
@@ -209,6 +408,7 @@ static void bin(orc_sys *s, const double *X, const double lam_grid)
 static int collide(const orc_sys *s, const double *X, double lam, const double *q,
                    double Rq, int64_t pid, double *mg)
 {
+    if (s->images) return collide_images(s, X, lam, q, Rq, pid, mg);
     int64_t c[3] = {0, 0, 0};
     for (int a = 0; a < s->dim; a++) c[a] = cell_coord(q[a], s->w[a], s->n[a]);
     int zlo = s->dim == 3 ? -1 : 0, zhi = s->dim == 3 ? 1 : 0;
@@ -265,6 +465,7 @@ static int move_particle(orc_sys *s, double *X, double lam, int64_t pid)
         int hit = collide(s, X, lam, q, Rq, pid, s->margin ? &mg : NULL);
         if (s->margin && mg < pmin) pmin = mg;
         if (!hit) {
+            if (s->images) orc_imgtab_move(&s->img, pid, q_old, q);
             for (int a = 0; a < s->dim; a++) X[pid * s->dim + a] = q[a];
             if (s->margin) s->margin[pid] = pmin;
             return 1;
@@ -279,6 +480,7 @@ static int move_particle(orc_sys *s, double *X, double lam, int64_t pid)
 static int64_t sweep_once(orc_sys *s, double *X, double lam, double lam_grid)
 {
     bin(s, X, lam_grid);
+    if (s->images) orc_imgtab_build(&s->img, s->dim, s->n, s->w, X, s->N);
     int64_t acc = 0;
     if (s->literal) {
         for (int64_t pid = 0; pid < s->N; pid++) acc += move_particle(s, X, lam, pid);
@@ -304,6 +506,7 @@ static int64_t sweep_once(orc_sys *s, double *X, double lam, double lam_grid)
 static int64_t check_count(orc_sys *s, const double *X, double lam, double lam_grid, uint8_t *flags)
 {
     bin(s, X, lam_grid);
+    if (s->images) orc_imgtab_build(&s->img, s->dim, s->n, s->w, X, s->N);
     int64_t cnt = 0;
     for (int64_t pid = 0; pid < s->N; pid++) {
         int hit = collide(s, X, lam, &X[pid * s->dim], lam * s->r[pid], pid, NULL);
@@ -351,6 +554,7 @@ orc_sys *orc_create(int dim, const double L[3], int64_t N, const double *X, cons
 void orc_destroy(orc_sys *s)
 {
     if (!s) return;
+    orc_imgtab_free(&s->img);
     free(s->X);
     free(s->r);
     free(s->members);
@@ -364,6 +568,26 @@ double orc_get_lambda(const orc_sys *s) { return s->lam; }
 void orc_set_lambda(orc_sys *s, double lam) { s->lam = lam; }
 uint64_t orc_get_sweep(const orc_sys *s) { return s->sweep; }
 void orc_set_margin(orc_sys *s, double *margin) { s->margin = margin; }
+
+/* Periodicity by image particles (1) or by the minimum image (0). */
+void orc_set_images(orc_sys *s, int on) { s->images = on ? 1 : 0; }
+
+/* Compares the image entries kept move by move during the last sweep with
+ * a rebuild from X (the configuration swept last); the number of
+ * mismatching padded cells (0 when consistent), -1 outside the images mode.
+ * For the tests of the maintenance. */
+int64_t orc_images_verify(orc_sys *s, const double *X)
+{
+    if (!s->images || !s->img.cnt) return -1;
+    return orc_imgtab_verify(&s->img, X, s->N);
+}
+
+/* Image entries (shift != 0) currently held, or -1 outside the images mode. */
+int64_t orc_images_count(const orc_sys *s)
+{
+    if (!s->images || !s->img.cnt) return -1;
+    return orc_imgtab_images(&s->img);
+}
 
 /* counters: iters, accepted iterations, shake iterations, accepted moves, sweeps */
 void orc_get_counters(const orc_sys *s, int64_t out[5])
@@ -419,6 +643,7 @@ static int cmp_i64(const void *a, const void *b)
 int64_t orc_pairs(orc_sys *s, int64_t *ij, int64_t cap)
 {
     bin(s, s->X, s->lam);
+    if (s->images) orc_imgtab_build(&s->img, s->dim, s->n, s->w, s->X, s->N);
     int64_t cnt = 0;
     int64_t *part = (int64_t *)malloc(sizeof(int64_t) * (size_t)(s->N > 0 ? s->N : 1));
     int zlo = s->dim == 3 ? -1 : 0, zhi = s->dim == 3 ? 1 : 0;
@@ -428,7 +653,27 @@ int64_t orc_pairs(orc_sys *s, int64_t *ij, int64_t cap)
         int64_t c[3] = {0, 0, 0};
         for (int a = 0; a < s->dim; a++) c[a] = cell_coord(q[a], s->w[a], s->n[a]);
         int64_t np = 0;
-        for (int sx = -1; sx <= 1; sx++)
+        if (s->images) {
+            /* image particles: entries of the 3^d padded cells around i's
+             * cell, plain differences to x_t + s L */
+            const orc_imgtab *tb = &s->img;
+            for (int sz = zlo; sz <= zhi; sz++)
+                for (int sy = -1; sy <= 1; sy++)
+                    for (int sx = -1; sx <= 1; sx++) {
+                        int64_t pc = orc_imgtab_near(tb, q, sx, sy, sz);
+                        for (int64_t k = 0; k < tb->cnt[pc]; k++) {
+                            int64_t t = tb->id[pc][k];
+                            if (t <= i) continue;
+                            const int8_t *sh = &tb->sh[pc][3 * k];
+                            double d[3] = {0.0, 0.0, 0.0};
+                            for (int a = 0; a < s->dim; a++) d[a] = q[a] - (s->X[t * s->dim + a] + (double)sh[a] * s->L[a]);
+                            double ss = d[0] * d[0] + d[1] * d[1];
+                            if (s->dim == 3) ss = ss + d[2] * d[2];
+                            if (sqrt(ss) <= Ri + s->lam * s->r[t]) part[np++] = t;
+                        }
+                    }
+        }
+        for (int sx = -1; sx <= 1 && !s->images; sx++)
             for (int sy = -1; sy <= 1; sy++)
                 for (int sz = zlo; sz <= zhi; sz++) {
                     int64_t nx = (c[0] + sx + s->n[0]) % s->n[0];

@@ -58,6 +58,10 @@
  * pair is evaluated in a frame centred between the two platelets, so that
  * swapping them gives the same operations and the same answer.
  *
+ * Periodicity: the minimum image of the centre difference by default; in
+ * the images mode (orc_plt_set_images) explicit image platelets as for the
+ * spheres (orc_images.h): the difference is (x_j + s L) - x_i.
+ *
  * Tests may substitute another contact predicate for the sweeps and checks
  * (orc_plt_set_contact) -- the binary32 decision of the CUDA kernel, kept as
  * a kernel specification beside the tests -- to compare whole sweeps with
@@ -68,6 +72,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include "orc_images.h"
 
 int orc_unit_dir_stream(uint64_t seed, uint64_t sweep, uint64_t pid, uint64_t l, int dim, int stream, double u[3]);
 double orc_wrap(double x, double L);
@@ -240,6 +246,8 @@ typedef struct orc_plt {
     int64_t *cell_start, *members;
     int64_t iters, accepted_iters, shake_iters, moves_accepted;
     orc_plt_contact_fn contact;
+    int images;      /* periodicity by image platelets instead of the minimum image */
+    orc_imgtab img;
 } orc_plt;
 
 static int64_t pcell_coord(double x, double w, int64_t n)
@@ -272,6 +280,7 @@ static void pbin(orc_plt *s, const double *X, double lam_grid)
     for (int64_t i = 0; i < s->N; i++) s->members[fill[cell_of[i]]++] = i;
     free(fill);
     free(cell_of);
+    if (s->images) orc_imgtab_build(&s->img, 3, s->n, s->w, X, s->N);
 }
 
 /* Alg 5 for a platelet at centre q with normal u (id pid): any other
@@ -282,6 +291,25 @@ static int pcollide(const orc_plt *s, const double *X, const double *U, double l
     int64_t c[3];
     for (int a = 0; a < 3; a++) c[a] = pcell_coord(q[a], s->w[a], s->n[a]);
     double a = lam * s->a0, t = lam * s->t0;
+    if (s->images) {
+        /* image platelets: entries of the 27 padded cells around q's cell,
+         * plain differences (x_j + s L) - q */
+        const orc_imgtab *tb = &s->img;
+        for (int sz = -1; sz <= 1; sz++)
+            for (int sy = -1; sy <= 1; sy++)
+                for (int sx = -1; sx <= 1; sx++) {
+                    int64_t pc = orc_imgtab_near(tb, q, sx, sy, sz);
+                    for (int64_t k = 0; k < tb->cnt[pc]; k++) {
+                        int64_t j = tb->id[pc][k];
+                        if (j == pid) continue;
+                        const int8_t *sh = &tb->sh[pc][3 * k];
+                        double d[3];
+                        for (int b = 0; b < 3; b++) d[b] = (X[3 * j + b] + (double)sh[b] * s->L[b]) - q[b];
+                        if (s->contact(d, u, &U[3 * j], a, t)) return 1;
+                    }
+                }
+        return 0;
+    }
     for (int sx = -1; sx <= 1; sx++)
         for (int sy = -1; sy <= 1; sy++)
             for (int sz = -1; sz <= 1; sz++) {
@@ -334,6 +362,7 @@ static int pmove(orc_plt *s, double *X, double *U, double lam, int64_t pid)
     for (int l = 0; l < s->N_l; l++) {
         orc_plt_trial(s->seed, s->sweep, (uint64_t)pid, (uint64_t)l, s->L, s->c_m, s->c_r, x0, u0, q, u);
         if (!pcollide(s, X, U, lam, q, u, pid)) {
+            if (s->images) orc_imgtab_move(&s->img, pid, x0, q);
             for (int a = 0; a < 3; a++) {
                 X[3 * pid + a] = q[a];
                 U[3 * pid + a] = u[a];
@@ -414,9 +443,21 @@ orc_plt *orc_plt_create(const double L[3], int64_t N, const double *X, const dou
  * reference's binary64 orc_plt_collide).  For tests only. */
 void orc_plt_set_contact(orc_plt *s, orc_plt_contact_fn fn) { s->contact = fn ? fn : orc_plt_collide; }
 
+/* Periodicity by image platelets (1) or by the minimum image (0). */
+void orc_plt_set_images(orc_plt *s, int on) { s->images = on ? 1 : 0; }
+
+/* Image entries kept move by move during the last sweep against a rebuild
+ * from P (mismatching padded cells; -1 outside the images mode). */
+int64_t orc_plt_images_verify(orc_plt *s)
+{
+    if (!s->images || !s->img.cnt) return -1;
+    return orc_imgtab_verify(&s->img, s->X, s->N);
+}
+
 void orc_plt_destroy(orc_plt *s)
 {
     if (!s) return;
+    orc_imgtab_free(&s->img);
     free(s->X);
     free(s->U);
     free(s->members);

@@ -55,7 +55,7 @@ class srm_params(Structure):
                 ("n_clusters", c_int32), ("cluster_sigma", c_double), ("f0", c_double),
                 ("init_pos", c_void_p), ("lambda0", c_double), ("lambda_t", c_double),
                 ("guard", c_double), ("sweep0", c_uint64), ("wait_limit", c_int32),
-                ("reserved", c_int32)]
+                ("images", c_int32)]
 
 
 ALLOC_FN = CFUNCTYPE(c_void_p, c_void_p, c_size_t, c_void_p)
@@ -100,7 +100,8 @@ class srm_tuning(Structure):
 
 class srm_plt_params(Structure):
     _fields_ = [("c_w", c_double), ("c_m", c_double), ("c_r", c_double), ("N_k", c_int32), ("N_l", c_int32),
-                ("N_shake", c_int32), ("wait_limit", c_int32), ("sweep0", c_uint64)]
+                ("N_shake", c_int32), ("wait_limit", c_int32), ("sweep0", c_uint64), ("images", c_int32),
+                ("reserved", c_int32)]
 
 
 class srm_plt_step_info(Structure):
@@ -381,7 +382,7 @@ class Rve:
     def __init__(self, dim, box, radii, target_phi, seed=1, *, n=None, c_m, c_w=0.01, N_k=10,
                  N_l=10, N_shake=10, precision=PREC_F64, init="rsa", positions=None, f0=0.1,
                  n_clusters=0, cluster_sigma=0.0, lambda0=0.0, lambda_t=0.0, guard=4e-6,
-                 sweep0=0, wait_limit=0, stream=None, torch_memory=True):
+                 sweep0=0, wait_limit=0, images=False, stream=None, torch_memory=True):
         import torch
         lib = load()
         self.dim = int(dim)
@@ -413,6 +414,7 @@ class Rve:
         p.f0, p.n_clusters, p.cluster_sigma = f0, n_clusters, cluster_sigma
         p.lambda0, p.lambda_t, p.guard, p.sweep0 = lambda0, lambda_t, guard, sweep0
         p.wait_limit = wait_limit
+        p.images = 1 if images else 0
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
@@ -725,7 +727,7 @@ class Platelets:
     rotation rate c_r."""
 
     def __init__(self, box, x, u, a0, t0, lambda0, lambda_t, seed, *, c_m, c_w=0.01, c_r=0.0, N_k=10, N_l=10,
-                 N_shake=10, wait_limit=0, sweep0=0, stream=None):
+                 N_shake=10, wait_limit=0, sweep0=0, images=False, stream=None):
         import torch
         lib = load()
         self.box = tuple(float(v) for v in box)
@@ -735,6 +737,8 @@ class Platelets:
         lib.srm_plt_params_default(ctypes.byref(p))
         p.c_w, p.c_m, p.c_r, p.N_k, p.N_l, p.N_shake = c_w, c_m, c_r, N_k, N_l, N_shake
         p.wait_limit, p.sweep0 = wait_limit, sweep0
+        self._images = 1 if images else 0
+        p.images = self._images
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         L = (c_double * 3)(*self.box)
@@ -754,6 +758,7 @@ class Platelets:
         p = srm_plt_params()
         load().srm_plt_params_default(ctypes.byref(p))
         p.c_w, p.c_m, p.c_r, p.N_k, p.N_l, p.N_shake, p.wait_limit = c_w, c_m, c_r, N_k, N_l, N_shake, wait_limit
+        p.images = self._images
         _check(load().srm_plt_set_params(self._h, ctypes.byref(p)))
 
     def step(self) -> dict:

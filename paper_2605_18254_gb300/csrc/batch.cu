@@ -298,6 +298,7 @@ srm_status srm_save(srm_rve *h, void *buf, size_t *len)
     hd.p.N_shake = s.N_shake;
     hd.p.precision = hd.prec;
     hd.p.guard = s.guard;
+    hd.p.images = s.images;
     hd.lam_P = s.lam_P;
     hd.lam_t = s.lam_t;
     hd.sweep = s.sweep;

@@ -75,7 +75,7 @@ __device__ __forceinline__ void check_one(RveDev *st, int i, int &hit, unsigned 
                             h = d2 <= __fmul_rn(__fmul_rn(rs, rs), g1);
                         } else {
                             const double q[3] = {p.x, p.y, p.z};
-                            h = collide_exact<DIM>(q, p.w, t.x, t.y, t.z, t.w, st->L, st->halfL);
+                            h = collide64<DIM>(st->images, q, p.w, t.x, t.y, t.z, t.w, st->L, st->halfL);
                         }
                         if (h) {
                             hit = 1;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_pairs_count(RveDev *st, int want_gap)
                         const double4_32a t = pos[j];
                         const double tt[3] = {t.x, t.y, t.z};
                         double gap;
-                        if (gap_exact<DIM>(q, p.w, tt, t.w, st->L, st->halfL, &gap)) cnt++;
+                        if (gap64<DIM>(st->images, q, p.w, tt, t.w, st->L, st->halfL, &gap)) cnt++;
                         if (gap < mg) mg = gap;
                     }
                 }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_pairs_fill(RveDev *st, long long *ij)
                     const double4_32a t = pos[j];
                     const double tt[3] = {t.x, t.y, t.z};
                     double gap;
-                    if (gap_exact<DIM>(q, p.w, tt, t.w, st->L, st->halfL, &gap) && k < cnt) {
+                    if (gap64<DIM>(st->images, q, p.w, tt, t.w, st->L, st->halfL, &gap) && k < cnt) {
                         // insertion into the sorted run [base, base + k)
                         long long at = base + k;
                         while (at > base && ij[2 * (at - 1) + 1] > (long long)other) {

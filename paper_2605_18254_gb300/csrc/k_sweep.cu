@@ -569,7 +569,7 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
                     }
                     cc.examined++;
                     if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
-                    else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                    else hit = collide64<DIM>(st->images, q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
                 }
                 if (!__any_sync(0xffffffffu, hit)) {
                     if constexpr (F32) np = make_float4(qf[0], qf[1], qf[2], p.w);
@@ -835,7 +835,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                         const PT c = cpos[ch * 32 + bt];
                         cc.examined++;
                         if constexpr (F32) hit = hit_f32<DIM>(qf, Rm, c, g1);
-                        else hit = collide_exact<DIM>(qd, Rd, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        else hit = collide64<DIM>(st->images, qd, Rd, c.x, c.y, c.z, c.w, st->L, st->halfL);
                     }
                 }
             }
@@ -935,8 +935,8 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                         h1 = lmax > 1 && hit_f32<DIM>(a1, p.w, c, g1);
                     } else {
                         const double a0[3] = {q0.x, q0.y, q0.z}, a1[3] = {q1.x, q1.y, q1.z};
-                        h0 = collide_exact<DIM>(a0, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
-                        h1 = lmax > 1 && collide_exact<DIM>(a1, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        h0 = collide64<DIM>(st->images, a0, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        h1 = lmax > 1 && collide64<DIM>(st->images, a1, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
                     }
                 }
                 const bool f0 = (sb & 1u) || __any_sync(0xffffffffu, h0);
@@ -981,7 +981,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                             const PT c = cpos[ch * 32 + bt];
                             cc.examined++;
                             if constexpr (F32) hit = hit_f32<DIM>(qs, p.w, c, g1);
-                            else hit = collide_exact<DIM>(qt, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                            else hit = collide64<DIM>(st->images, qt, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
                         }
                     }
                 }
@@ -1066,7 +1066,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                             const PT c = cpos[nlist[jj]];
                             cc.examined++;
                             if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
-                            else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                            else hit = collide64<DIM>(st->images, q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
                         }
                     }
                     const unsigned hb_ = __ballot_sync(0xffffffffu, hit);
@@ -1115,7 +1115,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                             const PT c = cpos[csub * 32 + bt];
                             cc.examined++;
                             if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
-                            else hit = collide_exact<DIM>(q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                            else hit = collide64<DIM>(st->images, q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
                         }
                     }
                     const unsigned hb_ = __ballot_sync(0xffffffffu, hit);

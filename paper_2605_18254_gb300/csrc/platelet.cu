@@ -260,6 +260,7 @@ struct PltDev {
     double L[3], halfL[3], w[3];
     int32_t n[3], H[3];
     int32_t N, ncells, N_l, wait_limit;
+    int32_t images;  // periodicity by image platelets instead of the minimum image
     double a, t, c_m, c_r;
     uint64_t seed, sweep;
     uint32_t epoch;
@@ -282,13 +283,21 @@ __device__ __forceinline__ int32_t cell_of_point(const PltDev &d, const double q
     return c[0] + d.n[0] * (c[1] + d.n[1] * c[2]);
 }
 
+// Centre of platelet t minus q under the handle's periodicity: the minimum
+// image of the difference, or (images) the difference to t's periodic image
+// nearest to q, (x_t +- L) - q, with the image formed first.
 __device__ __forceinline__ void min_image(const PltDev &d, const double4_32a &xt, const double q[3], double dj[3])
 {
     const double v[3] = {xt.x, xt.y, xt.z};
     for (int j = 0; j < 3; j++) {
         double x = v[j] - q[j];
-        if (x > d.halfL[j]) x -= d.L[j];
-        if (x < -d.halfL[j]) x += d.L[j];
+        if (d.images) {
+            if (x > d.halfL[j]) x = (v[j] - d.L[j]) - q[j];
+            else if (x < -d.halfL[j]) x = (v[j] + d.L[j]) - q[j];
+        } else {
+            if (x > d.halfL[j]) x -= d.L[j];
+            if (x < -d.halfL[j]) x += d.L[j];
+        }
         dj[j] = x;
     }
 }
@@ -729,6 +738,7 @@ srm_status bin(srm_plt *h, int c, double lam, double lam_grid, PltDev &d)
     d.ncells = (int32_t)ncells;
     d.N_l = h->p.N_l;
     d.wait_limit = h->p.wait_limit == 0 ? WAIT_DEFAULT : h->p.wait_limit;
+    d.images = h->p.images ? 1 : 0;
     d.a = lam * h->a0;
     d.t = lam * h->t0;
     d.c_m = h->p.c_m;

@@ -340,6 +340,7 @@ srm_status member_load(Group &g, Member &mb, const Prep &q)
     s.status = 0;
     s.pairs_sweep = s.pairs_check = s.stage_overflow = s.trials = s.pairs_alg5 = s.near_fallback = 0;
     s.wait_limit = q.p.wait_limit == 0 ? (1 << 22) : q.p.wait_limit;
+    s.images = q.p.images ? 1 : 0;
     mb.dim = q.dim;
     mb.n = q.n;
     mb.S0 = q.S0;

@@ -81,6 +81,7 @@ struct RveDev {
     unsigned long long near_fallback;   // particles whose near list exceeded its capacity (general path)
     uint32_t *done;       // [ncells_cap] epoch stamp of the last sweep that finished the cell
     int32_t wait_limit;   // polls of one dependency before the sweep gives up (< 0: none)
+    int32_t images;       // FP64 form: periodicity by image particles instead of the minimum image
     // directions of trials 0 and 1 of every particle for the coming sweep,
     // in the cell-sorted order of the destination slot: [2 n] float4 (FP32
     // form) or double4_32a (FP64 form), entry 2 g + l for slot g, trial l
@@ -413,6 +414,40 @@ __device__ __forceinline__ bool collide_exact(const double q[3], double Rq, doub
     return __dsqrt_rn(ss) <= rs;
 }
 
+// The same predicate with image particles instead of the minimum image
+// (Section 2's other periodicity): per axis the image of t nearest to q,
+// y = t + L or t - L (one rounding) when |q - t| exceeds half the box, then
+// the plain difference q - y -- the arithmetic of the reference's image
+// entries x_t + s L.
+template <int DIM>
+__device__ __forceinline__ bool collide_img(const double q[3], double Rq, double tx, double ty, double tz, double Rt,
+                                            const double L[3], const double halfL[3])
+{
+    const double t[3] = {tx, ty, tz};
+    double ss = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        double d = __dsub_rn(q[a], t[a]);
+        if (d > halfL[a]) d = __dsub_rn(q[a], __dadd_rn(t[a], L[a]));
+        else if (d < -halfL[a]) d = __dsub_rn(q[a], __dsub_rn(t[a], L[a]));
+        ss = a == 0 ? __dmul_rn(d, d) : __dadd_rn(ss, __dmul_rn(d, d));
+    }
+    const double rs = __dadd_rn(Rq, Rt);
+    const double b = __dmul_rn(rs, rs);
+    if (ss > __dmul_rn(b, 1.0 + 0x1p-48)) return false;
+    if (ss <= __dmul_rn(b, 1.0 - 0x1p-51)) return true;
+    return __dsqrt_rn(ss) <= rs;
+}
+
+// Algorithm 5's pair test of the FP64 form under the RVE's periodicity.
+template <int DIM>
+__device__ __forceinline__ bool collide64(int images, const double q[3], double Rq, double tx, double ty, double tz,
+                                          double Rt, const double L[3], const double halfL[3])
+{
+    return images ? collide_img<DIM>(q, Rq, tx, ty, tz, Rt, L, halfL)
+                  : collide_exact<DIM>(q, Rq, tx, ty, tz, Rt, L, halfL);
+}
+
 // Gap S - (Rq + Rt) and the literal predicate, for certification.
 template <int DIM>
 __device__ __forceinline__ bool gap_exact(const double q[3], double Rq, const double t[3], double Rt,
@@ -430,6 +465,32 @@ __device__ __forceinline__ bool gap_exact(const double q[3], double Rq, const do
     const double rs = __dadd_rn(Rq, Rt);
     *gap = __dsub_rn(S, rs);
     return S <= rs;
+}
+
+// gap_exact with image particles (the arithmetic of collide_img).
+template <int DIM>
+__device__ __forceinline__ bool gap_img(const double q[3], double Rq, const double t[3], double Rt, const double L[3],
+                                        const double halfL[3], double *gap)
+{
+    double ss = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        double d = __dsub_rn(q[a], t[a]);
+        if (d > halfL[a]) d = __dsub_rn(q[a], __dadd_rn(t[a], L[a]));
+        else if (d < -halfL[a]) d = __dsub_rn(q[a], __dsub_rn(t[a], L[a]));
+        ss = a == 0 ? __dmul_rn(d, d) : __dadd_rn(ss, __dmul_rn(d, d));
+    }
+    const double S = __dsqrt_rn(ss);
+    const double rs = __dadd_rn(Rq, Rt);
+    *gap = __dsub_rn(S, rs);
+    return S <= rs;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool gap64(int images, const double q[3], double Rq, const double t[3], double Rt,
+                                      const double L[3], const double halfL[3], double *gap)
+{
+    return images ? gap_img<DIM>(q, Rq, t, Rt, L, halfL, gap) : gap_exact<DIM>(q, Rq, t, Rt, L, halfL, gap);
 }
 
 // Grid of Algorithm 1 for scale lam: cellSize = 2.5 lam rmax + c_m,
