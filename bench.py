@@ -169,6 +169,43 @@ def cpu_sample(w, sweeps=1):
     return w.n * sweeps / dt, dt
 
 
+def cpu_samples(w, states):
+    """The FP64 reference on the host, one sweep of Algorithm 3 over all
+    particles from each of the given states (label, positions, scale): the
+    swept scale is the state's scale swollen by one step (a sweep of the N_k
+    loop).  Returns {label: seconds}."""
+    import oracle
+    out = {}
+    for label, x, lam in states:
+        s = oracle.System(w.dim, w.box, x, w.radii, lam=lam * (1.0 + w.c_w), target_phi=w.target_phi, c_w=w.c_w,
+                          c_m=w.c_m, N_k=w.N_k, N_l=w.N_l, N_shake=w.N_shake, seed=w.seed)
+        t0 = time.perf_counter()
+        s.sweep()
+        out[label] = time.perf_counter() - t0
+    return out
+
+
+def weighted_oracle_time(samples, record):
+    """Extrapolated reference time of a whole generation: the run's sweeps
+    (record: (scale, sweeps so far) after each chunk of iterations) each
+    timed at the reference's per-sweep time for that scale, interpolated
+    linearly in the scale between the sampled states ((scale, seconds))."""
+    pts = sorted(samples)
+
+    def t_at(lam):
+        if lam <= pts[0][0]:
+            return pts[0][1]
+        for (l0, t0), (l1, t1) in zip(pts, pts[1:]):
+            if lam <= l1:
+                return t1 if l1 <= l0 else t0 + (t1 - t0) * (lam - l0) / (l1 - l0)
+        return pts[-1][1]
+    total, prev_lam, prev_sw = 0.0, record[0][0], record[0][1]
+    for lam, sw in record[1:]:
+        total += (sw - prev_sw) * t_at(0.5 * (lam + prev_lam))
+        prev_lam, prev_sw = lam, sw
+    return total
+
+
 def make_workload(name):
     import srm_inputs
     return srm_inputs.RECIPES[name]()
@@ -194,7 +231,9 @@ def run_reference(args, rank, world):
         "config": workload_desc(w, 64),
         "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step: 1 sweep of Algorithm 3 over all {w.n} particles at the "
-                                   "first swollen scale, single-threaded FP64 reference"},
+                                   "first swollen scale (the start of the run, where sweeps are cheapest; the "
+                                   "other states of the run need the GPU to reach), single-threaded FP64 "
+                                   "reference"},
         "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "wall_s": time.time() - t0,
@@ -348,9 +387,27 @@ def run_ours(args, rank, world, local_rank):
     g = new_rve()
     g.set_timing(True)
     st0 = g.state()
-    info = g.run_to_target()
+    record = [(st0["lambda"], 0)]
+    states = [("start", np.ascontiguousarray(w.x), st0["lambda"])]
+    mid_phi = 0.5 * (w.target_phi + 0.1)
+    while True:
+        info = g.run_to_target(25) if not g.state()["done"] else None
+        st = g.state()
+        record.append((st["lambda"], st["sweeps"]))
+        if len(states) == 1 and st["phi"] >= mid_phi:
+            states.append((f"phi={st['phi']:.3f}", g.positions()[0], st["lambda"]))
+        if st["done"]:
+            break
+    states.append((f"phi={st['phi']:.3f}", g.positions()[0], st["lambda"]))
     tm = g.timings()
     st1 = g.state()
+    g.close()
+    # the check's floor: the first iterations, where almost every particle
+    # moves and the check only reads the moved flags
+    g = new_rve()
+    g.set_timing(True)
+    g.run_to_target(3)
+    tm0 = g.timings()
     g.close()
     per_launch = {
         "sweep": tm["ms_sweep"] / max(1, tm["sweep_launches"]),
@@ -397,6 +454,22 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
                 "stage_ms_total": totals}
     roof["peak_source"] = f"{pk_kind}" + (" (HBM from MEASURED_PEAKS.json)" if pk_kind == "measured" else "")
+    # the overlap check (Algorithm 6) against HBM: its algorithmic bytes per
+    # launch are the moved flag, the position and the cell index of every
+    # particle plus the cell starts (FP32 form, 3D: 1 + 16 + 4 + 4 / 1.5)
+    cb = (1 + (16 if args.precision == 32 else 32) + 4) + 4.0 / 1.5
+    ck_ms = per_launch["check"]
+    floor_ms = tm0["ms_check"] / max(1, tm0["check_launches"])
+    roof["check"] = {
+        "kernel": f"k_check<{args.precision == 32}>", "bound": "hbm", "per_launch_ms": ck_ms,
+        "bytes_per_launch": cb * w.n, "achieved": cb * w.n / (ck_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+        "unit": "GB/s", "frac": cb * w.n / (ck_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+        "floor_ms": floor_ms, "floor_frac": cb * w.n / (floor_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+        "launches": tm["check_launches"],
+        "note": ("per_launch_ms over the whole generation; floor_ms over the checks of the first 3 iterations, "
+                 "where almost every particle moved and the check only reads flags (launch and read floor); "
+                 "the time above the floor is the stencil walks of the particles that did not move"),
+    }
 
     # ---- FP64 form on the same sample (first sweeps), for the precision comparison
     cmp = {}
@@ -419,12 +492,20 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        ups, dt = cpu_sample(w, 1)
         import platform
-        cpu = {"value": ups, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"1 sweep of Algorithm 3 over all {w.n} particles at the first swollen scale "
-                         f"({dt:.1f} s, single-threaded FP64 reference; host {platform.machine()}, "
-                         f"{os.cpu_count()} cores)"}
+        secs = cpu_samples(w, states)
+        lam_of = {label: lam for label, _, lam in states}
+        t_ref = weighted_oracle_time([(lam_of[k] * (1.0 + w.c_w), v) for k, v in secs.items()], record)
+        sw_run = record[-1][1]
+        cpu = {"value": w.n * sw_run / t_ref, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+               "sample": (f"1 sweep of Algorithm 3 over all {w.n} particles from each of {len(states)} states of the "
+                          f"GPU run ({', '.join(f'{k}: {v:.2f} s' for k, v in secs.items())}; single-threaded FP64 "
+                          f"reference; host {platform.machine()}, {os.cpu_count()} cores), weighted by the run's "
+                          f"{sw_run} sweeps over the scale"),
+               "extrapolated_time_to_target_s": t_ref,
+               "gpu_time_to_target_s": dev_max / args.steps,
+               "note": "extrapolated: per-sweep times interpolated between the sampled states, times the sweeps of "
+                       "the GPU run; the reference runs the same method in the same order (FP64)"}
 
     h2d = int(x_host.numel() * 8 + r_host.numel() * 8)
     d2h = int(w.n * w.dim * 8 + w.n * 8)

@@ -110,6 +110,195 @@ __global__ void __launch_bounds__(256) k_check(BatchDev *bd)
 }
 
 // ---------------------------------------------------------------------------
+// The same count, one warp per cell: the moved flags of the cell's particles
+// decide whether it has work; if so, the non-moved particles of the cells
+// within H are staged in shared memory (FP32 form: shifted into the home
+// cell's frame), keeping those whose distance to the home cell box allows a
+// contact with the largest non-moved home particle, and each non-moved home
+// particle tests them with the lanes -- one load of each candidate per cell
+// instead of one per home particle.  The predicate and its roundings are
+// those of check_one, so the count is the same.  A cell whose staged set
+// would exceed CK_CAP falls back to check_one per particle.
+// ---------------------------------------------------------------------------
+constexpr int CK_WARPS = 4;
+constexpr int CK_CAP = 256;
+
+template <bool F32>
+struct CheckSmem {
+    using PT = typename std::conditional<F32, float4, double4_32a>::type;
+    static constexpr size_t off_gidx = ST_HDR + (size_t)CK_CAP * sizeof(PT);
+    static constexpr size_t bytes = (off_gidx + (size_t)CK_CAP * 4 + 31) / 32 * 32;
+};
+
+template <int DIM, bool F32>
+__device__ __forceinline__ void check_cell(RveDev *st, int cell, unsigned char *base, int &hits,
+                                           unsigned &examined)
+{
+    using SM = CheckSmem<F32>;
+    using PT = typename SM::PT;
+    const int lane = threadIdx.x & 31;
+    StencilSmem &S = *reinterpret_cast<StencilSmem *>(base);
+    PT *cand = reinterpret_cast<PT *>(base + ST_HDR);
+    uint32_t *gidx = reinterpret_cast<uint32_t *>(base + SM::off_gidx);
+    const Slot d = st->slot[st->dst_idx];
+    const PT *pos = reinterpret_cast<const PT *>(d.pos);
+    const uint32_t *cs = st->cell_start;
+    const uint8_t *flags = st->flags;
+    const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
+    if (nh == 0) return;
+    // non-moved home particles and the largest radius among them
+    bool any = false;
+    float rh = 0.f;
+    for (uint32_t m = lane; m < nh; m += 32)
+        if (!flags[hb + m]) {
+            any = true;
+            rh = fmaxf(rh, (float)pos[hb + m].w);
+        }
+    if (!__any_sync(0xffffffffu, any)) return;
+    for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
+    int hx, hy, hz;
+    decode_cell((uint32_t)cell, st->gn, hx, hy, hz);
+    int nst, center;
+    const uint32_t T = list_stencil(st, cs, hx, hy, hz, 0, S, nst, center);
+    const float w[3] = {(float)st->gw[0], (float)st->gw[1], (float)st->gw[2]};
+    const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
+    auto approx = [&](const PT &c) -> float4 {
+        if constexpr (F32) {
+            return c;
+        } else {
+            double ex = c.x - ox, ey = c.y - oy, ez = DIM == 3 ? c.z - oz : 0.0;
+            if (ex > st->halfL[0]) ex -= st->L[0];
+            if (ex < -st->halfL[0]) ex += st->L[0];
+            if (ey > st->halfL[1]) ey -= st->L[1];
+            if (ey < -st->halfL[1]) ey += st->L[1];
+            if (DIM == 3) {
+                if (ez > st->halfL[2]) ez -= st->L[2];
+                if (ez < -st->halfL[2]) ez += st->L[2];
+            }
+            return make_float4((float)ex, (float)ey, (float)ez, (float)c.w);
+        }
+    };
+    // stage the non-moved candidates within reach of the home box; the flag
+    // and the position of four chunks are loaded before any is used, so
+    // that a cell costs few memory round trips
+    constexpr int U = 4;
+    uint32_t Tk = 0;
+    bool overflow = false;
+    for (uint32_t k0 = 0; k0 < T && !overflow; k0 += 32 * U) {
+        PT c[U];
+        uint8_t f[U];
+        uint32_t g[U];
+        int jj[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t k = k0 + 32 * u + (uint32_t)lane;
+            f[u] = 1;
+            g[u] = 0;
+            jj[u] = 0;
+            if (k < T) {
+                jj[u] = find_cell(S, nst, k);
+                g[u] = S.b[jj[u]] + (k - S.o[jj[u]]);
+                f[u] = flags[g[u]];
+                c[u] = pos[g[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            bool keep = false;
+            if (!f[u]) {
+                if constexpr (F32) {
+                    // the shift of check_one: one fused multiply-add per axis
+                    c[u].x = __fmaf_rn((float)S.sh[jj[u]][0], w[0], c[u].x);
+                    c[u].y = __fmaf_rn((float)S.sh[jj[u]][1], w[1], c[u].y);
+                    c[u].z = __fmaf_rn((float)S.sh[jj[u]][2], w[2], c[u].z);
+                }
+                const float4 ca = approx(c[u]);
+                const float r = rh + ca.w;
+                keep = box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (overflow || Tk + __popc(bal) > (uint32_t)CK_CAP) {
+                overflow = true;
+                continue;
+            }
+            if (keep) {
+                const uint32_t at = Tk + __popc(bal & ((1u << lane) - 1u));
+                cand[at] = c[u];
+                gidx[at] = g[u];
+            }
+            Tk += __popc(bal);
+        }
+    }
+    __syncwarp();
+    if (overflow) {
+        for (uint32_t m = lane; m < nh; m += 32) {
+            int hit = 0;
+            if (!flags[hb + m]) check_one<DIM, F32>(st, (int)(hb + m), hit, examined);
+            hits += hit;
+        }
+        return;
+    }
+    const float g1 = 1.0f + st->guard;
+    for (uint32_t m = 0; m < nh; m++) {
+        const uint32_t gi = hb + m;
+        if (flags[gi]) continue;  // the same value for every lane
+        const PT p = pos[gi];
+        bool hit = false;
+        for (uint32_t kk = lane; kk < Tk && !hit; kk += 32) {
+            if (gidx[kk] == gi) continue;
+            const PT t = cand[kk];
+            examined++;
+            if constexpr (F32) {
+                const float ex = __fsub_rn(p.x, t.x), ey = __fsub_rn(p.y, t.y);
+                float d2 = __fmaf_rn(ey, ey, __fmul_rn(ex, ex));
+                if (DIM == 3) {
+                    const float ez = __fsub_rn(p.z, t.z);
+                    d2 = __fmaf_rn(ez, ez, d2);
+                }
+                const float rs = __fadd_rn(p.w, t.w);
+                hit = d2 <= __fmul_rn(__fmul_rn(rs, rs), g1);
+            } else {
+                const double q[3] = {p.x, p.y, p.z};
+                hit = collide64<DIM>(st->images, q, p.w, t.x, t.y, t.z, t.w, st->L, st->halfL);
+            }
+        }
+        if (__any_sync(0xffffffffu, hit) && lane == 0) hits++;
+    }
+}
+
+// Cells of the RVEs at work (plan actc, 256-cell chunks), one warp per cell
+// in a grid-stride loop.
+template <bool F32>
+__global__ void __launch_bounds__(CK_WARPS * 32) k_check_cells(BatchDev *bd)
+{
+    extern __shared__ __align__(32) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *base = smem + (size_t)wib * CheckSmem<F32>::bytes;
+    const int B = bd->B;
+    const int total = bd->actc[B] * 256;
+    const int stride = gridDim.x * CK_WARPS;
+    for (int gc = blockIdx.x * CK_WARPS + wib; gc < total; gc += stride) {
+        const int chunk = gc >> 8;
+        int r = 0;
+        if (lane == 0) r = find_seg(bd->actc, B, chunk);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        RveDev *st = bd->rv[r];
+        const int cell = (chunk - bd->actc[r]) * 256 + (gc & 255);
+        if (!st->do_check || cell >= st->ncells) continue;
+        int hits = 0;
+        unsigned examined = 0;
+        if (st->dim == 3) check_cell<3, F32>(st, cell, base, hits, examined);
+        else check_cell<2, F32>(st, cell, base, hits, examined);
+        hits = __reduce_add_sync(0xffffffffu, hits);
+        examined = __reduce_add_sync(0xffffffffu, examined);
+        if (lane == 0) {
+            if (hits) atomicAdd(&st->red[0], (unsigned long long)hits);
+            if (examined) atomicAdd(&st->pairs_check, (unsigned long long)examined);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Inspection of P in binary64: a fresh binning of P at its own scale into a
 // scratch slot (absolute binary64 positions for either form), then pairs and
 // certification on that slot.
@@ -264,13 +453,31 @@ static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); 
 
 int check_cap_max(bool f32) { return f32 ? 512 : 256; }
 
+static int g_ck_blocks[2] = {0, 0};
+
+// A persistent grid of all the blocks that stay resident, at most one warp
+// per cell of the group's capacity.
 void launch_check(const BatchShape &b, cudaStream_t s)
 {
-    if (b.f32) k_check<true><<<b.blocks_p, 256, 0, s>>>(b.d);
-    else k_check<false><<<b.blocks_p, 256, 0, s>>>(b.d);
+    const int want = (b.blocks_c * 256 + CK_WARPS - 1) / CK_WARPS;
+    const int res = g_ck_blocks[b.f32 ? 1 : 0];
+    const int nb = want < res ? want : res;
+    if (b.f32) k_check_cells<true><<<nb, CK_WARPS * 32, CK_WARPS * CheckSmem<true>::bytes, s>>>(b.d);
+    else k_check_cells<false><<<nb, CK_WARPS * 32, CK_WARPS * CheckSmem<false>::bytes, s>>>(b.d);
 }
 
-void check_configure() {}
+void check_configure()
+{
+    if (g_ck_blocks[0]) return;
+    int dev = 0, sms = 1, b32 = 0, b64 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_check_cells<true>, CK_WARPS * 32, CK_WARPS * CheckSmem<true>::bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_check_cells<false>, CK_WARPS * 32,
+                                                  CK_WARPS * CheckSmem<false>::bytes);
+    g_ck_blocks[1] = (b32 > 0 ? b32 : 1) * (sms > 0 ? sms : 1);
+    g_ck_blocks[0] = (b64 > 0 ? b64 : 1) * (sms > 0 ? sms : 1);
+}
 
 // Binning of P into a scratch slot, in binary64, for the inspection of one
 // RVE (its single-member batch).

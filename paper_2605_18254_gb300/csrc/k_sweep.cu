@@ -92,15 +92,6 @@ __device__ __forceinline__ bool within_f32(const float4 &p, const float4 &t, flo
     return ex * ex + ey * ey + ez * ez <= r * r * 1.0004f;
 }
 
-// Squared distance from a point (relative to the home corner) to the home box.
-__device__ __forceinline__ float box_dist2(const float4 &t, const float w[3], int dim)
-{
-    const float ex = fmaxf(fmaxf(-t.x, t.x - w[0]), 0.f);
-    const float ey = fmaxf(fmaxf(-t.y, t.y - w[1]), 0.f);
-    const float ez = dim == 3 ? fmaxf(fmaxf(-t.z, t.z - w[2]), 0.f) : 0.f;
-    return ex * ex + ey * ey + ez * ez;
-}
-
 // FP32 form of Algorithm 5 for one pair: trial q of a particle of radius Rq
 // against candidate c (both relative to the same corner), with the guard g1.
 // Explicit roundings (no contraction left to the compiler), so that the

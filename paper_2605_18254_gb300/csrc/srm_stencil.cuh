@@ -135,6 +135,15 @@ __device__ __forceinline__ void list_stencil_split(const RveDev *st, const uint3
     __syncwarp();
 }
 
+// Squared distance from a point (relative to the home corner) to the home box.
+__device__ __forceinline__ float box_dist2(const float4 &t, const float w[3], int dim)
+{
+    const float ex = fmaxf(fmaxf(-t.x, t.x - w[0]), 0.f);
+    const float ey = fmaxf(fmaxf(-t.y, t.y - w[1]), 0.f);
+    const float ez = dim == 3 ? fmaxf(fmaxf(-t.z, t.z - w[2]), 0.f) : 0.f;
+    return ex * ex + ey * ey + ez * ez;
+}
+
 // Stencil cell holding flattened candidate k (binary search over offsets).
 __device__ __forceinline__ int find_cell(const StencilSmem &S, int nst, uint32_t k)
 {
