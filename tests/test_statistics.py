@@ -77,3 +77,61 @@ def test_fp32_gpu_agrees_with_reference():
     g2, p2 = oracle_ensemble(range(1001, 1001 + RVES))
     assert stats.ks_2samp(g1, g2).pvalue > 0.01
     assert stats.ks_2samp(p1, p2).pvalue > 0.01
+
+
+# ---------------------------------------------------------------------------
+# 3D: monodisperse spheres (FP32 and FP64 forms) and the benchmark's own
+# input -- log-normal radii, Gaussian clusters -- at small size, each a GPU
+# ensemble against a reference ensemble with disjoint seeds.
+# ---------------------------------------------------------------------------
+RVES3 = 12
+
+
+def mono3(seed):
+    return srm_inputs._mono("ks3", 3, 600, 0.40, 0.1, seed)
+
+
+def poly3(seed):
+    # 1500 spheres of the benchmark recipe, 6 clusters of 250
+    return srm_inputs.poly_1m(seed=seed, n=1500, clusters=6)
+
+
+CASES3 = {"mono_fp32": (mono3, 32), "mono_fp64": (mono3, 64), "poly_clustered_fp32": (poly3, 32)}
+
+
+def oracle_ensemble3(maker, seeds, rng):
+    g, p = [], []
+    for s in seeds:
+        w = maker(s)
+        o = oracle.System(3, w.box, w.x, w.radii, lam=1.0, target_phi=w.target_phi, c_w=0.02, c_m=w.c_m, seed=s)
+        o.run()
+        assert abs(o.phi() - w.target_phi) < 1e-9
+        a, b = gaps_and_distances(o.x, o.radii(), w.box, rng)
+        g.append(a)
+        p.append(b)
+    return np.concatenate(g), np.concatenate(p)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", sorted(CASES3))
+def test_3d_gpu_agrees_with_reference(case):
+    import paper_2605_18254_gb300 as srm
+    maker, prec = CASES3[case]
+    rng = np.random.default_rng(10)
+    g, p = [], []
+    for s in range(1, 1 + RVES3):
+        w = maker(s)
+        r = srm.Rve(3, w.box, w.radii, w.target_phi, s, c_m=w.c_m, c_w=0.02, precision=prec, init="explicit",
+                    positions=w.x)
+        assert r.run_to_target()["converged"]
+        x, R = r.positions()
+        assert r.certify()[0] == 0
+        a, b = gaps_and_distances(x, R, w.box, rng)
+        g.append(a)
+        p.append(b)
+        r.close()
+    g1, p1 = np.concatenate(g), np.concatenate(p)
+    g2, p2 = oracle_ensemble3(maker, range(2001, 2001 + RVES3), np.random.default_rng(11))
+    assert np.min(g1) > 0 and np.min(g2) > 0
+    assert stats.ks_2samp(g1, g2).pvalue > 0.01, case
+    assert stats.ks_2samp(p1, p2).pvalue > 0.01, case
