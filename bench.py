@@ -570,7 +570,7 @@ def run_ensemble(args, rank, world, local_rank):
         e[0].record(stream)
         b = srm.Batch(jobs, stream=stream.cuda_stream)
         if tuned:
-            b.set_tuning(tuned["sweep_blocks_per_sm"], tuned["stage_capacity"])
+            b.set_tuning(tuned["sweep_blocks_per_sm"], tuned["stage_capacity"], tuned["sweep_path"])
         e[1].record(stream)
         if tune:
             tuned.update(b.autotune(8))
@@ -616,9 +616,10 @@ def run_ensemble(args, rank, world, local_rank):
                    "rves": count, "particles": n_total,
                    "tuning": {"sweep_blocks_per_sm": tuned.get("sweep_blocks_per_sm"),
                               "stage_capacity": tuned.get("stage_capacity"),
+                              "sweep_path": tuned.get("sweep_path"),
                               "how": "srm_batch_autotune during the first warm-up step (candidate sweep "
-                                     "grids and staging capacities timed on the running batch), applied to "
-                                     "every later batch"},
+                                     "grids, staging capacities and FP32 sweep kernels timed on the running "
+                                     "batch), applied to every later batch"},
                    "l2": "256 MiB buffer written between timed steps (L2 flushed)"},
         "time_to_target_s": dev / args.steps, "certified": all(r["ok"] for r in res),
         "e2e": {"value": upd / e2e, "unit": "particle-updates/s",
@@ -801,6 +802,40 @@ def run_regimes(args, rank, world, local_rank):
 # ---------------------------------------------------------------------------
 # platelets (Section 3.3): house of cards to rho = 5, then relaxation
 # ---------------------------------------------------------------------------
+def platelet_cpu_baseline(w, states, record, relaxed, relax, D):
+    """The binary64 reference on one host core, one sweep from each sampled
+    state of the GPU run (generation states at their next swollen scale, and
+    the relaxed state with the relaxation parameters), extrapolated to the
+    run: generation sweeps at the per-sweep time interpolated in the scale
+    between the sampled states, plus the relaxation sweeps at the relaxed
+    state's time."""
+    import oracle
+    samples, times = [], {}
+    for label, x, u, lam in states:
+        lam_s = min(lam * (1.0 + w.c_w), 1.0)
+        o = oracle.PlateletSystem(w.box, x, u, w.a0, w.t0, lam=lam_s, lam_t=1.0, c_w=w.c_w, c_m=w.c_m,
+                                  c_r=w.c_r, seed=w.seed)
+        t0 = time.perf_counter()
+        o.sweep()
+        times[label] = time.perf_counter() - t0
+        samples.append((lam, times[label]))
+    o = oracle.PlateletSystem(w.box, relaxed[0], relaxed[1], w.a0, w.t0, lam=1.0, lam_t=1.0, c_w=0.0,
+                              c_m=0.1 * D, c_r=0.1, seed=w.seed)
+    t0 = time.perf_counter()
+    o.sweep()
+    t_rel = time.perf_counter() - t0
+    t_gen = weighted_oracle_time(samples, record)
+    sweeps = record[-1][1] + relax
+    total = t_gen + relax * t_rel
+    return {"value": w.n * sweeps / total, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "one sweep of the single-threaded binary64 reference from each of "
+                      + ", ".join(f"{k}: {v:.2f} s" for k, v in times.items())
+                      + f" (states of the GPU generation) and from the relaxed state: {t_rel:.2f} s",
+            "extrapolated_time_to_target_s": t_gen, "extrapolated_relaxation_s": relax * t_rel,
+            "note": "extrapolated: generation sweeps at per-sweep times interpolated in the scale between the "
+                    "sampled states, plus the relaxation sweeps at the relaxed state's time"}
+
+
 def run_platelets(args, rank, world, local_rank):
     """20000 spherodisks of aspect ratio 100 from a bounding-sphere RSA start
     to number density 5 (Eq. 1) with house-of-cards parameters, then
@@ -875,27 +910,27 @@ def run_platelets(args, rank, world, local_rank):
     dev, e2e, upd = combine_ranks(dev, e2e, upd, dist, torch.device("cuda", local_rank))
     if rank != 0:
         return
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        import oracle
-        o = oracle.PlateletSystem(w.box, w.x, w.u, w.a0, w.t0, lam=w.lambda0, lam_t=1.0, c_w=w.c_w, c_m=w.c_m,
-                                  c_r=w.c_r, seed=w.seed)
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < 15.0 and o.lam < 1.0:
-            o.iterate()
-        dt = time.perf_counter() - t0
-        sw = o.counters()["sweeps"]
-        cpu = {"value": w.n * sw / dt, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"the first {o.counters()['iters']} iterations of the same generation ({sw} sweeps, "
-                         f"{dt:.1f} s, single-threaded binary64 reference, reaching rho = "
-                         f"{w.rho_t * o.lam ** 3:.2f}; the early sweeps are the cheapest ones)"}
     r0 = res[0]
-    # neighbour alignment of the house of cards (a generation alone) and after the relaxation
+    # the generation again in chunks of 10 iterations (same result), keeping
+    # the states the reference is timed on: the start, the first past
+    # rho = 2.5 and the house of cards at rho = 5; also the neighbour
+    # alignment of the house of cards and after the relaxation
     g = srm.Platelets(w.box, w.x, w.u, w.a0, w.t0, w.lambda0, 1.0, w.seed, c_w=w.c_w, c_m=w.c_m, c_r=w.c_r,
                       stream=stream.cuda_stream)
-    g.run_to_target(4000)
-    hx, hu, _ = g.state()
+    record, states = [(w.lambda0, 0)], [("start", w.x, w.u, w.lambda0)]
+    while True:
+        info = g.run_to_target(10)
+        hx, hu, st = g.state()
+        record.append((st["lambda_"], int(st["sweep"])))
+        if len(states) == 1 and st["rho"] >= 0.5 * w.rho_t:
+            states.append((f"rho={st['rho']:.2f}", hx, hu, st["lambda_"]))
+        if info["converged"]:
+            break
+    states.append((f"rho={st['rho']:.2f}", hx, hu, st["lambda_"]))
     g.close()
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = platelet_cpu_baseline(w, states, record, last["relaxed"], relax, D)
     order = {"house_of_cards": alignment(hx, hu), "relaxed": alignment(*last["relaxed"]),
              "measure": "mean |n_i . n_j| over pairs of centres closer than D; 0.5 for random orientations"}
     line = {

@@ -252,17 +252,22 @@ srm_status srm_get_state(srm_rve *h, srm_state_info *out);
 typedef struct srm_tuning {
     int32_t sweep_blocks_per_sm;   /* blocks per SM of the persistent sweep grid; 0 = all that fit */
     int32_t stage_capacity;        /* candidates a sweep warp stages in shared memory (rounded up to a
-                                      multiple of 32, clamped to [64, 512] FP32 / [64, 256] FP64;
+                                      multiple of 32, clamped to [64, 1024] FP32 / [64, 384] FP64;
                                       <= 0 keeps the current one) */
     int32_t candidates;            /* autotune output: shapes tried */
-    int32_t reserved;
+    int32_t sweep_path;            /* FP32 sweep kernel: 1 = general path only (fewer registers, more
+                                      resident warps), 2 = with the staged path (a cell's whole stencil
+                                      copied to shared memory); 0 keeps the current one.  The FP64
+                                      sweep has the general path only (2 is SRM_E_ARG there).  Default
+                                      at creation: 1, with the staging capacity at most 256 */
     double ns_per_particle_sweep;  /* autotune output: best device time per particle sweep */
 } srm_tuning;
 
 /* Autotuner: runs the RVE (or batch) for `supersteps` super-steps (>= 1,
  * rounded up to whole recorded graphs of 8) with each candidate shape --
  * blocks per SM from 2 to the resident maximum, staging capacity at the
- * current value, half and twice -- in two interleaved rounds, scores each
+ * current value, half and twice, both FP32 sweep paths -- in two
+ * interleaved rounds, scores each
  * by device time per particle sweep (CUDA events) and keeps the fastest.
  * The super-steps are real work: the RVEs advance (and may finish).  *best
  * (may be NULL) receives the chosen shape.  Synchronises the stream. */

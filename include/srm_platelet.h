@@ -73,7 +73,12 @@ typedef struct srm_plt_params {
                          /* difference to a platelet near a face is taken to   */
                          /* its periodic image, (x_j + s L) - x_i, one         */
                          /* rounding per axis                                  */
-    int32_t reserved;
+    int32_t sweep_kernel; /* 0: a block per cell with the 27 cells around it  */
+                         /* in shared memory wherever that set holds every     */
+                         /* platelet a trial can touch (stencil half-width 1   */
+                         /* and 2 (a + t) + 2^-15 a + 2 c_m below the cell     */
+                         /* width), else a warp per cell reading global        */
+                         /* memory; 1: always a warp per cell.  Same results.  */
 } srm_plt_params;
 
 /* Defaults: c_w = 0.01, c_m = 0 (must be set), c_r = 0, N_k = N_l =
@@ -156,6 +161,13 @@ srm_status srm_plt_state(srm_plt *h, double *x, double *u, double *lambda, doubl
  * SRM_E_ARG for m outside [0, 2^31), a <= 0 or t <= 0. */
 srm_status srm_plt_collide_pairs(const double *dj, const double *ni, const double *nj, int64_t m, double a,
                                  double t, uint8_t *out, void *cuda_stream);
+
+/* Sweep kernels used so far: out[0] sweeps run by the block-per-cell kernel
+ * with the staged neighbourhood, out[1] sweeps run by the warp-per-cell
+ * kernel, out[2] cells the block-per-cell kernel moved from global memory
+ * because their 27 cells held more than 1024 platelets.  Synchronises the
+ * stream. */
+srm_status srm_plt_sweep_stats(srm_plt *h, int64_t out[3]);
 
 void srm_plt_destroy(srm_plt *h);
 

@@ -95,13 +95,13 @@ class srm_job(Structure):
 
 class srm_tuning(Structure):
     _fields_ = [("sweep_blocks_per_sm", c_int32), ("stage_capacity", c_int32), ("candidates", c_int32),
-                ("reserved", c_int32), ("ns_per_particle_sweep", c_double)]
+                ("sweep_path", c_int32), ("ns_per_particle_sweep", c_double)]
 
 
 class srm_plt_params(Structure):
     _fields_ = [("c_w", c_double), ("c_m", c_double), ("c_r", c_double), ("N_k", c_int32), ("N_l", c_int32),
                 ("N_shake", c_int32), ("wait_limit", c_int32), ("sweep0", c_uint64), ("images", c_int32),
-                ("reserved", c_int32)]
+                ("sweep_kernel", c_int32)]
 
 
 class srm_plt_step_info(Structure):
@@ -197,6 +197,7 @@ def load() -> ctypes.CDLL:
                                   c_int32),
                 "srm_plt_collide_pairs": ([c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double, c_void_p,
                                            c_void_p], c_int32),
+                "srm_plt_sweep_stats": ([H, POINTER(c_int64)], c_int32),
                 "srm_plt_destroy": ([H], None),
             }
             for name, (args, res) in sig.items():
@@ -445,8 +446,9 @@ class Rve:
         _check(load().srm_autotune(self.h, int(supersteps), ctypes.byref(t)))
         return _as_dict(t)
 
-    def set_tuning(self, sweep_blocks_per_sm: int, stage_capacity: int = 0):
-        t = srm_tuning(sweep_blocks_per_sm=int(sweep_blocks_per_sm), stage_capacity=int(stage_capacity))
+    def set_tuning(self, sweep_blocks_per_sm: int, stage_capacity: int = 0, sweep_path: int = 0):
+        t = srm_tuning(sweep_blocks_per_sm=int(sweep_blocks_per_sm), stage_capacity=int(stage_capacity),
+                       sweep_path=int(sweep_path))
         _check(load().srm_set_tuning(self.h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -593,8 +595,9 @@ class Batch:
         _check(load().srm_batch_autotune(self.h, int(supersteps), ctypes.byref(t)))
         return _as_dict(t)
 
-    def set_tuning(self, sweep_blocks_per_sm: int, stage_capacity: int = 0):
-        t = srm_tuning(sweep_blocks_per_sm=int(sweep_blocks_per_sm), stage_capacity=int(stage_capacity))
+    def set_tuning(self, sweep_blocks_per_sm: int, stage_capacity: int = 0, sweep_path: int = 0):
+        t = srm_tuning(sweep_blocks_per_sm=int(sweep_blocks_per_sm), stage_capacity=int(stage_capacity),
+                       sweep_path=int(sweep_path))
         _check(load().srm_batch_set_tuning(self.h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -727,7 +730,7 @@ class Platelets:
     rotation rate c_r."""
 
     def __init__(self, box, x, u, a0, t0, lambda0, lambda_t, seed, *, c_m, c_w=0.01, c_r=0.0, N_k=10, N_l=10,
-                 N_shake=10, wait_limit=0, sweep0=0, images=False, stream=None):
+                 N_shake=10, wait_limit=0, sweep0=0, images=False, sweep_kernel=0, stream=None):
         import torch
         lib = load()
         self.box = tuple(float(v) for v in box)
@@ -738,7 +741,9 @@ class Platelets:
         p.c_w, p.c_m, p.c_r, p.N_k, p.N_l, p.N_shake = c_w, c_m, c_r, N_k, N_l, N_shake
         p.wait_limit, p.sweep0 = wait_limit, sweep0
         self._images = 1 if images else 0
+        self._sweep_kernel = int(sweep_kernel)
         p.images = self._images
+        p.sweep_kernel = self._sweep_kernel
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         L = (c_double * 3)(*self.box)
@@ -759,6 +764,7 @@ class Platelets:
         load().srm_plt_params_default(ctypes.byref(p))
         p.c_w, p.c_m, p.c_r, p.N_k, p.N_l, p.N_shake, p.wait_limit = c_w, c_m, c_r, N_k, N_l, N_shake, wait_limit
         p.images = self._images
+        p.sweep_kernel = self._sweep_kernel
         _check(load().srm_plt_set_params(self._h, ctypes.byref(p)))
 
     def step(self) -> dict:
@@ -777,6 +783,13 @@ class Platelets:
         acc = c_int64()
         _check(load().srm_plt_sweeps(self._h, int(count), ctypes.byref(acc)))
         return acc.value
+
+    def sweep_stats(self) -> dict:
+        """Sweeps by kernel (block per cell with the staged neighbourhood;
+        warp per cell) and cells the block kernel could not stage."""
+        out = (c_int64 * 3)()
+        _check(load().srm_plt_sweep_stats(self._h, out))
+        return {"staged_sweeps": out[0], "warp_sweeps": out[1], "unstaged_cells": out[2]}
 
     def check(self):
         cnt = c_int64()

@@ -45,7 +45,9 @@ srm_status srm_batch_create(srm_batch **out, const srm_job *jobs, int32_t n_jobs
     g.f32 = qs[0].p.precision == SRM_PREC_F32;
     int cap = 64;
     for (const Prep &q : qs) cap = std::max(cap, q.cap_est);
-    g.cap = std::min(cap, srm::sweep_cap_max(g.f32));
+    g.cap = default_capacity(cap, g.f32);
+    g.sweep_path = default_sweep_path(g.f32, g.cap);
+    g.stencil_est = cap;
     srm_status st = SRM_OK;
     for (int32_t i = 0; i < n_jobs && st == SRM_OK; i++) {
         const Prep &q = qs[(size_t)i];
@@ -79,6 +81,7 @@ srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_
     g.f32 = precision == SRM_PREC_F32;
     const int cap = stage_capacity > 0 ? stage_capacity : 256;
     g.cap = std::max(64, std::min((cap + 31) / 32 * 32, srm::sweep_cap_max(g.f32)));
+    g.sweep_path = default_sweep_path(g.f32, g.cap);
     srm_status st = SRM_OK;
     for (int32_t i = 0; i < n_slots && st == SRM_OK; i++) {
         Member *mb = new Member();
@@ -150,7 +153,7 @@ srm_status srm_batch_autotune(srm_batch *b, int32_t supersteps, srm_tuning *best
 srm_status srm_batch_set_tuning(srm_batch *b, const srm_tuning *t)
 {
     if (!b || !t) return fail(SRM_E_ARG, "null argument");
-    return group_set_tuning(b->g, t->sweep_blocks_per_sm, t->stage_capacity);
+    return group_set_tuning(b->g, t->sweep_blocks_per_sm, t->stage_capacity, t->sweep_path);
 }
 
 srm_status srm_batch_get_tuning(srm_batch *b, srm_tuning *t)
@@ -159,6 +162,7 @@ srm_status srm_batch_get_tuning(srm_batch *b, srm_tuning *t)
     *t = srm_tuning{};
     t->sweep_blocks_per_sm = b->g.sweep_bps;
     t->stage_capacity = b->g.cap;
+    t->sweep_path = b->g.sweep_path;
     return SRM_OK;
 }
 

@@ -624,6 +624,7 @@ template <int DIM, bool F32>
 __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, unsigned char *base, int cap,
                                                   CellCount &cc)
 {
+    if constexpr (!F32) return false;  // the FP64 sweep has no staged variant
     using SM = SweepSmem<F32>;
     using PT = typename SM::PT;
     using DT = typename SM::DT;
@@ -1153,11 +1154,17 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     return true;
 }
 
-// Blocks per SM the register allocation must allow (build-time knobs; the
-// defaults are the fastest measured without spills: 96 registers for the
-// FP32 form, 128 for the FP64 form).
+// Blocks per SM the register allocation must allow (build-time knobs).  The
+// FP32 form comes in two variants: with the staged path (128 registers, no
+// spills) and general path only (96 registers, no spills: five blocks of
+// four warps per SM where shared memory allows, the better choice for
+// stencils of a few particles, where a cell's work is short and latency is
+// hidden by more warps).  The FP64 form has the general path only.
 #ifndef SRM_SWEEP_MIN_BLOCKS
 #define SRM_SWEEP_MIN_BLOCKS 4
+#endif
+#ifndef SRM_SWEEP_MIN_BLOCKS_GENERAL
+#define SRM_SWEEP_MIN_BLOCKS_GENERAL 5
 #endif
 #ifndef SRM_SWEEP_MIN_BLOCKS_F64
 #define SRM_SWEEP_MIN_BLOCKS_F64 4
@@ -1167,13 +1174,15 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
 // launch: work item tg is cell tg mod W of colour tg / W, W the colour cells
 // of all DIM-dimensional RVEs at work (offsets act), so items are handed out
 // in colour order.
-template <int DIM, bool F32>
-__global__ void __launch_bounds__(SW_WARPS * 32, F32 ? SRM_SWEEP_MIN_BLOCKS : SRM_SWEEP_MIN_BLOCKS_F64)
+template <int DIM, bool F32, bool STAGED>
+__global__ void __launch_bounds__(SW_WARPS * 32, !F32 ? SRM_SWEEP_MIN_BLOCKS_F64
+                                                 : (STAGED ? SRM_SWEEP_MIN_BLOCKS : SRM_SWEEP_MIN_BLOCKS_GENERAL))
     k_sweep_df(BatchDev *bd, int cap)
 {
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    unsigned char *base = smem + (size_t)wib * SweepSmem<F32>::bytes(cap);
+    unsigned char *base =
+        smem + (size_t)wib * (STAGED ? SweepSmem<F32>::bytes(cap) : SweepSmem<F32>::bytes_general(cap));
     const int B = bd->B;
     const int32_t *off = DIM == 3 ? bd->act3 : bd->act2;
     uint32_t *wq = &bd->wq[DIM == 3 ? 0 : 1];
@@ -1192,7 +1201,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32, F32 ? SRM_SWEEP_MIN_BLOCKS : SR
         RveDev *st = bd->rv[r];
         if (!st->active || st->dim != DIM || t >= st->nsub) continue;
         CellCount cc;
-        if (!sweep_cell_staged<DIM, F32>(st, chi, t, base, cap, cc)) sweep_cell<DIM, F32>(st, chi, t, base, cap, cc);
+        bool staged = false;
+        if constexpr (STAGED) staged = sweep_cell_staged<DIM, F32>(st, chi, t, base, cap, cc);
+        if (!staged) sweep_cell<DIM, F32>(st, chi, t, base, cap, cc);
         const unsigned examined = __reduce_add_sync(0xffffffffu, cc.examined);
         if (lane == 0) {
             if (cc.moved) atomicAdd(&st->red[3], (unsigned long long)cc.moved);
@@ -1209,8 +1220,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32, F32 ? SRM_SWEEP_MIN_BLOCKS : SR
 // at most 32 chunks.
 int sweep_cap_max(bool f32) { return f32 ? 1024 : 384; }
 
-static size_t sweep_smem(bool f32, int cap)
+static size_t sweep_smem(bool f32, int cap, bool staged)
 {
+    if (!staged) return SW_WARPS * (f32 ? SweepSmem<true>::bytes_general(cap) : SweepSmem<false>::bytes_general(cap));
     return SW_WARPS * (f32 ? SweepSmem<true>::bytes(cap) : SweepSmem<false>::bytes(cap));
 }
 
@@ -1226,22 +1238,35 @@ static int resident_blocks(K kern, size_t smem)
     return nb > 0 ? nb : 1;
 }
 
-template <int DIM, bool F32>
+template <int DIM, bool F32, bool STAGED>
 static void launch_sweep_dim(const BatchShape &b, cudaStream_t s)
 {
-    const size_t smem = sweep_smem(F32, b.cap);
+    const size_t smem = sweep_smem(F32, b.cap, STAGED);
     const int64_t want64 = (b.sub_total * (DIM == 3 ? 27 : 9) + SW_WARPS - 1) / SW_WARPS;
     const int want = (int)(want64 > 0x7fffffff ? 0x7fffffff : want64);
-    int per_sm = resident_blocks(k_sweep_df<DIM, F32>, smem);
+    int per_sm = resident_blocks(k_sweep_df<DIM, F32, STAGED>, smem);
     if (b.sweep_bps > 0 && b.sweep_bps < per_sm) per_sm = b.sweep_bps;
     const int res = per_sm * (g_sms > 0 ? g_sms : 1);
-    k_sweep_df<DIM, F32><<<want < res ? want : res, SW_WARPS * 32, smem, s>>>(b.d, b.cap);
+    k_sweep_df<DIM, F32, STAGED><<<want < res ? want : res, SW_WARPS * 32, smem, s>>>(b.d, b.cap);
 }
 
-int sweep_blocks_per_sm(bool f32, int cap)
+// The FP64 form always takes the general path: measured, staging made it
+// slower (1e5 monodisperse spheres: 29%; the clustered 1e6-sphere RVE: 11%),
+// its binary64 arithmetic dominating what staging saves.
+template <int DIM>
+static void launch_sweep_form(const BatchShape &b, cudaStream_t s)
 {
-    const size_t smem = sweep_smem(f32, cap);
-    return f32 ? resident_blocks(k_sweep_df<3, true>, smem) : resident_blocks(k_sweep_df<3, false>, smem);
+    if (!b.f32) launch_sweep_dim<DIM, false, false>(b, s);
+    else if (b.staged) launch_sweep_dim<DIM, true, true>(b, s);
+    else launch_sweep_dim<DIM, true, false>(b, s);
+}
+
+int sweep_blocks_per_sm(bool f32, int cap, bool staged)
+{
+    staged = staged && f32;
+    const size_t smem = sweep_smem(f32, cap, staged);
+    if (!f32) return resident_blocks(k_sweep_df<3, false, false>, smem);
+    return staged ? resident_blocks(k_sweep_df<3, true, true>, smem) : resident_blocks(k_sweep_df<3, true, false>, smem);
 }
 
 // Trial directions (k_draw), then the sweep of the 3D and of the 2D RVEs
@@ -1252,14 +1277,8 @@ void launch_sweep(const BatchShape &b, cudaStream_t s)
     const int nb = plan_blocks(b.blocks_p);
     if (b.f32) k_draw<true><<<nb, 256, 0, s>>>(b.d);
     else k_draw<false><<<nb, 256, 0, s>>>(b.d);
-    if (b.has3d) {
-        if (b.f32) launch_sweep_dim<3, true>(b, s);
-        else launch_sweep_dim<3, false>(b, s);
-    }
-    if (b.has2d) {
-        if (b.f32) launch_sweep_dim<2, true>(b, s);
-        else launch_sweep_dim<2, false>(b, s);
-    }
+    if (b.has3d) launch_sweep_form<3>(b, s);
+    if (b.has2d) launch_sweep_form<2>(b, s);
 }
 
 int sweep_launches(const BatchShape &b) { return 1 + (b.has3d ? 1 : 0) + (b.has2d ? 1 : 0); }
@@ -1272,11 +1291,15 @@ void sweep_configure()
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const int s32 = (int)sweep_smem(true, sweep_cap_max(true)), s64 = (int)sweep_smem(false, sweep_cap_max(false));
-    cudaFuncSetAttribute(k_sweep_df<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-    cudaFuncSetAttribute(k_sweep_df<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-    cudaFuncSetAttribute(k_sweep_df<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-    cudaFuncSetAttribute(k_sweep_df<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    const int s32 = (int)sweep_smem(true, sweep_cap_max(true), true);
+    const int g32 = (int)sweep_smem(true, sweep_cap_max(true), false);
+    const int s64 = (int)sweep_smem(false, sweep_cap_max(false), false);
+    cudaFuncSetAttribute(k_sweep_df<3, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    cudaFuncSetAttribute(k_sweep_df<2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    cudaFuncSetAttribute(k_sweep_df<3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
+    cudaFuncSetAttribute(k_sweep_df<2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
+    cudaFuncSetAttribute(k_sweep_df<3, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    cudaFuncSetAttribute(k_sweep_df<2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
 }
 
 }  // namespace srm

@@ -268,7 +268,7 @@ struct PltDev {
     int32_t *cell_of, *count, *start, *members;
     uint32_t *stamp;
     uint32_t *ctr;  // [0] work counter, [1] status
-    unsigned long long *acc;  // [0] accepted moves, [1] colliding platelets
+    unsigned long long *acc;  // [0] accepted moves, [1] colliding platelets, [2] unstaged cells
 };
 
 __device__ __forceinline__ int32_t wrapc(int32_t c, int32_t n)
@@ -584,6 +584,274 @@ __global__ void __launch_bounds__(128) k_psweep(PltDev d)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sweep with the cell's neighbourhood in shared memory (grids whose stencil
+// half-width is 1 on every axis).  One block of CW warps per cell: after the
+// waits the block copies the platelets listed in the 27 cells around the
+// home cell (centres and normals in binary64, plus binary32 offsets from the
+// home cell's centre) to shared memory.  These hold every platelet a trial of
+// a home platelet can touch: a home platelet moves at most c_m, a listed
+// platelet has moved at most c_m from where it was binned, and a contact
+// needs centres within 2 (a + t) (plus the 2^-16 a widening), all below the
+// cell width when the half-width is 1.  Platelets beyond reach are never in
+// contact (the first pre-test), so the OR over the staged set equals the OR
+// over the 27 cells around the trial's own cell.
+//
+// The home platelets go one after the other in id order.  Warp k forms and
+// tests trial l0 + k, so CW trials are decided at once; the move is the
+// first clean trial in trial order, and a warp stops early once a trial of
+// lower index is known to be clean (its own answer no longer matters).  A
+// trial test: a binary32 scan of the staged offsets keeps the platelets
+// within the pre-test's reach (with a relative margin of 2^-10, far above
+// the rounding of the offsets), then the binary64 minimum-image difference,
+// the binary32 pre-tests and the rim bisections as in trial_collides.  The
+// mover's new state goes to global memory and to the staged copy; its
+// binary32 offset is recomputed.  Thread 0 makes every global write of the
+// cell.
+// ---------------------------------------------------------------------------
+constexpr int CW = 8;          // warps of a cell block (trials decided at once)
+constexpr int CCAP = 1024;     // platelets of the 27 cells a block stages
+constexpr int CSURV = 128;     // prefilter survivors a warp lists per trial (more are tested in place)
+constexpr int CPAIRS = 32;     // pairs per warp queued for the rim tests (more are tested in place)
+
+struct CellStage {
+    double4_32a X[CCAP], U[CCAP];
+    float4 F[CCAP];  // offset from the home cell's centre (minimum image), binary32
+    int32_t id[CCAP];
+    int16_t surv[CW][CSURV];
+    PairGeom pair[CW][CPAIRS];
+    int npair[CW];
+    int cstart[28];
+    int ccell[27];
+    int best[2];  // lowest clean trial of the current round (two rounds alternate)
+    int item, ok;
+};
+
+__device__ __forceinline__ float4 stage_offset(const PltDev &d, const double4_32a &x, const double c[3])
+{
+    double v[3] = {x.x - c[0], x.y - c[1], x.z - c[2]};
+    for (int j = 0; j < 3; j++) {
+        if (v[j] > d.halfL[j]) v[j] -= d.L[j];
+        if (v[j] < -d.halfL[j]) v[j] += d.L[j];
+    }
+    return make_float4((float)v[0], (float)v[1], (float)v[2], 0.0f);
+}
+
+// The full pair decision for staged platelet i against trial (q, u).
+__device__ __forceinline__ bool staged_pair(const PltDev &d, const CellStage &S, int i, const double q[3],
+                                            const double u[3])
+{
+    double dj[3];
+    min_image(d, S.X[i], q, dj);
+    const double nt[3] = {S.U[i].x, S.U[i].y, S.U[i].z};
+    return collide(dj, u, nt, d.a, d.t);
+}
+
+// Does trial (q, u) of platelet pid (trial index l) touch a staged platelet?
+// Warp-collective; may return early (true) once a trial below l is clean.
+__device__ bool trial_collides_staged(const PltDev &d, CellStage &S, int nst, int32_t pid, int l, const int *best,
+                                      const double q[3], const double u[3], const double c[3], int warp, int lane)
+{
+    float qf[3];
+    {
+        const float4 o = stage_offset(d, double4_32a{q[0], q[1], q[2], 0.0}, c);
+        qf[0] = o.x;
+        qf[1] = o.y;
+        qf[2] = o.z;
+    }
+    const float Lf[3] = {(float)d.L[0], (float)d.L[1], (float)d.L[2]};
+    const float hLf[3] = {0.5f * Lf[0], 0.5f * Lf[1], 0.5f * Lf[2]};
+    const float af = (float)d.a, tf = (float)d.t;
+    const float rf = ((af + af) + ((tf + tf) + af * SLACK)) * (1.0f + 0x1p-10f);
+    const float rf2 = rf * rf;
+    bool hit = false;
+    int n = 0;
+    for (int i0 = 0; i0 < nst; i0 += 32) {
+        const int i = i0 + lane;
+        bool keep = false;
+        if (i < nst && S.id[i] != pid) {
+            const float4 f = S.F[i];
+            float v[3] = {f.x - qf[0], f.y - qf[1], f.z - qf[2]};
+            for (int j = 0; j < 3; j++) {
+                if (v[j] > hLf[j]) v[j] -= Lf[j];
+                if (v[j] < -hLf[j]) v[j] += Lf[j];
+            }
+            keep = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] <= rf2;
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        const int at = n + __popc(bal & ((1u << lane) - 1u));
+        if (keep) {
+            if (at < CSURV) S.surv[warp][at] = (int16_t)i;
+            else if (!hit) hit = staged_pair(d, S, i, q, u);
+        }
+        n += __popc(bal);
+    }
+    if (lane == 0) S.npair[warp] = 0;
+    __syncwarp();
+    if (__any_sync(FULL, hit)) return true;
+    if (n > CSURV) n = CSURV;
+    for (int k = lane; k < n && !hit; k += 32) {
+        const int i = S.surv[warp][k];
+        double dj[3];
+        min_image(d, S.X[i], q, dj);
+        const double nt[3] = {S.U[i].x, S.U[i].y, S.U[i].z};
+        PairGeom g;
+        if (!pair_pretest(dj, u, nt, d.a, d.t, g)) continue;
+        const int slot = atomicAdd(&S.npair[warp], 1);
+        if (slot < CPAIRS) {
+            S.pair[warp][slot] = g;
+        } else {
+            for (int which = 0; which < 2 && !hit; which++)
+                for (int k0 = 0; k0 < 8 && !hit; k0++) hit = pair_arc(g, which, k0);
+        }
+    }
+    __syncwarp();
+    if (__any_sync(FULL, hit)) return true;
+    const int np = S.npair[warp] < CPAIRS ? S.npair[warp] : CPAIRS;
+    const int tasks = 16 * np;
+    for (int r0 = 0; r0 < tasks; r0 += 32) {
+        // a lower trial is clean: this answer is unused (one vote, so that
+        // the warp leaves together)
+        if (__any_sync(FULL, *(volatile const int *)best < l)) return true;
+        const int tsk = r0 + lane;
+        bool h = false;
+        if (tsk < tasks) h = pair_arc(S.pair[warp][tsk >> 4], (tsk >> 3) & 1, tsk & 7);
+        if (__any_sync(FULL, h)) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(CW * 32, 1) k_psweep_staged(PltDev d)
+{
+    extern __shared__ __align__(32) unsigned char psm[];
+    CellStage &S = *reinterpret_cast<CellStage *>(psm);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int S0 = d.n[0] / 3, S1 = d.n[1] / 3, S2 = d.n[2] / 3;
+    const int per = S0 * S1 * S2;
+    const int total = 27 * per;
+    int round = 0;
+    if (tid == 0) S.best[0] = S.best[1] = d.N_l;
+    for (;;) {
+        if (tid == 0) S.item = (int)atomicAdd(&d.ctr[0], 1u);
+        __syncthreads();
+        const int w = S.item;
+        if (w >= total) return;
+        const int chi = w / per, r = w - chi * per;
+        const int cx = 3 * (r % S0) + chi % 3, cy = 3 * ((r / S0) % S1) + (chi / 3) % 3;
+        const int cz = 3 * (r / (S0 * S1)) + chi / 9;
+        const int cell = cx + d.n[0] * (cy + d.n[1] * cz);
+        if (warp == 0) {
+            const bool ok = wait_lower(d, cx, cy, cz, chi, lane);
+            if (lane == 0) S.ok = ok;
+        }
+        __syncthreads();
+        if (!S.ok) return;
+        // warp 0 synchronised with the producers' release stores; every
+        // thread orders its own reads after them
+        fence_acquire();
+        if (tid < 27) {
+            const int nx = wrapc(cx + tid % 3 - 1, d.n[0]), ny = wrapc(cy + (tid / 3) % 3 - 1, d.n[1]);
+            const int nz = wrapc(cz + tid / 9 - 1, d.n[2]);
+            const int nc = nx + d.n[0] * (ny + d.n[1] * nz);
+            S.ccell[tid] = nc;
+            S.cstart[tid + 1] = d.start[nc + 1] - d.start[nc];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            S.cstart[0] = 0;
+            for (int k = 1; k <= 27; k++) S.cstart[k] += S.cstart[k - 1];
+        }
+        __syncthreads();
+        const int nst = S.cstart[27];
+        const double c[3] = {(cx + 0.5) * d.w[0], (cy + 0.5) * d.w[1], (cz + 0.5) * d.w[2]};
+        unsigned long long acc = 0;
+        if (nst > CCAP) {
+            // too many to stage: warp 0 moves the cell's platelets as k_psweep
+            // does (global memory), the other warps wait
+            if (tid == 0) atomicAdd(&d.acc[2], 1ull);
+            if (warp == 0) {
+                WarpScratch &ws = *reinterpret_cast<WarpScratch *>(psm);  // over the unused stage
+                const int32_t k1 = d.start[cell + 1];
+                for (int32_t k = d.start[cell]; k < k1; k++) {
+                    const int32_t pid = d.members[k];
+                    const double4_32a xp = d.X[pid], up = d.U[pid];
+                    const double x0[3] = {xp.x, xp.y, xp.z}, u0[3] = {up.x, up.y, up.z};
+                    for (int l = 0; l < d.N_l; l++) {
+                        double q[3], u[3];
+                        trial(d, (uint64_t)pid, (uint64_t)l, x0, u0, q, u);
+                        if (!trial_collides(d, pid, q, u, lane, ws)) {
+                            if (lane == 0) {
+                                d.X[pid] = double4_32a{q[0], q[1], q[2], 0.0};
+                                d.U[pid] = double4_32a{u[0], u[1], u[2], 0.0};
+                            }
+                            acc++;
+                            break;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        } else {
+            for (int i = tid; i < nst; i += CW * 32) {
+                int k = 0;
+                while (S.cstart[k + 1] <= i) k++;
+                const int32_t id = d.members[d.start[S.ccell[k]] + (i - S.cstart[k])];
+                const double4_32a x = d.X[id];
+                S.X[i] = x;
+                S.U[i] = d.U[id];
+                S.F[i] = stage_offset(d, x, c);
+                S.id[i] = id;
+            }
+            __syncthreads();
+            // the home cell is stencil cell 13 (offsets 0, 0, 0); its
+            // platelets are listed in ascending id
+            const int hs = S.cstart[13], he = S.cstart[14];
+            for (int m = hs; m < he; m++) {
+                const int32_t pid = S.id[m];
+                const double4_32a xp = S.X[m], up = S.U[m];
+                const double x0[3] = {xp.x, xp.y, xp.z}, u0[3] = {up.x, up.y, up.z};
+                for (int l0 = 0; l0 < d.N_l; l0 += CW) {
+                    const int l = l0 + warp;
+                    int *best = &S.best[round & 1];
+                    double q[3], u[3];
+                    bool clean = false;
+                    if (l < d.N_l) {
+                        trial(d, (uint64_t)pid, (uint64_t)l, x0, u0, q, u);
+                        clean = !trial_collides_staged(d, S, nst, pid, l, best, q, u, c, warp, lane);
+                        if (clean && lane == 0) atomicMin(best, l);
+                    }
+                    __syncthreads();
+                    const int lb = *best;  // N_l: no clean trial this round
+                    if (lb < d.N_l && lb == l && lane == 0) {
+                        const double4_32a nx4{q[0], q[1], q[2], 0.0}, nu4{u[0], u[1], u[2], 0.0};
+                        S.X[m] = nx4;
+                        S.U[m] = nu4;
+                        S.F[m] = stage_offset(d, nx4, c);
+                    }
+                    if (tid == 0) S.best[(round + 1) & 1] = d.N_l;
+                    round++;
+                    __syncthreads();
+                    if (lb < d.N_l) {
+                        // thread 0 makes every global write of the cell, so
+                        // that its release of the cell's stamp publishes them
+                        if (tid == 0) {
+                            d.X[pid] = S.X[m];
+                            d.U[pid] = S.U[m];
+                        }
+                        acc++;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (acc) atomicAdd(&d.acc[0], acc);
+            st_release(&d.stamp[cell], d.epoch);
+        }
+    }
+}
+
 // Algorithm 6: does platelet i collide with any other platelet listed in
 // the 27 cells around its cell?
 __global__ void __launch_bounds__(128) k_pcheck(PltDev d, uint8_t *flags)
@@ -647,6 +915,7 @@ struct srm_plt {
     int64_t ncells_cap = 0;
     uint32_t epoch = 0;
     int64_t iters = 0, accepted = 0, shaken = 0, sweeps = 0, moves = 0;
+    int64_t staged_sweeps = 0, warp_sweeps = 0;  // sweeps by kernel
 };
 
 namespace {
@@ -675,6 +944,7 @@ srm_status check_params(const srm_plt_params &p)
     if (!(p.c_r >= 0.0 && p.c_r < 1.0)) return fail(SRM_E_ARG, "c_r must be in [0, 1)");
     if (p.N_k < 1 || p.N_l < 1 || p.N_l > 65535 || p.N_shake < 0)
         return fail(SRM_E_ARG, "N_k >= 1, N_l in 1..65535, N_shake >= 0");
+    if (p.sweep_kernel != 0 && p.sweep_kernel != 1) return fail(SRM_E_ARG, "sweep_kernel must be 0 or 1");
     return SRM_OK;
 }
 
@@ -764,6 +1034,31 @@ srm_status bin(srm_plt *h, int c, double lam, double lam_grid, PltDev &d)
     return SRM_OK;
 }
 
+// The staged sweep holds every platelet a trial can touch when a contact
+// (centres within 2 (a + t) + 2^-16 a, the kernel's widened reach) plus the
+// two moves of at most c_m stays below the cell width on every axis (taken
+// with the widening doubled).
+bool staged_fits(const PltDev &d)
+{
+    const double need = (2.0 * (d.a + d.t) + d.a * 0x1p-15) + 2.0 * d.c_m;
+    for (int a = 0; a < 3; a++)
+        if (d.H[a] != 1 || !(need < d.w[a])) return false;
+    return true;
+}
+
+int staged_blocks_per_sm()
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(srm::plt::k_psweep_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(srm::plt::CellStage));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srm::plt::k_psweep_staged, srm::plt::CW * 32,
+                                                      sizeof(srm::plt::CellStage));
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm;
+}
+
 // One sweep of Algorithm 3 on copy c at scale lam, binned on the grid of
 // lam_grid; advances the sweep counter.
 srm_status sweep_once(srm_plt *h, int c, double lam, double lam_grid)
@@ -773,9 +1068,22 @@ srm_status sweep_once(srm_plt *h, int c, double lam, double lam_grid)
     if (st != SRM_OK) return st;
     d.epoch = ++h->epoch;
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(uint32_t), h->s));  // work counter (the status word stays)
-    int64_t blocks = ((int64_t)d.ncells + 3) / 4;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    srm::plt::k_psweep<<<(int)blocks, 128, 0, h->s>>>(d);
+    if (h->p.sweep_kernel == 0 && staged_fits(d)) {
+        h->staged_sweeps++;
+        // every block resident at once (a block may wait for any other)
+        const int per_sm = staged_blocks_per_sm();
+        int sms = 0, dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int64_t blocks = (int64_t)per_sm * sms;
+        if (blocks > d.ncells) blocks = d.ncells;
+        srm::plt::k_psweep_staged<<<(int)blocks, srm::plt::CW * 32, sizeof(srm::plt::CellStage), h->s>>>(d);
+    } else {
+        h->warp_sweeps++;
+        int64_t blocks = ((int64_t)d.ncells + 3) / 4;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        srm::plt::k_psweep<<<(int)blocks, 128, 0, h->s>>>(d);
+    }
     CK(cudaGetLastError());
     h->sweep++;
     h->sweeps++;
@@ -893,7 +1201,7 @@ srm_status srm_plt_init(srm_plt **out, const double box[3], int64_t n, double a0
         (st = dalloc(h, &h->U[0], nn)) != SRM_OK || (st = dalloc(h, &h->U[1], nn)) != SRM_OK ||
         (st = dalloc(h, &h->cell_of, nn)) != SRM_OK || (st = dalloc(h, &h->members, nn)) != SRM_OK ||
         (st = dalloc(h, &h->flags, nn)) != SRM_OK || (st = dalloc(h, &h->ctr, 2)) != SRM_OK ||
-        (st = dalloc(h, &h->acc, 2)) != SRM_OK) {
+        (st = dalloc(h, &h->acc, 3)) != SRM_OK) {
         srm_plt_destroy(h);
         return st;
     }
@@ -914,7 +1222,7 @@ srm_status srm_plt_init(srm_plt **out, const double box[3], int64_t n, double a0
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->U[0], hu.data(), sizeof(double) * 4 * nn, cudaMemcpyHostToDevice, h->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ctr, 0, 2 * sizeof(uint32_t), h->s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, 2 * sizeof(unsigned long long), h->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, 3 * sizeof(unsigned long long), h->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);  // host staging buffers go out of scope
     if (e != cudaSuccess) {
         srm_plt_destroy(h);
@@ -1096,6 +1404,18 @@ srm_status srm_plt_collide_pairs(const double *dj, const double *ni, const doubl
     cudaFreeAsync(o, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(SRM_E_CUDA, std::string("pair decisions: ") + cudaGetErrorString(e));
+    return SRM_OK;
+}
+
+srm_status srm_plt_sweep_stats(srm_plt *h, int64_t out[3])
+{
+    if (!h || !out) return fail(SRM_E_ARG, "null argument");
+    unsigned long long unstaged = 0;
+    CK(cudaMemcpyAsync(&unstaged, h->acc + 2, sizeof(unstaged), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    out[0] = h->staged_sweeps;
+    out[1] = h->warp_sweeps;
+    out[2] = (int64_t)unstaged;
     return SRM_OK;
 }
 

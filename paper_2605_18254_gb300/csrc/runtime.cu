@@ -84,15 +84,14 @@ int64_t cells_for(int dim, const double L[3], double rmax, double c_m, double la
     return tot;
 }
 
-// Staging capacity of the warp-per-cell sweep: the sweep copies a cell's
-// whole stencil (3^d cells) to shared memory when it fits, so the capacity
-// is sized from the mean stencil population on the grid of the target scale
-// (the coarsest grid of the run, whose cells hold the most particles), 3^d
-// N / cells, with room for 1.8 times the mean (measured at the end of the
-// 1e6-sphere clustered run: median 1.07, maximum 1.76 times the mean).
-// Denser cells take the general path, which culls and reads what does not
-// fit from global memory (same results); the autotuner also tries half and
-// twice this capacity.
+// Whole-stencil staging estimate: the staged path copies a cell's whole
+// stencil (3^d cells) to shared memory when it fits, so this is sized from
+// the mean stencil population on the grid of the target scale (the coarsest
+// grid of the run, whose cells hold the most particles), 3^d N / cells, with
+// room for 1.8 times the mean (measured at the end of the 1e6-sphere
+// clustered run: median 1.07, maximum 1.76 times the mean).  The general
+// path culls while it stages and needs less (default_capacity); denser
+// cells read what does not fit from global memory (same results).
 static int staging_estimate(const Prep &q)
 {
     int64_t pa[3];
@@ -416,6 +415,8 @@ static srm_status make_batchdev(Group &g, const std::vector<Member *> &ms, Batch
     sh.has2d = has2d;
     sh.cap = g.cap;
     sh.sweep_bps = g.sweep_bps;
+    sh.staged = g.sweep_path == 2;
+    sh.check_cells = g.stencil_est > 256;
     return SRM_OK;
 }
 
@@ -484,13 +485,32 @@ bool idle_mode(int32_t m);
 // staging capacity.  The graphs are recorded again; results do not depend
 // on either (the dataflow order is that of the cells' colours, and cells
 // that do not fit the staging read the rest from global memory).
-srm_status group_set_tuning(Group &g, int sweep_bps, int cap)
+// Launch shape when none is chosen: the sweep kernel with the general path
+// only, staging at most 256 culled candidates per warp.  Measured (GB300,
+// FP32): on the clustered 1e6-sphere RVE the general kernel at capacity 256
+// swept 5% faster than at the whole-stencil estimate 704 (more resident
+// warps, no staging overflow) and 7% faster than the staged kernel; on the
+// ensemble of small RVEs the autotuner picked the general kernel; the staged
+// kernel won on 1e5 monodisperse spheres (7%), where the autotuner finds it.
+int default_sweep_path(bool f32, int cap)
+{
+    (void)f32;
+    (void)cap;
+    return 1;
+}
+
+int default_capacity(int estimate, bool f32) { return std::min(std::min(estimate, 256), srm::sweep_cap_max(f32)); }
+
+srm_status group_set_tuning(Group &g, int sweep_bps, int cap, int path)
 {
     const int cmax = srm::sweep_cap_max(g.f32);
     cap = cap <= 0 ? g.cap : (cap + 31) / 32 * 32;
     if (cap < 64) cap = 64;
     if (cap > cmax) cap = cmax;
     if (sweep_bps < 0) return fail(SRM_E_ARG, "blocks per SM must be >= 0");
+    if (path < 0 || path > 2) return fail(SRM_E_ARG, "sweep path must be 0, 1 or 2");
+    if (path == 2 && !g.f32) return fail(SRM_E_ARG, "the FP64 sweep has no staged variant");
+    if (path == 0) path = g.sweep_path;
     CK(cudaStreamSynchronize(g.stream));
     if (g.g1) cudaGraphExecDestroy(g.g1);
     if (g.gN) cudaGraphExecDestroy(g.gN);
@@ -500,6 +520,8 @@ srm_status group_set_tuning(Group &g, int sweep_bps, int cap)
     g.sweep_bps = sweep_bps;
     g.sh.cap = cap;
     g.sh.sweep_bps = sweep_bps;
+    g.sweep_path = path;
+    g.sh.staged = path == 2;
     srm_status st = capture(g, 1, &g.g1);
     if (st != SRM_OK) return st;
     return capture(g, g.gN_steps, &g.gN);
@@ -525,12 +547,17 @@ srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best)
         c = std::max(64, std::min(cmax, (c + 31) / 32 * 32));
         if (std::find(caps.begin(), caps.end(), c) == caps.end()) caps.push_back(c);
     }
-    std::vector<std::pair<int, int>> cand;
-    for (int c : caps) {
-        const int mx = srm::sweep_blocks_per_sm(g.f32, c);
-        for (int b = 2; b < mx; b++) cand.push_back({b, c});
-        cand.push_back({0, c});
-    }
+    struct Cand {
+        int bps, cap, path;
+    };
+    std::vector<Cand> cand;
+    for (int path = 1; path <= (g.f32 ? 2 : 1); path++)
+        for (int c : caps) {
+            const int mx = srm::sweep_blocks_per_sm(g.f32, c, path == 2);
+            for (int b = 2; b < mx; b++) cand.push_back({b, c, path});
+            cand.push_back({0, c, path});
+        }
+    const int path0 = g.sweep_path;
     std::vector<double> score(cand.size(), 0.0);
     std::vector<int> seen(cand.size(), 0);
     cudaEvent_t e0, e1;
@@ -540,7 +567,7 @@ srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best)
     srm_status st = SRM_OK;
     for (int round = 0; round < 2 && st == SRM_OK; round++) {
         for (size_t k = 0; k < cand.size() && st == SRM_OK; k++) {
-            if ((st = group_set_tuning(g, cand[k].first, cand[k].second)) != SRM_OK) break;
+            if ((st = group_set_tuning(g, cand[k].bps, cand[k].cap, cand[k].path)) != SRM_OK) break;
             if ((st = pull_states(g)) != SRM_OK) break;
             const double w0 = group_work(g);
             CK(cudaEventRecord(e0, g.stream));
@@ -568,8 +595,8 @@ srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best)
             bi = k;
         }
     const bool any = bs < 1e300;
-    const int bps = any ? cand[bi].first : 0, cap = any ? cand[bi].second : cap0;
-    if ((st = group_set_tuning(g, bps, cap)) != SRM_OK) return st;
+    const int bps = any ? cand[bi].bps : 0, cap = any ? cand[bi].cap : cap0, path = any ? cand[bi].path : path0;
+    if ((st = group_set_tuning(g, bps, cap, path)) != SRM_OK) return st;
     // leave every RVE between iterations, as the other calls expect (an
     // iteration takes at most N_k + N_shake + 1 super-steps)
     for (int k = 0; k < 4096; k++) {
@@ -584,7 +611,7 @@ srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best)
         best->sweep_blocks_per_sm = bps;
         best->stage_capacity = cap;
         best->candidates = (int32_t)cand.size();
-        best->reserved = 0;
+        best->sweep_path = path;
         best->ns_per_particle_sweep = any ? 1e6 * bs : 0.0;
     }
     return SRM_OK;
@@ -852,7 +879,9 @@ srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_r
     Group &g = h->g;
     group_setup(g, cuda_stream, alloc);
     g.f32 = q.p.precision == SRM_PREC_F32;
-    g.cap = std::min(q.cap_est, srm::sweep_cap_max(g.f32));
+    g.cap = default_capacity(q.cap_est, g.f32);
+    g.sweep_path = default_sweep_path(g.f32, g.cap);
+    g.stencil_est = q.cap_est;
     Member *mb = new Member();
     mb->dim = q.dim;
     g.m.push_back(mb);
@@ -1079,7 +1108,7 @@ srm_status srm_autotune(srm_rve *h, int32_t supersteps, srm_tuning *best)
 srm_status srm_set_tuning(srm_rve *h, const srm_tuning *t)
 {
     if (!h || !t) return fail(SRM_E_ARG, "null argument");
-    return group_set_tuning(h->g, t->sweep_blocks_per_sm, t->stage_capacity);
+    return group_set_tuning(h->g, t->sweep_blocks_per_sm, t->stage_capacity, t->sweep_path);
 }
 
 srm_status srm_get_tuning(srm_rve *h, srm_tuning *t)
@@ -1088,6 +1117,7 @@ srm_status srm_get_tuning(srm_rve *h, srm_tuning *t)
     *t = srm_tuning{};
     t->sweep_blocks_per_sm = h->g.sweep_bps;
     t->stage_capacity = h->g.cap;
+    t->sweep_path = h->g.sweep_path;
     return SRM_OK;
 }
 

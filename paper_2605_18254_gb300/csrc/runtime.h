@@ -64,6 +64,8 @@ struct Group {
     bool f32 = false;
     int cap = 64;
     int sweep_bps = 0;  // blocks per SM of the sweep grid (0: all that fit)
+    int sweep_path = 1;  // FP32 sweep variant: 1 general path only, 2 with the staged path
+    int stencil_est = 0;  // largest whole-stencil estimate of the members (the check's kernel choice)
     BatchDev *d = nullptr;
     BatchShape sh{};
     cudaStream_t stream = nullptr;      // the caller's stream: all work runs here
@@ -115,7 +117,9 @@ srm_status run_group(Group &g, int64_t max_iters);
 void launch_set_cap(Group &g, size_t r, int64_t cap);
 bool idle_mode(int32_t m);
 srm_status member_idle(Group &g, size_t r);
-srm_status group_set_tuning(Group &g, int sweep_bps, int cap);
+srm_status group_set_tuning(Group &g, int sweep_bps, int cap, int path);
+int default_sweep_path(bool f32, int cap);
+int default_capacity(int estimate, bool f32);
 srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best);
 srm_status member_certify(Group &g, size_t r, int64_t *overlap_pairs, double *min_gap, double *phi);
 srm_status member_positions(Group &g, size_t r, double *xyz, double *radii);

@@ -26,6 +26,8 @@ struct BatchShape {
     bool has2d;         // some RVE is (or a slot may hold) a 2D RVE
     int cap;            // candidates a sweep warp stages in shared memory
     int sweep_bps;      // blocks per SM of the persistent sweep grid (0: all that fit)
+    bool staged;        // FP32 sweep: the variant with the staged path
+    bool check_cells;   // check: a warp per cell (dense stencils) instead of a thread per particle
 };
 
 void launch_begin(const BatchShape &b, cudaStream_t s);
@@ -40,7 +42,7 @@ void launch_sweep(const BatchShape &b, cudaStream_t s);
 int sweep_launches(const BatchShape &b);
 void sweep_configure();
 int sweep_cap_max(bool f32);
-int sweep_blocks_per_sm(bool f32, int cap);  // resident sweep blocks per SM (3D kernel)
+int sweep_blocks_per_sm(bool f32, int cap, bool staged);  // resident sweep blocks per SM (3D kernel)
 int check_cap_max(bool f32);
 void launch_check(const BatchShape &b, cudaStream_t s);
 void check_configure();

@@ -227,14 +227,45 @@ def test_fp32_sweep_within_tolerance(seed, dim):
     assert frac > 0.99
 
 
-@pytest.mark.parametrize("lam,sweeps,tuning", [(1.0, 1, None), (1.08, 2, None), (1.08, 2, (1, 64))])
+@pytest.mark.parametrize("lam,sweeps,tuning", [(1.0, 1, None), (1.08, 2, None), (1.08, 2, (0, 0, 1)),
+                                               (1.08, 2, (1, 64))])
 def test_fp32_sweep_polydisperse_clustered(lam, sweeps, tuning):
     # log-normal radii and a clustered start: dense cluster cores give cells
     # with many particles and staged candidate lists of several 32-wide chunks;
-    # a staging capacity of 64 sends the cells to the general path
+    # the default kernel there has the staged path, (0, 0, 1) selects the one
+    # with the general path only, and a staging capacity of 64 sends the
+    # cells to the general path (overflowing its staging)
     w = srm_inputs.poly_1m(n=20000)
     frac, _, _ = fp32_sweep_check(w, lam, w.c_m, sweeps=sweeps, tuning=tuning)
     assert frac > 0.99
+
+
+@pytest.mark.parametrize("maker", [lambda: srm_inputs.poly_1m(n=20000), lambda: small_3d(3000, 0.45),
+                                   lambda: srm_inputs.disks_1k()])
+def test_fp32_sweep_kernels_agree_bit_for_bit(maker):
+    """The two FP32 sweep kernels (general path only; with the staged path)
+    and an overflowing staging capacity evaluate the same binary32
+    operations on the same candidates: iterations agree bit for bit."""
+    w = maker()
+    runs = []
+    for tuning in ((0, 0, 1), (0, 0, 2), (1, 64, 2)):
+        g, _ = pair(w, precision=32)
+        g.set_tuning(*tuning)
+        assert g.tuning()["sweep_path"] == tuning[2]
+        infos = [g.step() for _ in range(5)]
+        runs.append((g.positions()[0], [(i["result"], i["k_sweeps"]) for i in infos], g.state()["sweep"]))
+        g.close()
+    for x, it, sw in runs[1:]:
+        np.testing.assert_array_equal(x, runs[0][0])
+        assert it == runs[0][1] and sw == runs[0][2]
+
+
+def test_fp64_has_no_staged_sweep_kernel():
+    g, _ = pair(small_3d(500, 0.3))
+    assert g.tuning()["sweep_path"] == 1
+    with pytest.raises(srm.SrmError):
+        g.set_tuning(0, 0, 2)
+    g.close()
 
 
 @pytest.mark.parametrize("capacity", [0, 64])

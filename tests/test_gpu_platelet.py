@@ -65,13 +65,13 @@ def small_workload(n, seed, aspect=20.0, rho_t=3.0, **kw):
     return srm_inputs.platelets(seed=seed, n=n, aspect=aspect, rho_t=rho_t, **kw)
 
 
-def both(w, lam0=None, lam_t=1.0, **kw):
+def both(w, lam0=None, lam_t=1.0, gpu_kw=None, **kw):
     """The GPU handle and the reference on the kernel specification's
     contact predicate, on the same start."""
     lam0 = w.lambda0 if lam0 is None else lam0
     args = dict(c_w=w.c_w, c_m=w.c_m, c_r=w.c_r)
     args.update(kw)
-    g = srm.Platelets(w.box, w.x, w.u, w.a0, w.t0, lam0, lam_t, w.seed, **args)
+    g = srm.Platelets(w.box, w.x, w.u, w.a0, w.t0, lam0, lam_t, w.seed, **args, **(gpu_kw or {}))
     o = oracle.PlateletSystem(w.box, w.x, w.u, w.a0, w.t0, lam=lam0, lam_t=lam_t, seed=w.seed,
                               contact=spec.address(), **args)
     return g, o
@@ -105,12 +105,14 @@ def assert_same_state(g, o):
     assert info["sweep"] == o.sweep_counter
 
 
-@pytest.mark.parametrize("c_r", [0.0, 0.05])
-def test_sweeps_bit_exact(c_r):
+@pytest.mark.parametrize("c_r,kernel", [(0.0, 0), (0.05, 0), (0.05, 1)])
+def test_sweeps_bit_exact(c_r, kernel):
+    """Kernel 0: a block per cell with the 27 cells around it in shared
+    memory (this grid qualifies); kernel 1: a warp per cell."""
     w = small_workload(3000, 11)
     # sweeps at 2.5 times the starting size, where neighbours interact
     lam = 2.5 * w.lambda0
-    g, o = both(w, lam0=lam, c_m=0.05 * w.extra["D"], c_r=c_r)
+    g, o = both(w, lam0=lam, c_m=0.05 * w.extra["D"], c_r=c_r, gpu_kw=dict(sweep_kernel=kernel))
     a, t = lam * w.a0, lam * w.t0
     for _ in range(3):
         x0, u0, _ = g.state()
@@ -118,6 +120,39 @@ def test_sweeps_bit_exact(c_r):
         assert_same_state(g, o)
         x1, u1, _ = g.state()
         assert assert_sweep_one_sided(w.box, x0, u0, x1, u1, a, t) > 50
+    st = g.sweep_stats()
+    assert (st["staged_sweeps"], st["warp_sweeps"]) == ((3, 0) if kernel == 0 else (0, 3))
+    assert st["unstaged_cells"] == 0
+    g.close()
+
+
+def test_staged_sweep_overflow_matches_warp_kernel():
+    """A cluster of 1500 overlapping platelets inside a few cells: the 27
+    cells around those cells hold more than the 1024 platelets the block
+    kernel stages, so it moves them from global memory; both kernels end
+    bit for bit alike, and equal the reference on one sweep."""
+    rng = np.random.default_rng(21)
+    n_bg, n_cl = 1500, 1500
+    # cells of width 1/18: the 27 cells around the cluster's centre hold it all
+    x = np.concatenate([rng.uniform(0, 1, (n_bg, 3)), 0.5 + rng.uniform(-0.05, 0.05, (n_cl, 3))])
+    u = rand_units(rng, n_bg + n_cl)
+    a0, t0, c_m = 0.02, 0.0005, 0.004
+    runs = []
+    for kernel in (0, 1):
+        g = srm.Platelets((1, 1, 1), x, u, a0, t0, 1.0, 1.0, 5, c_m=c_m, c_r=0.05, sweep_kernel=kernel)
+        moved = g.sweeps(2)
+        xs, us, _ = g.state()
+        runs.append((xs, us, moved, g.sweep_stats()))
+        g.close()
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2] > 0
+    assert runs[0][3]["staged_sweeps"] == 2 and runs[0][3]["unstaged_cells"] > 0
+    assert runs[1][3]["warp_sweeps"] == 2
+    g = srm.Platelets((1, 1, 1), x, u, a0, t0, 1.0, 1.0, 5, c_m=c_m, c_r=0.05)
+    o = oracle.PlateletSystem((1, 1, 1), x, u, a0, t0, c_m=c_m, c_r=0.05, seed=5, contact=spec.address())
+    assert g.sweeps(1) == o.sweep()
+    assert_same_state(g, o)
     g.close()
 
 
@@ -175,14 +210,17 @@ def test_check_flags_bit_exact():
     g.close()
 
 
-def test_three_cells_per_axis_and_single_platelet():
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_three_cells_per_axis_and_single_platelet(kernel):
     w = small_workload(60, 15, aspect=10.0, rho_t=1.0)
     c_m = 0.05 * w.extra["D"]
-    g, o = both(w, lam0=1.0, c_m=c_m, c_r=0.1)
+    g, o = both(w, lam0=1.0, c_m=c_m, c_r=0.1, gpu_kw=dict(sweep_kernel=kernel))
     assert list(oracle.grid(3, w.box, 1.0, w.a0 + w.t0, c_m)[0]) == [3, 3, 3]
     for _ in range(2):
         assert g.sweeps(1) == o.sweep()
     assert_same_state(g, o)
+    if kernel == 0:
+        assert g.sweep_stats()["staged_sweeps"] == 2
     g.close()
     x = np.array([[0.5, 0.999, 0.001]])
     u = np.array([[0.0, 0.6, 0.8]])
