@@ -266,7 +266,8 @@ typedef struct srm_tuning {
 /* Autotuner: runs the RVE (or batch) for `supersteps` super-steps (>= 1,
  * rounded up to whole recorded graphs of 8) with each candidate shape --
  * blocks per SM from 2 to the resident maximum, staging capacity at the
- * current value, half and twice, both FP32 sweep paths -- in two
+ * current value and twice (never below: stencils grow as the particles
+ * swell), both FP32 sweep paths -- in two
  * interleaved rounds, scores each
  * by device time per particle sweep (CUDA events) and keeps the fastest.
  * The super-steps are real work: the RVEs advance (and may finish).  *best

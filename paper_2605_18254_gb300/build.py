@@ -29,9 +29,11 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
 # add separately (they reproduce the reference bit for bit without explicit
 # rounding intrinsics)
 NO_FMAD = {"platelet.cu"}
-# tuning knob: blocks per SM the sweep kernel's register allocation must allow
-if os.environ.get("SRM_SWEEP_MIN_BLOCKS"):
-    NVCC_FLAGS += [f"-DSRM_SWEEP_MIN_BLOCKS={int(os.environ['SRM_SWEEP_MIN_BLOCKS'])}"]
+# tuning knobs: blocks per SM the register allocation of the sweep kernels
+# (staged, general) must allow
+for _k in ("SRM_SWEEP_MIN_BLOCKS", "SRM_SWEEP_MIN_BLOCKS_GENERAL"):
+    if os.environ.get(_k):
+        NVCC_FLAGS += [f"-D{_k}={int(os.environ[_k])}"]
 
 
 def _nvcc() -> str:
