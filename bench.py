@@ -404,7 +404,12 @@ def run_ours(args, rank, world, local_rank):
     states.append((f"phi={st['phi']:.3f}", g.positions()[0], st["lambda"]))
     tm = g.timings()
     st1 = g.state()
+    tun = g.tuning()
     g.close()
+    f32 = int(args.precision == 32)
+    staged = int(tun["sweep_path"] == 2)
+    kname = {"sweep": f"k_draw + k_sweep_df<{w.dim},{f32},{staged}> ({'staged' if staged else 'general'} path)",
+             "check": f"{'k_check_cells' if st1['check_kernel'] else 'k_check'}<{f32}>"}
     # the check's floor: the first iterations, where almost every particle
     # moves and the check only reads the moved flags
     g = new_rve()
@@ -433,7 +438,7 @@ def run_ours(args, rank, world, local_rank):
         peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e12
         if args.precision == 64:
             peak = peak / 64.0
-        roof = {"kernel": f"k_{dom}{args.precision}<{w.dim}>", "bound": "alu", "achieved": achieved,
+        roof = {"kernel": kname[dom], "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": committed_traffic(f"k_{dom}{args.precision}"),
                 "per_launch_ms": per_launch[dom],
@@ -464,10 +469,11 @@ def run_ours(args, rank, world, local_rank):
     ck_ms = per_launch["check"]
     floor_ms = tm0["ms_check"] / max(1, tm0["check_launches"])
     roof["check"] = {
-        "kernel": f"k_check<{args.precision == 32}>", "bound": "hbm", "per_launch_ms": ck_ms,
+        "kernel": kname["check"], "bound": "hbm", "per_launch_ms": ck_ms,
         "bytes_per_launch": cb * w.n, "achieved": cb * w.n / (ck_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
         "unit": "GB/s", "frac": cb * w.n / (ck_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
         "floor_ms": floor_ms, "floor_frac": cb * w.n / (floor_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+        "traffic": committed_traffic(f"k_check{args.precision}"),
         "launches": tm["check_launches"],
         "note": ("per_launch_ms over the whole generation; floor_ms over the checks of the first 3 iterations, "
                  "where almost every particle moved and the check only reads flags (launch and read floor); "

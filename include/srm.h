@@ -232,7 +232,8 @@ typedef struct srm_state_info {
     uint64_t pairs_check;       /* candidate pairs tested by the checks (Alg 6)      */
     uint64_t stage_overflow;    /* sweep cells whose candidates exceeded the staging */
     int32_t stage_capacity;     /* candidates a sweep warp stages in shared memory   */
-    int32_t reserved0;
+    int32_t check_kernel;       /* Alg 6 kernel: 0 a thread per particle, 1 a warp per
+                                   cell (whole-stencil estimate above 256)          */
     uint64_t trials;            /* trial moves evaluated by the sweeps (Alg 3)       */
     uint64_t pairs_alg5;        /* pairs Alg 5 examines for those trials: for each,
                                    the particles of the 3^d cells around the home
@@ -267,7 +268,7 @@ typedef struct srm_tuning {
  * rounded up to whole recorded graphs of 8) with each candidate shape --
  * blocks per SM from 2 to the resident maximum, staging capacity at the
  * current value and twice (never below: stencils grow as the particles
- * swell), both FP32 sweep paths -- in two
+ * swell); the sweep kernel (sweep_path) stays as set -- in two
  * interleaved rounds, scores each
  * by device time per particle sweep (CUDA events) and keeps the fastest.
  * The super-steps are real work: the RVEs advance (and may finish).  *best
@@ -401,11 +402,11 @@ void srm_batch_destroy(srm_batch *b);
  * thread when the call starts is reported (SRM_E_CUDA) and left pending.
  *
  * The first call on a device looks up the device address of the static
- * array (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array, whose
- * contents are whatever the last call left (each call clears what it needs
- * zeroed): calls that overlap on the GPU -- from two threads, or on two
- * streams without ordering between them -- race and give wrong results. */
+ * array (cudaGetSymbolAddress) with that device current.  All calls share
+ * the one array, whose contents are whatever the last call left (each call
+ * clears what it needs zeroed): calls that overlap on the GPU -- from two
+ * threads, or on two streams without ordering between them -- race and give
+ * wrong results. */
 #define SRM_NOALLOC_MAX_PARTICLES 32768
 #define SRM_NOALLOC_MAX_CELLS 65536
 srm_status srm_certify_noalloc(int32_t dim, const double box[3], int64_t n, const double *xyz,

@@ -84,7 +84,7 @@ class srm_state_info(Structure):
                 ("shaken", c_int64), ("sweeps", c_int64), ("done", c_int32),
                 ("grid", c_int32 * 3), ("kernel_launches", c_int64), ("pairs_sweep", c_uint64),
                 ("pairs_check", c_uint64), ("stage_overflow", c_uint64), ("stage_capacity", c_int32),
-                ("reserved0", c_int32), ("trials", c_uint64), ("pairs_alg5", c_uint64),
+                ("check_kernel", c_int32), ("trials", c_uint64), ("pairs_alg5", c_uint64),
                 ("near_fallback", c_uint64)]
 
 

@@ -554,8 +554,11 @@ srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best)
     struct Cand {
         int bps, cap, path;
     };
+    // the sweep kernel stays the current one: measured early in a run (the
+    // only place the tuner can), the staged kernel looked faster on the
+    // ensemble of small RVEs and was 25% slower over the whole run
     std::vector<Cand> cand;
-    for (int path = 1; path <= (g.f32 ? 2 : 1); path++)
+    for (int path = g.sweep_path; path <= g.sweep_path; path++)
         for (int c : caps) {
             const int mx = srm::sweep_blocks_per_sm(g.f32, c, path == 2);
             for (int b = 2; b < mx; b++) cand.push_back({b, c, path});
@@ -841,6 +844,7 @@ void fill_state(const Group &g, size_t r, srm_state_info *o)
     o->pairs_alg5 = s.pairs_alg5;
     o->near_fallback = s.near_fallback;
     o->stage_capacity = g.cap;
+    o->check_kernel = g.sh.check_cells ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
