@@ -46,7 +46,7 @@ srm_status srm_batch_create(srm_batch **out, const srm_job *jobs, int32_t n_jobs
     int cap = 64;
     for (const Prep &q : qs) cap = std::max(cap, q.cap_est);
     g.cap = default_capacity(cap, g.f32);
-    g.sweep_path = default_sweep_path(g.f32, g.cap);
+    g.sweep_path = DEFAULT_SWEEP_PATH;
     g.stencil_est = cap;
     srm_status st = SRM_OK;
     for (int32_t i = 0; i < n_jobs && st == SRM_OK; i++) {
@@ -81,7 +81,7 @@ srm_status srm_batch_create_slots(srm_batch **out, int32_t n_slots, int64_t max_
     g.f32 = precision == SRM_PREC_F32;
     const int cap = stage_capacity > 0 ? stage_capacity : 256;
     g.cap = std::max(64, std::min((cap + 31) / 32 * 32, srm::sweep_cap_max(g.f32)));
-    g.sweep_path = default_sweep_path(g.f32, g.cap);
+    g.sweep_path = DEFAULT_SWEEP_PATH;
     srm_status st = SRM_OK;
     for (int32_t i = 0; i < n_slots && st == SRM_OK; i++) {
         Member *mb = new Member();

@@ -50,8 +50,7 @@ namespace srm {
 constexpr int NEAR_CAP = 64;
 constexpr int PRE_NH = 32;    // home particles whose first trials are copied up front
 constexpr int PRE_TRIALS = 2; // trials drawn ahead of the sweep per particle
-constexpr int NL_CAP = 256;   // staged path: entries of a particle's near index list (in the hap area)
-static_assert(NL_CAP * 2 <= 32 * 16, "the near index list lives in the 32 x float4 hap area");
+constexpr int NL_CAP = 256;   // staged path: entries of a particle's near index list
 
 template <bool F32>
 struct SweepSmem {
@@ -65,14 +64,14 @@ struct SweepSmem {
                 (size_t)NEAR_CAP * sizeof(PT) + (size_t)PRE_NH * PRE_TRIALS * sizeof(PT) + 31) /
                32 * 32;
     }
-    // staged path: stencil, every candidate, near bits (one word per
-    // 32-candidate chunk and home particle of a group), stencil cell of each
-    // candidate, binary32 copies of a group's home particles, the pre-tests
-    // of trials 0 and 1 of a group's particles, pre-drawn directions
+    // staged path (FP32 form): stencil, every candidate, near bits (one word
+    // per 32-candidate chunk and home particle of a group), stencil cell of
+    // each candidate, a particle's near index list, the pre-tests of trials
+    // 0 and 1 of a group's particles, pre-drawn directions
     static __host__ __device__ constexpr size_t off_bits(int cap) { return ST_HDR + (size_t)cap * sizeof(PT); }
     static __host__ __device__ constexpr size_t off_cid(int cap) { return off_bits(cap) + (size_t)cap * 4; }
-    static __host__ __device__ constexpr size_t off_hap(int cap) { return (off_cid(cap) + (size_t)cap + 15) / 16 * 16; }
-    static __host__ __device__ constexpr size_t off_shit(int cap) { return off_hap(cap) + 32 * sizeof(float4); }
+    static __host__ __device__ constexpr size_t off_nl(int cap) { return (off_cid(cap) + (size_t)cap + 15) / 16 * 16; }
+    static __host__ __device__ constexpr size_t off_shit(int cap) { return off_nl(cap) + NL_CAP * sizeof(uint16_t); }
     static __host__ __device__ constexpr size_t off_pre(int cap) { return (off_shit(cap) + 32 + 31) / 32 * 32; }
     static __host__ __device__ constexpr size_t bytes_staged(int cap)
     {
@@ -591,8 +590,8 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
 }
 
 // ---------------------------------------------------------------------------
-// The staged path of one cell: every candidate of the stencil is copied to
-// shared memory (cp.async, 16 bytes per copy), so that the cell's service
+// The staged path of one cell (FP32 form): every candidate of the stencil is
+// copied to shared memory (cp.async, 16 bytes per copy), so that the cell's service
 // time -- which lies on the chain of the colour order -- holds one memory
 // round trip instead of a load per chunk, and the work that does not
 // depend on lower-colour cells is done before waiting for them:
@@ -620,21 +619,19 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
 // general path, so the results are the same.  Returns false, having issued
 // nothing, when the two lists do not fit cap candidates.
 // ---------------------------------------------------------------------------
-template <int DIM, bool F32>
+template <int DIM>
 __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, unsigned char *base, int cap,
                                                   CellCount &cc)
 {
-    if constexpr (!F32) return false;  // the FP64 sweep has no staged variant
-    using SM = SweepSmem<F32>;
-    using PT = typename SM::PT;
-    using DT = typename SM::DT;
-    constexpr int PIECES = (int)(sizeof(PT) / 16);
+    using SM = SweepSmem<true>;
+    using PT = float4;
     const int lane = threadIdx.x & 31;
     StencilSmem &S = *reinterpret_cast<StencilSmem *>(base);
     PT *cpos = reinterpret_cast<PT *>(base + ST_HDR);
     uint32_t *wbits = reinterpret_cast<uint32_t *>(base + SM::off_bits(cap));
     uint8_t *cid = base + SM::off_cid(cap);
-    float4 *hap = reinterpret_cast<float4 *>(base + SM::off_hap(cap));
+    // a particle's near list, as candidate indices
+    uint16_t *nlist = reinterpret_cast<uint16_t *>(base + SM::off_nl(cap));
     uint32_t *shit = reinterpret_cast<uint32_t *>(base + SM::off_shit(cap));
     PT *pre = reinterpret_cast<PT *>(base + SM::off_pre(cap));
     uint8_t *const flags = st->flags;
@@ -645,8 +642,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     const int s0 = st->sub[0], s1 = st->sub[1];
     const float w[3] = {(float)st->gw[0], (float)st->gw[1], (float)st->gw[2]};
     const uint64_t seed = st->seed, sweep = st->sweep;
-    const double c_m = st->c_m;
-    const float cmf = (float)c_m;
+    const float cmf = (float)st->c_m;
     const float g1 = 1.0f + st->guard;
     const int N_l = st->N_l;
 
@@ -666,7 +662,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     const uint32_t npre = nh < (uint32_t)PRE_NH ? nh : (uint32_t)PRE_NH;
     {
         const PT *src = reinterpret_cast<const PT *>(st->dirs) + 2 * (size_t)hb;
-        for (uint32_t e = lane; e < npre * PRE_TRIALS * PIECES; e += 32)
+        for (uint32_t e = lane; e < npre * PRE_TRIALS; e += 32)
             cp_async16(reinterpret_cast<unsigned char *>(pre) + 16 * (size_t)e,
                        reinterpret_cast<const unsigned char *>(src) + 16 * (size_t)e);
     }
@@ -677,7 +673,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
         const uint32_t nj = S.n[j], o = list0 + S.o[j];
         const unsigned char *src = reinterpret_cast<const unsigned char *>(pos + S.b[j]);
         unsigned char *dst = reinterpret_cast<unsigned char *>(cpos + o);
-        for (uint32_t e = 0; e < nj * PIECES; e++) cp_async16(dst + 16 * (size_t)e, src + 16 * (size_t)e);
+        for (uint32_t e = 0; e < nj; e++) cp_async16(dst + 16 * (size_t)e, src + 16 * (size_t)e);
         for (uint32_t e = 0; e < nj; e++) cid[o + e] = (uint8_t)j;
     };
     for (int j = lane; j < nst; j += 32)
@@ -685,31 +681,13 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     cp_async_wait();
     __syncwarp();
 
-    // FP64 form: binary32 copies relative to the home corner, for the culls
-    const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
-    auto approx = [&](const PT &c) -> float4 {
-        if constexpr (F32) {
-            return c;
-        } else {
-            double ex = c.x - ox, ey = c.y - oy, ez = DIM == 3 ? c.z - oz : 0.0;
-            if (ex > st->halfL[0]) ex -= st->L[0];
-            if (ex < -st->halfL[0]) ex += st->L[0];
-            if (ey > st->halfL[1]) ey -= st->L[1];
-            if (ey < -st->halfL[1]) ey += st->L[1];
-            if (DIM == 3) {
-                if (ez > st->halfL[2]) ez -= st->L[2];
-                if (ez < -st->halfL[2]) ez += st->L[2];
-            }
-            return make_float4((float)ex, (float)ey, (float)ez, (float)c.w);
-        }
-    };
     // largest home radius
     float rh = 0.f;
     for (uint32_t m = lane; m < nh; m += 32) rh = fmaxf(rh, (float)cpos[m].w);
     for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
-    // FP32 form: shift into the home cell's frame; both forms: keep the
-    // candidates of [src, src + n) that can reach the home cell (the cull of
-    // the general path), compacted to dst <= src -- a chunk's entries are
+    // shift into the home cell's frame and keep the candidates of
+    // [src, src + n) that can reach the home cell (the cull of the general
+    // path), compacted to dst <= src -- a chunk's entries are
     // read before any is written, and writes land at or below the chunk's
     // first index.  The home particles (indices below nh of the first list)
     // are all kept, at their own index.
@@ -721,15 +699,12 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
             PT c;
             if (k0 + lane < n) {
                 c = cpos[k];
-                if constexpr (F32) {
-                    const int j = cid[k];
-                    c.x = __fmaf_rn((float)S.sh[j][0], w[0], c.x);
-                    c.y = __fmaf_rn((float)S.sh[j][1], w[1], c.y);
-                    c.z = __fmaf_rn((float)S.sh[j][2], w[2], c.z);
-                }
-                const float4 ca = approx(c);
-                const float r = rh + ca.w + 2.f * cmf;
-                keep = (src == 0 && k < nh) || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+                const int j = cid[k];
+                c.x = __fmaf_rn((float)S.sh[j][0], w[0], c.x);
+                c.y = __fmaf_rn((float)S.sh[j][1], w[1], c.y);
+                c.z = __fmaf_rn((float)S.sh[j][2], w[2], c.z);
+                const float r = rh + c.w + 2.f * cmf;
+                keep = (src == 0 && k < nh) || box_dist2(c, w, DIM) <= r * r * 1.0004f;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
@@ -743,10 +718,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     const uint32_t Tkn = cull(0, Tn, 0);
     const uint32_t Tkp = (Tkn + 31) / 32 * 32;
     if (Tkn + lane < Tkp) {
-        PT far;
-        far.x = far.y = far.z = (DT)1e30;
-        far.w = (DT)0;
-        cpos[Tkn + lane] = far;
+        cpos[Tkn + lane] = make_float4(1e30f, 1e30f, 1e30f, 0.0f);
     }
     // positions of trials 0 and 1 of the first home particles, in place of
     // their directions
@@ -755,39 +727,24 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
         if ((int)(pi & 1) >= N_l) continue;
         const PT p = cpos[m];
         const PT e = pre[pi];
-        PT q;
-        if constexpr (F32) {
-            q.x = trial_f32(p.x, cmf, e.x);
-            q.y = trial_f32(p.y, cmf, e.y);
-            q.z = DIM == 3 ? trial_f32(p.z, cmf, e.z) : p.z;
-        } else {
-            q.x = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, e.x)), st->L[0]);
-            q.y = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, e.y)), st->L[1]);
-            q.z = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, e.z)), st->L[2]) : p.z;
-        }
-        q.w = (DT)0;
-        pre[pi] = q;
+        pre[pi] = make_float4(trial_f32(p.x, cmf, e.x), trial_f32(p.y, cmf, e.y),
+                              DIM == 3 ? trial_f32(p.z, cmf, e.z) : p.z, 0.0f);
     }
     __syncwarp();
     // near bits of home particles g0 .. g0+gn-1 over chunks [c0, c1)
     auto mark = [&](uint32_t g0, uint32_t gn, uint32_t c0, uint32_t c1, uint32_t Tk) {
-        if constexpr (!F32) {
-            if ((uint32_t)lane < gn) hap[lane] = approx(cpos[g0 + lane]);
-            __syncwarp();
-        }
         for (uint32_t ch = c0; ch < c1; ch++) {
             const uint32_t k = ch * 32 + (uint32_t)lane;
             uint32_t bits = 0;
             if (k < Tk) {
-                const float4 ca = approx(cpos[k]);
+                const float4 ca = cpos[k];
                 const float base_r = ca.w + cmf + (k < nh ? cmf : 0.f);
                 for (uint32_t mm = 0; mm < gn; mm += 4) {
                     float4 pm[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         const uint32_t hq = mm + q < gn ? mm + q : gn - 1;
-                        if constexpr (F32) pm[q] = cpos[g0 + hq];
-                        else pm[q] = hap[hq];
+                        pm[q] = cpos[g0 + hq];
                     }
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
@@ -812,11 +769,9 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
             const uint32_t mm = pi >> 1;
             bool hit = false;
             if (pi < 2 * npre && (int)(pi & 1) < N_l) {
-                const float Rm = (float)cpos[mm].w;
-                const double Rd = (double)cpos[mm].w;
+                const float Rm = cpos[mm].w;
                 const PT qq = pre[pi];
-                const float qf[3] = {(float)qq.x, (float)qq.y, (float)qq.z};
-                const double qd[3] = {(double)qq.x, (double)qq.y, (double)qq.z};
+                const float qf[3] = {qq.x, qq.y, qq.z};
                 for (uint32_t ch = c0; ch < c1 && !hit; ch++) {
                     uint32_t wd = wbits[ch * 32 + mm];
                     // drop the home candidates (indices below nh)
@@ -826,8 +781,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                         wd &= wd - 1;
                         const PT c = cpos[ch * 32 + bt];
                         cc.examined++;
-                        if constexpr (F32) hit = hit_f32<DIM>(qf, Rm, c, g1);
-                        else hit = collide64<DIM>(st->images, qd, Rd, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                        hit = hit_f32<DIM>(qf, Rm, c, g1);
                     }
                 }
             }
@@ -885,9 +839,6 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
     // chunk c
     const int tpar = nchunks <= 4 ? 8 : (nchunks <= 8 ? 4 : (nchunks <= 16 ? 2 : 1));
     const int G = 32 / tpar, tsub = lane / G, csub = lane % G;
-    // a particle's near list, as candidate indices (the binary32 copies of
-    // the FP64 form's home particles are no longer needed here)
-    uint16_t *nlist = reinterpret_cast<uint16_t *>(hap);
     // the word of chunk `lane` of home particle mm of the current group
     auto word_all = [&](uint32_t mm) -> uint32_t {
         return (uint32_t)lane < nchunks ? wbits[lane * 32 + mm] : 0u;
@@ -921,22 +872,15 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                 if ((hw >> lane) & 1u) {
                     const PT c = cpos[lane];
                     cc.examined += lmax;
-                    if constexpr (F32) {
-                        const float a0[3] = {q0.x, q0.y, q0.z}, a1[3] = {q1.x, q1.y, q1.z};
-                        h0 = hit_f32<DIM>(a0, p.w, c, g1);
-                        h1 = lmax > 1 && hit_f32<DIM>(a1, p.w, c, g1);
-                    } else {
-                        const double a0[3] = {q0.x, q0.y, q0.z}, a1[3] = {q1.x, q1.y, q1.z};
-                        h0 = collide64<DIM>(st->images, a0, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
-                        h1 = lmax > 1 && collide64<DIM>(st->images, a1, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
-                    }
+                    const float a0[3] = {q0.x, q0.y, q0.z}, a1[3] = {q1.x, q1.y, q1.z};
+                    h0 = hit_f32<DIM>(a0, p.w, c, g1);
+                    h1 = lmax > 1 && hit_f32<DIM>(a1, p.w, c, g1);
                 }
                 const bool f0 = (sb & 1u) || __any_sync(0xffffffffu, h0);
                 const bool f1 = lmax < 2 || (sb & 2u) || __any_sync(0xffffffffu, h1);
                 if (!f0 || !f1) {
                     const PT qa = !f0 ? q0 : q1;
-                    if constexpr (F32) np = make_float4(qa.x, qa.y, qa.z, p.w);
-                    else np = make_double4_32a(qa.x, qa.y, qa.z, p.w);
+                    np = make_float4(qa.x, qa.y, qa.z, p.w);
                     done = true;
                     cc.trials += !f0 ? 1 : 2;
                 } else {
@@ -948,20 +892,13 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                 // trial t and walks the marked home candidates
                 const int lmax = N_l < PRE_TRIALS ? N_l : PRE_TRIALS;
                 const uint32_t sb = (shit[(2 * (m - g0)) >> 5] >> ((2 * (m - g0)) & 31)) & 3u;
-                double qt[3] = {0.0, 0.0, 0.0};
                 float qs[3] = {0.f, 0.f, 0.f};
                 bool hit = false;
                 if (lane < lmax) {
                     const PT e = pre[PRE_TRIALS * m + lane];  // the trial position
-                    if constexpr (F32) {
-                        qs[0] = e.x;
-                        qs[1] = e.y;
-                        qs[2] = e.z;
-                    } else {
-                        qt[0] = e.x;
-                        qt[1] = e.y;
-                        qt[2] = e.z;
-                    }
+                    qs[0] = e.x;
+                    qs[1] = e.y;
+                    qs[2] = e.z;
                     hit = (sb >> lane) & 1u;
                     for (uint32_t ch = 0; ch * 32 < nh && !hit; ch++) {
                         uint32_t wd = wbits[ch * 32 + (m - g0)];
@@ -972,21 +909,15 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                             wd &= wd - 1;
                             const PT c = cpos[ch * 32 + bt];
                             cc.examined++;
-                            if constexpr (F32) hit = hit_f32<DIM>(qs, p.w, c, g1);
-                            else hit = collide64<DIM>(st->images, qt, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                            hit = hit_f32<DIM>(qs, p.w, c, g1);
                         }
                     }
                 }
                 const unsigned clean = ~__ballot_sync(0xffffffffu, hit) & ((1u << lmax) - 1u);
                 if (clean) {
                     const int sl = __ffs(clean) - 1;
-                    if constexpr (F32) {
-                        np = make_float4(__shfl_sync(0xffffffffu, qs[0], sl), __shfl_sync(0xffffffffu, qs[1], sl),
-                                         __shfl_sync(0xffffffffu, qs[2], sl), p.w);
-                    } else {
-                        np = make_double4_32a(__shfl_sync(0xffffffffu, qt[0], sl), __shfl_sync(0xffffffffu, qt[1], sl),
-                                              __shfl_sync(0xffffffffu, qt[2], sl), p.w);
-                    }
+                    np = make_float4(__shfl_sync(0xffffffffu, qs[0], sl), __shfl_sync(0xffffffffu, qs[1], sl),
+                                     __shfl_sync(0xffffffffu, qs[2], sl), p.w);
                     done = true;
                     cc.trials += sl + 1;
                 } else {
@@ -1021,44 +952,27 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
             while (!done && l0 < N_l) {
                 // later trials eight at a time, drawn by the lanes
                 const int lmax = N_l - l0 < 8 ? N_l - l0 : 8;
-                double qt[3] = {0.0, 0.0, 0.0};
                 float qs[3] = {0.f, 0.f, 0.f};
-                DT u[3] = {(DT)0, (DT)0, (DT)0};
-                draw8<DIM, F32>(seed, sweep, (uint64_t)pid_m, l0, u);
+                float u[3] = {0.f, 0.f, 0.f};
+                draw8<DIM, true>(seed, sweep, (uint64_t)pid_m, l0, u);
                 if (lane < lmax) {
-                    if constexpr (F32) {
-                        qs[0] = trial_f32(p.x, cmf, u[0]);
-                        qs[1] = trial_f32(p.y, cmf, u[1]);
-                        qs[2] = DIM == 3 ? trial_f32(p.z, cmf, u[2]) : p.z;
-                    } else {
-                        qt[0] = wrap_d(__dadd_rn(p.x, __dmul_rn(c_m, u[0])), st->L[0]);
-                        qt[1] = wrap_d(__dadd_rn(p.y, __dmul_rn(c_m, u[1])), st->L[1]);
-                        qt[2] = DIM == 3 ? wrap_d(__dadd_rn(p.z, __dmul_rn(c_m, u[2])), st->L[2]) : p.z;
-                    }
+                    qs[0] = trial_f32(p.x, cmf, u[0]);
+                    qs[1] = trial_f32(p.y, cmf, u[1]);
+                    qs[2] = DIM == 3 ? trial_f32(p.z, cmf, u[2]) : p.z;
                 }
                 l0 += lmax;
                 if (nn <= (uint32_t)NL_CAP) {
                     // lane (t, j): trial t = lane / 4 against entries j, j + 4, ...
                     const int tr = lane >> 2, j0 = lane & 3;
                     const int src = tr < lmax ? tr : 0;
-                    double q[3] = {0.0, 0.0, 0.0};
-                    float qf[3] = {0.f, 0.f, 0.f};
-                    if constexpr (F32) {
-                        qf[0] = __shfl_sync(0xffffffffu, qs[0], src);
-                        qf[1] = __shfl_sync(0xffffffffu, qs[1], src);
-                        qf[2] = __shfl_sync(0xffffffffu, qs[2], src);
-                    } else {
-                        q[0] = __shfl_sync(0xffffffffu, qt[0], src);
-                        q[1] = __shfl_sync(0xffffffffu, qt[1], src);
-                        q[2] = __shfl_sync(0xffffffffu, qt[2], src);
-                    }
+                    const float qf[3] = {__shfl_sync(0xffffffffu, qs[0], src), __shfl_sync(0xffffffffu, qs[1], src),
+                                         __shfl_sync(0xffffffffu, qs[2], src)};
                     bool hit = false;
                     if (tr < lmax) {
                         for (uint32_t jj = j0; jj < nn && !hit; jj += 4) {
                             const PT c = cpos[nlist[jj]];
                             cc.examined++;
-                            if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
-                            else hit = collide64<DIM>(st->images, q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                            hit = hit_f32<DIM>(qf, p.w, c, g1);
                         }
                     }
                     const unsigned hb_ = __ballot_sync(0xffffffffu, hit);
@@ -1070,14 +984,8 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                         }
                     cc.trials += acc >= 0 ? acc + 1 : lmax;
                     if (acc >= 0) {
-                        if constexpr (F32) {
-                            np = make_float4(__shfl_sync(0xffffffffu, qs[0], acc), __shfl_sync(0xffffffffu, qs[1], acc),
-                                             __shfl_sync(0xffffffffu, qs[2], acc), p.w);
-                        } else {
-                            np = make_double4_32a(__shfl_sync(0xffffffffu, qt[0], acc),
-                                                  __shfl_sync(0xffffffffu, qt[1], acc),
-                                                  __shfl_sync(0xffffffffu, qt[2], acc), p.w);
-                        }
+                        np = make_float4(__shfl_sync(0xffffffffu, qs[0], acc), __shfl_sync(0xffffffffu, qs[1], acc),
+                                         __shfl_sync(0xffffffffu, qs[2], acc), p.w);
                         done = true;
                     }
                     continue;
@@ -1087,17 +995,8 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                 for (int lb = 0; lb < lmax && !done; lb += tpar) {
                     const int tr = lb + tsub;  // this lane's trial (valid if < lmax)
                     const int src = tr < lmax ? tr : 0;
-                    double q[3] = {0.0, 0.0, 0.0};
-                    float qf[3] = {0.f, 0.f, 0.f};
-                    if constexpr (F32) {
-                        qf[0] = __shfl_sync(0xffffffffu, qs[0], src);
-                        qf[1] = __shfl_sync(0xffffffffu, qs[1], src);
-                        qf[2] = __shfl_sync(0xffffffffu, qs[2], src);
-                    } else {
-                        q[0] = __shfl_sync(0xffffffffu, qt[0], src);
-                        q[1] = __shfl_sync(0xffffffffu, qt[1], src);
-                        q[2] = __shfl_sync(0xffffffffu, qt[2], src);
-                    }
+                    const float qf[3] = {__shfl_sync(0xffffffffu, qs[0], src), __shfl_sync(0xffffffffu, qs[1], src),
+                                         __shfl_sync(0xffffffffu, qs[2], src)};
                     bool hit = false;
                     if (tr < lmax) {
                         uint32_t wd = word;
@@ -1106,8 +1005,7 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                             wd &= wd - 1;
                             const PT c = cpos[csub * 32 + bt];
                             cc.examined++;
-                            if constexpr (F32) hit = hit_f32<DIM>(qf, p.w, c, g1);
-                            else hit = collide64<DIM>(st->images, q, p.w, c.x, c.y, c.z, c.w, st->L, st->halfL);
+                            hit = hit_f32<DIM>(qf, p.w, c, g1);
                         }
                     }
                     const unsigned hb_ = __ballot_sync(0xffffffffu, hit);
@@ -1123,14 +1021,8 @@ __device__ __forceinline__ bool sweep_cell_staged(RveDev *st, int chi, int t, un
                     cc.trials += acc >= 0 ? acc + 1 : nr;
                     if (acc >= 0) {
                         const int sl = lb + acc;
-                        if constexpr (F32) {
-                            np = make_float4(__shfl_sync(0xffffffffu, qs[0], sl), __shfl_sync(0xffffffffu, qs[1], sl),
-                                             __shfl_sync(0xffffffffu, qs[2], sl), p.w);
-                        } else {
-                            np = make_double4_32a(__shfl_sync(0xffffffffu, qt[0], sl),
-                                                  __shfl_sync(0xffffffffu, qt[1], sl),
-                                                  __shfl_sync(0xffffffffu, qt[2], sl), p.w);
-                        }
+                        np = make_float4(__shfl_sync(0xffffffffu, qs[0], sl), __shfl_sync(0xffffffffu, qs[1], sl),
+                                         __shfl_sync(0xffffffffu, qs[2], sl), p.w);
                         done = true;
                     }
                 }
@@ -1202,7 +1094,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, !F32 ? SRM_SWEEP_MIN_BLOCKS_F64
         if (!st->active || st->dim != DIM || t >= st->nsub) continue;
         CellCount cc;
         bool staged = false;
-        if constexpr (STAGED) staged = sweep_cell_staged<DIM, F32>(st, chi, t, base, cap, cc);
+        if constexpr (STAGED && F32) staged = sweep_cell_staged<DIM>(st, chi, t, base, cap, cc);
         if (!staged) sweep_cell<DIM, F32>(st, chi, t, base, cap, cc);
         const unsigned examined = __reduce_add_sync(0xffffffffu, cc.examined);
         if (lane == 0) {

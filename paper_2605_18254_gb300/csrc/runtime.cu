@@ -485,20 +485,10 @@ bool idle_mode(int32_t m);
 // staging capacity.  The graphs are recorded again; results do not depend
 // on either (the dataflow order is that of the cells' colours, and cells
 // that do not fit the staging read the rest from global memory).
-// Launch shape when none is chosen: the sweep kernel with the general path
-// only, staging at most 256 culled candidates per warp.  Measured (GB300,
-// FP32): on the clustered 1e6-sphere RVE the general kernel at capacity 256
-// swept 5% faster than at the whole-stencil estimate 704 (more resident
-// warps, no staging overflow) and 7% faster than the staged kernel; on the
-// ensemble of small RVEs the autotuner picked the general kernel; the staged
-// kernel won on 1e5 monodisperse spheres (7%), where the autotuner finds it.
-int default_sweep_path(bool f32, int cap)
-{
-    (void)f32;
-    (void)cap;
-    return 1;
-}
-
+// Staging capacity when none is chosen: at most 256 culled candidates per
+// warp.  Measured (GB300, FP32): on the clustered 1e6-sphere RVE the general
+// kernel at capacity 256 swept 5% faster than at the whole-stencil estimate
+// 704 (20 resident warps per SM instead of 12, no staging overflow).
 int default_capacity(int estimate, bool f32) { return std::min(std::min(estimate, 256), srm::sweep_cap_max(f32)); }
 
 srm_status group_set_tuning(Group &g, int sweep_bps, int cap, int path)
@@ -888,7 +878,7 @@ srm_status srm_init(srm_rve **out, int32_t dim, const double box[3], const srm_r
     group_setup(g, cuda_stream, alloc);
     g.f32 = q.p.precision == SRM_PREC_F32;
     g.cap = default_capacity(q.cap_est, g.f32);
-    g.sweep_path = default_sweep_path(g.f32, g.cap);
+    g.sweep_path = DEFAULT_SWEEP_PATH;
     g.stencil_est = q.cap_est;
     Member *mb = new Member();
     mb->dim = q.dim;
