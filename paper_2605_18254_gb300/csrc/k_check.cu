@@ -159,7 +159,7 @@ __device__ __forceinline__ void check_cell(RveDev *st, int cell, unsigned char *
     int hx, hy, hz;
     decode_cell((uint32_t)cell, st->gn, hx, hy, hz);
     int nst, center;
-    const uint32_t T = list_stencil(st, cs, hx, hy, hz, 0, S, nst, center);
+    const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
     const float w[3] = {(float)st->gw[0], (float)st->gw[1], (float)st->gw[2]};
     const double ox = hx * st->gw[0], oy = hy * st->gw[1], oz = hz * st->gw[2];
     auto approx = [&](const PT &c) -> float4 {

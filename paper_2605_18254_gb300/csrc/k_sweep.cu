@@ -369,7 +369,7 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
                        reinterpret_cast<const unsigned char *>(src) + 16 * (size_t)e);
     }
     int nst, center;
-    const uint32_t T = list_stencil(st, cs, hx, hy, hz, chi, S, nst, center);
+    const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
     // population of the 3^d cells around the home cell (Algorithm 5's own
     // candidate set; the listed stencil is larger when H = 2)
     uint32_t T3 = 0;

@@ -65,7 +65,7 @@ struct Group {
     int cap = 64;
     int sweep_bps = 0;  // blocks per SM of the sweep grid (0: all that fit)
     int sweep_path = 1;  // FP32 sweep variant: 1 general path only, 2 with the staged path
-    int stencil_est = 0;  // largest whole-stencil estimate of the members (the check's kernel choice)
+    int stencil_est = 0;  // particle-weighted mean whole-stencil estimate of the members (the check's kernel choice)
     BatchDev *d = nullptr;
     BatchShape sh{};
     cudaStream_t stream = nullptr;      // the caller's stream: all work runs here

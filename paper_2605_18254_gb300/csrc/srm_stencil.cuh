@@ -12,9 +12,9 @@ constexpr int MAX_ST = 125;
 struct StencilSmem {
     uint32_t b[MAX_ST];  // first sorted index of stencil cell j
     uint32_t o[MAX_ST + 1];  // offset of cell j in the flattened candidate list
-    int32_t cell[MAX_ST];    // linear index of stencil cell j
+    int32_t cell[MAX_ST];    // linear index of stencil cell j (staged path)
     int8_t sh[MAX_ST][3];    // unwrapped shift of cell j from the home cell
-    uint8_t low[MAX_ST];     // 1: cell j has a lower colour than the home cell
+    uint8_t low[MAX_ST];     // 1: cell j has a lower colour than the home cell (staged path)
     uint32_t n[MAX_ST];      // particles of cell j (staged path)
 };
 
@@ -30,10 +30,9 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int cap)
 
 // Lists the stencil cells of home (hx, hy, hz) and returns the candidate
 // count; the home cell is stencil cell 0, so its particles are candidates
-// 0 .. n_home-1.  Cells whose colour (c_x mod 3 + 3 (c_y mod 3) + 9 (c_z mod
-// 3)) is below chi are marked low.
+// 0 .. n_home-1.
 __device__ __forceinline__ uint32_t list_stencil(const RveDev *st, const uint32_t *cs, int hx, int hy,
-                                                 int hz, int chi, StencilSmem &S, int &nst, int &center)
+                                                 int hz, StencilSmem &S, int &nst, int &center)
 {
     const int lane = threadIdx.x & 31;
     const int H0 = st->H[0], H1 = st->H[1], H2 = st->H[2];
@@ -58,8 +57,6 @@ __device__ __forceinline__ uint32_t list_stencil(const RveDev *st, const uint32_
             const uint32_t b = cs[c];
             cnt = cs[c + 1] - b;
             S.b[j] = b;
-            S.cell[j] = c;
-            S.low[j] = (uint8_t)(cx % 3 + 3 * (cy % 3) + 9 * (cz % 3) < chi);
             S.sh[j][0] = (int8_t)dx;
             S.sh[j][1] = (int8_t)dy;
             S.sh[j][2] = (int8_t)dz;

@@ -81,11 +81,14 @@ def test_fp32_form_unchanged_by_the_flag():
     np.testing.assert_array_equal(runs[0], runs[1])
 
 
-def test_platelet_sweeps_equal_reference_images_mode():
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_platelet_sweeps_equal_reference_images_mode(kernel):
+    """Both platelet sweep kernels (a block per cell with the staged
+    neighbourhood; a warp per cell)."""
     w = srm_inputs.platelets(seed=11, n=3000, aspect=20.0, rho_t=3.0)
     lam = 2.5 * w.lambda0
     args = dict(c_w=w.c_w, c_m=0.05 * w.extra["D"], c_r=0.05)
-    g = srm.Platelets(w.box, w.x, w.u, w.a0, w.t0, lam, 1.0, w.seed, images=True, **args)
+    g = srm.Platelets(w.box, w.x, w.u, w.a0, w.t0, lam, 1.0, w.seed, images=True, sweep_kernel=kernel, **args)
     o = oracle.PlateletSystem(w.box, w.x, w.u, w.a0, w.t0, lam=lam, lam_t=1.0, seed=w.seed, contact=spec.address(),
                               images=True, **args)
     for _ in range(3):
@@ -95,4 +98,6 @@ def test_platelet_sweeps_equal_reference_images_mode():
         np.testing.assert_array_equal(gx, ox)
         np.testing.assert_array_equal(gu, ou)
         assert o.images_verify() == 0
+    st = g.sweep_stats()
+    assert st["staged_sweeps" if kernel == 0 else "warp_sweeps"] == 3
     g.close()
