@@ -357,9 +357,12 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
     const uint32_t hb = cs[cell], nh = cs[cell + 1] - hb;
     if (nh == 0) return;  // nothing moves: nobody waits for an empty cell
     const uint32_t epoch = (uint32_t)(st->sweep + 1);
-    wait_lower_colours<DIM>(st, cs, hx, hy, hz, chi, epoch);
-    // the pre-drawn directions of the cell's particles (slot order = the
-    // cell's particles in ascending id), copied while the stencil is staged
+    // before the wait (none of this changes while the lower-colour cells
+    // run): the pre-drawn directions of the cell's particles (slot order =
+    // the cell's particles in ascending id), the stencil list, and an L2
+    // prefetch of every candidate's line -- L2 is the point of coherence, so
+    // lines of cells still moving are refreshed by their writes, and the
+    // staging loads after the wait find them there
     const uint32_t npre = nh < (uint32_t)PRE_NH ? nh : (uint32_t)PRE_NH;
     {
         const PT *src = reinterpret_cast<const PT *>(st->dirs) + 2 * (size_t)hb;
@@ -370,6 +373,12 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
     }
     int nst, center;
     const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
+    for (int j = lane; j < nst; j += 32) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(pos + S.b[j]);
+        const uintptr_t e = a + (uintptr_t)(S.o[j + 1] - S.o[j]) * sizeof(PT);
+        for (uintptr_t l = a & ~(uintptr_t)127; l < e; l += 128) prefetch_l2(reinterpret_cast<const void *>(l));
+    }
+    wait_lower_colours<DIM>(st, cs, hx, hy, hz, chi, epoch);
     // population of the 3^d cells around the home cell (Algorithm 5's own
     // candidate set; the listed stencil is larger when H = 2)
     uint32_t T3 = 0;

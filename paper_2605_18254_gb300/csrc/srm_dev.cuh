@@ -144,6 +144,12 @@ __device__ __forceinline__ void fence_acquire()
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
+// Hint: bring the global-memory line holding p into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Largest r with off[r] <= x (off non-decreasing, off[0] = 0).
 __device__ __forceinline__ int find_seg(const int32_t *off, int B, int x)
 {
