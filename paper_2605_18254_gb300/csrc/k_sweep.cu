@@ -50,6 +50,7 @@ namespace srm {
 constexpr int NEAR_CAP = 64;
 constexpr int PRE_NH = 32;    // home particles whose first trials are copied up front
 constexpr int PRE_TRIALS = 2; // trials drawn ahead of the sweep per particle
+constexpr int RING = 4;       // general path (FP32 form): 32-candidate chunks staged in flight
 constexpr int NL_CAP = 256;   // staged path: entries of a particle's near index list
 
 template <bool F32>
@@ -57,11 +58,13 @@ struct SweepSmem {
     using PT = typename std::conditional<F32, float4, double4_32a>::type;
     using DT = typename std::conditional<F32, float, double>::type;
     // general path: stencil, culled candidates (FP64 form: plus binary32
-    // copies), near list, pre-drawn directions
+    // copies), near list, pre-drawn directions (FP32 form: plus the ring of
+    // chunks in flight and their stencil cells)
     static __host__ __device__ constexpr size_t bytes_general(int cap)
     {
         return (ST_HDR + (size_t)cap * sizeof(PT) + (F32 ? 0 : (size_t)cap * sizeof(float4)) +
-                (size_t)NEAR_CAP * sizeof(PT) + (size_t)PRE_NH * PRE_TRIALS * sizeof(PT) + 31) /
+                (size_t)NEAR_CAP * sizeof(PT) + (size_t)PRE_NH * PRE_TRIALS * sizeof(PT) +
+                (F32 ? (size_t)RING * 32 * (sizeof(PT) + 1) : 0) + 31) /
                32 * 32;
     }
     // staged path (FP32 form): stencil, every candidate, near bits (one word
@@ -119,6 +122,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most N of the latest committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Position of the k-th (from 0) set bit of m; m has more than k set bits.
 // It is the largest p with popc(m & (2^p - 1)) <= k: a binary search over p,
@@ -370,6 +380,7 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
         for (uint32_t e = lane; e < npre * PRE_TRIALS * PIECES; e += 32)
             cp_async16(reinterpret_cast<unsigned char *>(pre) + 16 * (size_t)e,
                        reinterpret_cast<const unsigned char *>(src) + 16 * (size_t)e);
+        cp_async_commit();
     }
     int nst, center;
     const uint32_t T = list_stencil(st, cs, hx, hy, hz, S, nst, center);
@@ -424,41 +435,82 @@ __device__ __forceinline__ void sweep_cell(RveDev *st, int chi, int t, unsigned 
     };
 
     // 1. stage the candidates that can reach the home cell (home first).
-    // The load of the next 32-candidate chunk is issued before the current
-    // one is culled.  Staging stops at the first chunk that would overflow
-    // the capacity; candidates from kstop on are read from global memory
-    // (culled the same way) when the near lists are built.
+    // FP32 form: RING - 1 chunks of 32 candidates ahead of the one being
+    // culled are in flight (cp.async into a ring in shared memory); FP64
+    // form: the load of the next chunk is issued before the current one is
+    // culled.  Staging stops at the first chunk that would overflow the
+    // capacity; candidates from kstop on are read from global memory (culled
+    // the same way) when the near lists are built.
     float rh = 0.f;
     for (uint32_t m = lane; m < nh; m += 32) rh = fmaxf(rh, (float)pos[hb + m].w);
     for (int o = 16; o > 0; o >>= 1) rh = fmaxf(rh, __shfl_xor_sync(0xffffffffu, rh, o));
     uint32_t Tk = 0, kstop = T;
     bool stop = false;
-    PT cn;
-    int jn = 0;
-    if (lane < T) cn = pos[locate(lane, jn)];
-    for (uint32_t k0 = 0; k0 < T; k0 += 32) {
-        const uint32_t k = k0 + lane;
-        const PT c = k < T ? shift(cn, jn) : cn;
-        if (k + 32 < T) cn = pos[locate(k + 32, jn)];
-        bool keep = false;
-        float4 ca;
-        if (k < T) {
-            ca = approx(c);
-            const float r = rh + ca.w + 2.f * cmf;
-            keep = k < nh || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+    if constexpr (F32) {
+        PT *ring = pre + PRE_NH * PRE_TRIALS;
+        uint8_t *rj = reinterpret_cast<uint8_t *>(ring + RING * 32);  // stencil cell of each ring entry
+        const uint32_t nq = (T + 31) / 32;
+        // chunk q into ring slot q mod RING, one commit group per chunk
+        auto issue = [&](uint32_t q) {
+            const uint32_t k = q * 32 + (uint32_t)lane;
+            if (q < nq && k < T) {
+                int j;
+                const uint32_t g = locate(k, j);
+                cp_async16(ring + (q % RING) * 32 + lane, pos + g);
+                rj[(q % RING) * 32 + lane] = (uint8_t)j;
+            }
+            cp_async_commit();
+        };
+        for (uint32_t q = 0; q + 1 < (uint32_t)RING; q++) issue(q);
+        for (uint32_t q = 0; q < nq; q++) {
+            issue(q + RING - 1);  // into the slot of chunk q - 1, culled in the last round
+            cp_async_wait_group<RING - 1>();
+            const uint32_t k0 = q * 32, k = k0 + lane;
+            bool keep = false;
+            PT c;
+            if (k < T) {
+                c = shift(ring[(q % RING) * 32 + lane], rj[(q % RING) * 32 + lane]);
+                const float r = rh + c.w + 2.f * cmf;
+                keep = k < nh || box_dist2(c, w, DIM) <= r * r * 1.0004f;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (Tk + __popc(bal) > (uint32_t)cap) {
+                kstop = k0;
+                stop = true;
+                break;
+            }
+            const uint32_t at = Tk + __popc(bal & ((1u << lane) - 1u));
+            if (keep) cpos[at] = c;
+            Tk += __popc(bal);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (Tk + __popc(bal) > (uint32_t)cap) {
-            kstop = k0;
-            stop = true;
-            break;
+    } else {
+        PT cn;
+        int jn = 0;
+        if (lane < T) cn = pos[locate(lane, jn)];
+        for (uint32_t k0 = 0; k0 < T; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            const PT c = k < T ? shift(cn, jn) : cn;
+            if (k + 32 < T) cn = pos[locate(k + 32, jn)];
+            bool keep = false;
+            float4 ca;
+            if (k < T) {
+                ca = approx(c);
+                const float r = rh + ca.w + 2.f * cmf;
+                keep = k < nh || box_dist2(ca, w, DIM) <= r * r * 1.0004f;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (Tk + __popc(bal) > (uint32_t)cap) {
+                kstop = k0;
+                stop = true;
+                break;
+            }
+            const uint32_t at = Tk + __popc(bal & ((1u << lane) - 1u));
+            if (keep) {
+                cpos[at] = c;
+                if constexpr (!F32) capx[at] = ca;
+            }
+            Tk += __popc(bal);
         }
-        const uint32_t at = Tk + __popc(bal & ((1u << lane) - 1u));
-        if (keep) {
-            cpos[at] = c;
-            if constexpr (!F32) capx[at] = ca;
-        }
-        Tk += __popc(bal);
     }
     if (stop && lane == 0) atomicAdd(&st->stage_overflow, 1ull);
     cp_async_wait();
