@@ -119,9 +119,9 @@ bool idle_mode(int32_t m);
 srm_status member_idle(Group &g, size_t r);
 srm_status group_set_tuning(Group &g, int sweep_bps, int cap, int path);
 // Sweep kernel when none is chosen: the general path only (measured on GB300,
-// FP32: 7% faster than the staged kernel on the clustered 1e6-sphere RVE and
-// 25% on the ensemble of small RVEs; 7% slower on 1e5 monodisperse spheres,
-// where srm_set_tuning can select the staged one).
+// FP32: faster than the staged kernel on the clustered 1e6-sphere RVE (7%),
+// on the ensemble of small RVEs (25%) and, with its L2 prefetch and staging
+// ring, on 1e5 monodisperse spheres (3%)).
 constexpr int DEFAULT_SWEEP_PATH = 1;
 int default_capacity(int estimate, bool f32);
 srm_status group_autotune(Group &g, int32_t supersteps, srm_tuning *best);
