@@ -624,8 +624,8 @@ def run_ensemble(args, rank, world, local_rank):
                               "stage_capacity": tuned.get("stage_capacity"),
                               "sweep_path": tuned.get("sweep_path"),
                               "how": "srm_batch_autotune during the first warm-up step (candidate sweep "
-                                     "grids, staging capacities and FP32 sweep kernels timed on the running "
-                                     "batch), applied to every later batch"},
+                                     "grids and staging capacities timed on the running batch; the sweep "
+                                     "kernel stays the default), applied to every later batch"},
                    "l2": "256 MiB buffer written between timed steps (L2 flushed)"},
         "time_to_target_s": dev / args.steps, "certified": all(r["ok"] for r in res),
         "e2e": {"value": upd / e2e, "unit": "particle-updates/s",
