@@ -882,6 +882,91 @@ __global__ void __launch_bounds__(128) k_pcheck(PltDev d, uint8_t *flags)
     if (hit) atomicAdd(&d.acc[1], 1ull);
 }
 
+// Algorithm 6 with a cell's neighbourhood in shared memory (where the sweep's
+// block kernel applies: the 27 cells around a cell hold every platelet
+// within contact reach of its platelets): a block of CW warps per cell (a
+// static stride over the cells), the warps taking the home platelets in
+// turn, each decided as a trial at the platelet's own place and normal
+// (trial_collides_staged, never stopped early).  Cells whose 27 neighbours
+// hold more than CCAP platelets are checked by warp 0 one thread per
+// platelet, as k_pcheck does.
+__global__ void __launch_bounds__(CW * 32, 1) k_pcheck_staged(PltDev d, uint8_t *flags)
+{
+    extern __shared__ __align__(32) unsigned char psm[];
+    CellStage &S = *reinterpret_cast<CellStage *>(psm);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) S.best[0] = 1 << 30;  // no early stop
+    for (int cell = blockIdx.x; cell < d.ncells; cell += gridDim.x) {
+        __syncthreads();
+        const int cx = cell % d.n[0], cy = (cell / d.n[0]) % d.n[1], cz = cell / (d.n[0] * d.n[1]);
+        if (d.start[cell + 1] == d.start[cell]) continue;  // the same for every thread
+        if (tid < 27) {
+            const int nx = wrapc(cx + tid % 3 - 1, d.n[0]), ny = wrapc(cy + (tid / 3) % 3 - 1, d.n[1]);
+            const int nz = wrapc(cz + tid / 9 - 1, d.n[2]);
+            const int nc = nx + d.n[0] * (ny + d.n[1] * nz);
+            S.ccell[tid] = nc;
+            S.cstart[tid + 1] = d.start[nc + 1] - d.start[nc];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            S.cstart[0] = 0;
+            for (int k = 1; k <= 27; k++) S.cstart[k] += S.cstart[k - 1];
+        }
+        __syncthreads();
+        const int nst = S.cstart[27];
+        unsigned long long hits = 0;
+        if (nst > CCAP) {
+            if (warp == 0) {
+                const int32_t k1 = d.start[cell + 1];
+                for (int32_t k = d.start[cell] + lane; k < k1; k += 32) {
+                    const int32_t i = d.members[k];
+                    const double4_32a xp = d.X[i], up = d.U[i];
+                    const double q[3] = {xp.x, xp.y, xp.z}, u[3] = {up.x, up.y, up.z};
+                    bool hit = false;
+                    for (int o = 0; o < 27 && !hit; o++) {
+                        const int32_t je = d.start[S.ccell[o] + 1];
+                        for (int32_t j = d.start[S.ccell[o]]; j < je && !hit; j++) {
+                            const int32_t tj = d.members[j];
+                            if (tj == i) continue;
+                            const double4_32a xt = d.X[tj], ut = d.U[tj];
+                            double dj[3];
+                            min_image(d, xt, q, dj);
+                            const double nt[3] = {ut.x, ut.y, ut.z};
+                            hit = collide(dj, u, nt, d.a, d.t);
+                        }
+                    }
+                    if (flags) flags[i] = hit ? 1 : 0;
+                    hits += hit ? 1 : 0;
+                }
+            }
+        } else {
+            const double c[3] = {(cx + 0.5) * d.w[0], (cy + 0.5) * d.w[1], (cz + 0.5) * d.w[2]};
+            for (int i = tid; i < nst; i += CW * 32) {
+                int k = 0;
+                while (S.cstart[k + 1] <= i) k++;
+                const int32_t id = d.members[d.start[S.ccell[k]] + (i - S.cstart[k])];
+                const double4_32a x = d.X[id];
+                S.X[i] = x;
+                S.U[i] = d.U[id];
+                S.F[i] = stage_offset(d, x, c);
+                S.id[i] = id;
+            }
+            __syncthreads();
+            const int hs = S.cstart[13], he = S.cstart[14];
+            for (int m = hs + warp; m < he; m += CW) {
+                const double q[3] = {S.X[m].x, S.X[m].y, S.X[m].z}, u[3] = {S.U[m].x, S.U[m].y, S.U[m].z};
+                const bool hit = trial_collides_staged(d, S, nst, S.id[m], 0, &S.best[0], q, u, c, warp, lane);
+                if (lane == 0) {
+                    if (flags) flags[S.id[m]] = hit ? 1 : 0;
+                    hits += hit ? 1 : 0;
+                }
+            }
+        }
+        hits = __reduce_add_sync(0xffffffffu, (unsigned)hits);
+        if (lane == 0 && hits) atomicAdd(&d.acc[1], hits);
+    }
+}
+
 __global__ void k_ppairs(const double *dj, const double *ni, const double *nj, long long m, double a, double t,
                          uint8_t *out)
 {
@@ -1059,6 +1144,19 @@ int staged_blocks_per_sm()
     return per_sm;
 }
 
+int staged_check_blocks_per_sm()
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(srm::plt::k_pcheck_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(srm::plt::CellStage));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srm::plt::k_pcheck_staged, srm::plt::CW * 32,
+                                                      sizeof(srm::plt::CellStage));
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm;
+}
+
 // One sweep of Algorithm 3 on copy c at scale lam, binned on the grid of
 // lam_grid; advances the sweep counter.
 srm_status sweep_once(srm_plt *h, int c, double lam, double lam_grid)
@@ -1118,7 +1216,18 @@ srm_status check_copy(srm_plt *h, int c, double lam, double lam_grid, uint8_t *f
     srm_status st = bin(h, c, lam, lam_grid, d);
     if (st != SRM_OK) return st;
     CK(cudaMemsetAsync(h->acc + 1, 0, sizeof(unsigned long long), h->s));
-    srm::plt::k_pcheck<<<(int)((h->n + 127) / 128), 128, 0, h->s>>>(d, flags_dev);
+    if (h->p.sweep_kernel == 0 && staged_fits(d)) {
+        const int per_sm = staged_check_blocks_per_sm();
+        int sms = 0, dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int64_t blocks = (int64_t)per_sm * sms;
+        if (blocks > d.ncells) blocks = d.ncells;
+        srm::plt::k_pcheck_staged<<<(int)blocks, srm::plt::CW * 32, sizeof(srm::plt::CellStage), h->s>>>(d,
+                                                                                                         flags_dev);
+    } else {
+        srm::plt::k_pcheck<<<(int)((h->n + 127) / 128), 128, 0, h->s>>>(d, flags_dev);
+    }
     CK(cudaGetLastError());
     unsigned long long col = 0;
     if ((st = read_counters(h, moves, col)) != SRM_OK) return st;
