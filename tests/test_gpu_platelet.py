@@ -192,13 +192,16 @@ def test_run_to_target_bit_exact():
     g.close()
 
 
-def test_check_flags_bit_exact():
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_check_flags_bit_exact(kernel):
+    """Kernel 0: a block per cell with the staged neighbourhood (this grid
+    qualifies); kernel 1: a thread per platelet."""
     rng = np.random.default_rng(14)
     n = 4000
     x = rng.uniform(0, 1, (n, 3))
     u = rand_units(rng, n)
     a0, t0 = 0.02, 0.002
-    g = srm.Platelets((1, 1, 1), x, u, a0, t0, 1.0, 1.0, 3, c_m=0.001)
+    g = srm.Platelets((1, 1, 1), x, u, a0, t0, 1.0, 1.0, 3, c_m=0.001, sweep_kernel=kernel)
     cnt, flags = g.check()
     o = oracle.PlateletSystem((1, 1, 1), x, u, a0, t0, contact=spec.address())
     ocnt, oflags = o.check()
