@@ -73,12 +73,13 @@ typedef struct srm_plt_params {
                          /* difference to a platelet near a face is taken to   */
                          /* its periodic image, (x_j + s L) - x_i, one         */
                          /* rounding per axis                                  */
-    int32_t sweep_kernel; /* 0: a block per cell with the 27 cells around it  */
-                         /* in shared memory wherever that set holds every     */
-                         /* platelet a trial can touch (stencil half-width 1   */
-                         /* and 2 (a + t) + 2^-15 a + 2 c_m below the cell     */
-                         /* width), else a warp per cell reading global        */
-                         /* memory; 1: always a warp per cell.  Same results.  */
+    int32_t sweep_kernel; /* 0: sweeps and checks with a block per cell and   */
+                         /* the 27 cells around it in shared memory wherever   */
+                         /* that set holds every platelet a trial can touch    */
+                         /* (stencil half-width 1 and 2 (a + t) + 2^-15 a +    */
+                         /* 2 c_m below the cell width), else a warp per cell  */
+                         /* (sweep) and a thread per platelet (check) reading  */
+                         /* global memory; 1: always the latter.  Same results */
 } srm_plt_params;
 
 /* Defaults: c_w = 0.01, c_m = 0 (must be set), c_r = 0, N_k = N_l =
