@@ -31,7 +31,7 @@ def main(argv=None):
                     help="FP32 sweep kernel: 1 general path only, 2 with the staged path, 0 the default")
     ap.add_argument("--stage-capacity", type=int, default=0, help="sweep staging capacity (0: the default)")
     ap.add_argument("--plt-kernel", type=int, default=0, choices=[0, 1],
-                    help="platelet sweep: 0 block per cell where it applies, 1 warp per cell")
+                    help="platelet sweeps and checks: 0 a block per cell where it applies, 1 warp per cell / thread per platelet")
     a = ap.parse_args(argv)
     import torch
 
