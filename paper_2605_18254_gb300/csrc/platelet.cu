@@ -14,15 +14,18 @@
 // 1); per sweep a cell list (cell of each platelet, cell starts, ids sorted
 // by cell and by id inside a cell) and one completion stamp per cell.
 //
-// Sweep: one launch per sweep.  Each warp takes the next cell from a work
-// counter in canonical colour order, waits until the cells of lower colour
-// within reach are stamped for this sweep (bounded polls), then moves the
-// cell's platelets one after the other in id order: all lanes form the same
-// trial, lanes 0..26 each scan one of the 27 cells around the trial's cell
-// for platelets within bounding-sphere reach, all 32 lanes then decide the
-// staged pairs (binary32, the cost of the method), and a warp vote accepts
-// the first trial without a collision.  Lane 0 writes the new state; the
-// cell's stamp is released at the end.
+// Sweep: one launch per sweep, cells from a work counter in canonical colour
+// order, each waiting until the cells of lower colour within reach are
+// stamped for this sweep (bounded polls), then moving its platelets one
+// after the other in id order and releasing its stamp.  Two kernels with the
+// same results: k_psweep_staged (a block per cell, the 27 cells around it in
+// shared memory, eight trials decided at once; wherever that set holds every
+// platelet a trial can touch) and k_psweep (a warp per cell: all lanes form
+// the same trial, lanes 0..26 each scan one of the 27 cells around the
+// trial's cell for platelets within bounding-sphere reach, all 32 lanes then
+// decide the staged pairs, and a warp vote accepts the first trial without a
+// collision).  The check (Algorithm 6) likewise: k_pcheck_staged or
+// k_pcheck.
 #include <cmath>
 #include <cstring>
 #include <new>
