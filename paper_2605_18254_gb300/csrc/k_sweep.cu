@@ -22,14 +22,17 @@
 // before the sweep, so that the sweep itself draws only the later trials of
 // the few particles whose first two trials collide.
 //
-// Per cell, one warp:
-//  1. lists the stencil cells (home cell first) and stages in shared memory
-//     the candidates that can reach the home cell: distance to the home
-//     cell box <= R_home,max + R_t + 2 c_m (a conservative bound: trials stay
-//     within c_m of positions that stay within c_m of the box).  FP32 form:
-//     positions relative to the home cell corner; FP64 form: absolute
-//     binary64 positions plus binary32 copies relative to the corner (the
-//     next chunk's loads are in flight while a chunk is culled);
+// Per cell, one warp (the general path; the staged path is described at
+// sweep_cell_staged):
+//  0. before waiting for the lower-colour neighbours, lists the stencil cells
+//     (home cell first) and prefetches every candidate's line into L2;
+//  1. stages in shared memory the candidates that can reach the home cell:
+//     distance to the home cell box <= R_home,max + R_t + 2 c_m (a
+//     conservative bound: trials stay within c_m of positions that stay
+//     within c_m of the box).  FP32 form: positions relative to the home
+//     cell corner, four 32-candidate chunks in flight (cp.async ring); FP64
+//     form: absolute binary64 positions plus binary32 copies relative to the
+//     corner, the next chunk's loads in flight while a chunk is culled;
 //  2. for each particle of the cell, in ascending id: builds its near list,
 //     the candidates within R_i + R_t + c_m of it (superset of everything a
 //     trial can touch), as copies in shared memory; the two pre-drawn trials,
